@@ -1,0 +1,446 @@
+/*
+ * Plain CPU oracle for the compression scheme of Masui et al.,
+ * "A compression scheme for radio data in high performance computing"
+ * (arXiv:1503.00638).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg load this file's library.  The CUDA path shares
+ * no code, header, table or constant with it.
+ *
+ * Everything here is written to be read against the paper, one element or one
+ * bit at a time, with no blocking, fusion or reordering beyond what the paper's
+ * definitions state.  Compile with -O2 -ffp-contract=off so that no multiply-add
+ * is contracted (the float32 arithmetic of reading R1 below must be rounded
+ * after every operation).
+ *
+ * Readings of the paper where it is silent (numbered as in the design doc):
+ *   R1  q = 12 f s^2 is evaluated in float32, each operation rounded to
+ *       nearest: c = fl32(6 f / N); cross q = (c * A_i) * A_j;
+ *       auto q = ((2c) * A_i) * A_i.
+ *   R2  no rounding when q is not a positive, finite, normal float32.
+ *   R3  autos A_i are the unrounded real parts of product (i,i).
+ *   R4  products are ordered upper-triangle row-major: (0,0),(0,1),..,(0,n-1),
+ *       (1,1),(1,2),...
+ *   R5  the sign of a value that rounds to zero is kept.
+ *   R6  NaN and +-inf pass through; subnormals round like any other value.
+ *   R7  rounding up past FLT_MAX gives +-inf.
+ *   R9  a trailing partial block is shortened to a multiple of 8 elements and
+ *       transposed like a full block; the last (n mod 8) elements are copied
+ *       verbatim.
+ *   R11 compressed framing: 8-byte big-endian uncompressed byte count, 4-byte
+ *       big-endian block size in bytes, then per block a 4-byte big-endian
+ *       compressed length followed by the LZ4 block, then the verbatim tail.
+ */
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+#include <math.h>
+#include <float.h>
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1: noise from the radiometer equation                              */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. rad_simple evaluated on its diagonal (g = i, h = j, beta = alpha):
+ *   C_{aij,aij} = (1 + delta_ij) (1 - delta_ij delta_{a,Im}) V_ii V_jj / (2N).
+ * For a diagonal covariance the unmarginalized noise of Eq. noise,
+ * s^2 = 1 / (C^-1)_{aij,aij}, equals this diagonal entry.
+ * alpha = 0 for the real part, 1 for the imaginary part.  fp64. */
+double orc_rad_simple_var(int i, int j, int alpha, double Vii, double Vjj, double N)
+{
+    double d_ij = (i == j) ? 1.0 : 0.0;
+    double d_aim = (alpha == 1) ? 1.0 : 0.0;
+    return (1.0 + d_ij) * (1.0 - d_ij * d_aim) * Vii * Vjj / (2.0 * N);
+}
+
+/* Eq. rad_full1-3: covariance between component alpha of V_ij and component
+ * beta of V_gh, from the complex correlation matrix V (n x n, row-major,
+ * interleaved re/im, Hermitian).  fp64. */
+double orc_rad_full_cov(const double *V, int n, int alpha, int i, int j,
+                        int beta, int g, int h, double N)
+{
+#define VRE(a, b) V[2 * ((long)(a) * n + (b))]
+#define VIM(a, b) V[2 * ((long)(a) * n + (b)) + 1]
+    /* X = V_ig conj(V_jh),  Y = V_ih conj(V_jg) */
+    double xr = VRE(i, g) * VRE(j, h) + VIM(i, g) * VIM(j, h);
+    double xi = VIM(i, g) * VRE(j, h) - VRE(i, g) * VIM(j, h);
+    double yr = VRE(i, h) * VRE(j, g) + VIM(i, h) * VIM(j, g);
+    double yi = VIM(i, h) * VRE(j, g) - VRE(i, h) * VIM(j, g);
+#undef VRE
+#undef VIM
+    if (alpha == 0 && beta == 0) return (xr + yr) / (2.0 * N);   /* rad_full1 */
+    if (alpha == 1 && beta == 1) return (xr - yr) / (2.0 * N);   /* rad_full2 */
+    if (alpha == 0 && beta == 1) return (-xi + yi) / (2.0 * N);  /* rad_full3 */
+    /* C_{Im ij, Re gh} = C_{Re gh, Im ij}: rad_full3 with the pairs swapped */
+    return orc_rad_full_cov(V, n, 0, g, h, 1, i, j, N);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.2: granularity and rounding                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Reading R1: q = 12 f s^2 in float32 with a fixed operation order.
+ * Cross (i != j): s^2 = A_i A_j / (2N)  =>  q = (6f/N) A_i A_j.
+ * Auto real part: s^2 = A_i^2 / N     =>  q = (12f/N) A_i^2.          */
+float orc_q32(int is_auto, float Ai, float Aj, double f, double N)
+{
+    float c = (float)(6.0 * f / N);
+    if (is_auto) {
+        float c2 = 2.0f * c;
+        float t = c2 * Ai;
+        return t * Ai;
+    }
+    float t = c * Ai;
+    return t * Aj;
+}
+
+/* Eq. trunc_error: the granularity is the largest power of two g = 2^k with
+ * g < sqrt(q), i.e. 4^k < q.  Found by exact comparisons in fp64 (q is a
+ * float32, so it and every 4^k used here are exact doubles).
+ * Returns 0 and leaves *k alone when reading R2 says "no rounding". */
+int orc_granularity_exponent(float q, int *k)
+{
+    if (!(q > 0.0f) || !isfinite(q) || q < FLT_MIN) return 0;
+    double qd = (double)q;
+    int kk = 0;
+    while (ldexp(1.0, 2 * kk) >= qd) kk--;
+    while (ldexp(1.0, 2 * (kk + 1)) < qd) kk++;
+    *k = kk;
+    return 1;
+}
+
+/* Round x to the nearest multiple of 2^k, ties to the even multiple
+ * (Sec. 3.2 and its footnote on IEEE 754 ties-to-even).  The scaling by 2^-k
+ * and back is exact in fp64; nearbyint rounds half to even in the default
+ * rounding mode; the final conversion is exact or overflows (R7). */
+float orc_round_pow2(float x, int k)
+{
+    if (!isfinite(x)) return x;                       /* R6 */
+    double y = nearbyint(ldexp((double)x, -k));
+    return (float)ldexp(y, k);
+}
+
+/* One element: round x given its q (R2: no rounding when q is unusable). */
+float orc_round_element(float x, float q)
+{
+    int k;
+    if (!orc_granularity_exponent(q, &k)) return x;
+    return orc_round_pow2(x, k);
+}
+
+/* Precision reduction of a visibility cube (Sec. 6, steps 1-3).
+ * in/out: [n_freq][n_prod][n_time] complex64 stored as interleaved float32
+ * (re, im), time fastest; n_prod = n_in (n_in + 1) / 2 in the order of R4.
+ * Autos come from the unrounded input (R3).  Out of place. */
+void orc_reduce_precision_c64(const float *in, float *out, long n_freq, long n_in,
+                              long n_time, double N, double f)
+{
+    long n_prod = n_in * (n_in + 1) / 2;
+    for (long fr = 0; fr < n_freq; fr++) {
+        long p = 0;
+        for (long i = 0; i < n_in; i++) {
+            for (long j = i; j < n_in; j++, p++) {
+                for (long t = 0; t < n_time; t++) {
+                    long e = ((fr * n_prod + p) * n_time + t) * 2;
+                    /* product (i,i) sits at index i*n_in - i*(i-1)/2 (R4) */
+                    long pii = i * n_in - i * (i - 1) / 2;
+                    long pjj = j * n_in - j * (j - 1) / 2;
+                    float Ai = in[((fr * n_prod + pii) * n_time + t) * 2];
+                    float Aj = in[((fr * n_prod + pjj) * n_time + t) * 2];
+                    if (i == j) {
+                        float q = orc_q32(1, Ai, Ai, f, N);
+                        out[e] = orc_round_element(in[e], q);
+                        out[e + 1] = in[e + 1];   /* s = 0 for Im V_ii */
+                    } else {
+                        float q = orc_q32(0, Ai, Aj, f, N);
+                        out[e] = orc_round_element(in[e], q);
+                        out[e + 1] = orc_round_element(in[e + 1], q);
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* The granularity exponent chosen for every float of the cube (for tests of
+ * Sec. 5.1's error distribution).  No rounding is marked as -1000. */
+void orc_granularity_map_c64(const float *in, int32_t *kout, long n_freq, long n_in,
+                             long n_time, double N, double f)
+{
+    long n_prod = n_in * (n_in + 1) / 2;
+    for (long fr = 0; fr < n_freq; fr++) {
+        long p = 0;
+        for (long i = 0; i < n_in; i++) {
+            for (long j = i; j < n_in; j++, p++) {
+                for (long t = 0; t < n_time; t++) {
+                    long e = ((fr * n_prod + p) * n_time + t) * 2;
+                    long pii = i * n_in - i * (i - 1) / 2;
+                    long pjj = j * n_in - j * (j - 1) / 2;
+                    float Ai = in[((fr * n_prod + pii) * n_time + t) * 2];
+                    float Aj = in[((fr * n_prod + pjj) * n_time + t) * 2];
+                    int k;
+                    float q = orc_q32(i == j, Ai, Aj, f, N);
+                    int ok = orc_granularity_exponent(q, &k);
+                    kout[e] = ok ? k : -1000;
+                    kout[e + 1] = (ok && i != j) ? k : -1000;
+                }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.2: Bitshuffle, the blocked bit transpose                           */
+/* ------------------------------------------------------------------------ */
+
+/* Bit r of element e (r = 8 * byte + bit, little-endian element, LSB = bit 0
+ * as in the caption of Fig. f:bits) moves to bit-row r of the block:
+ * byte r * (B/8) + e/8, bit e % 8.  Blocks of B elements, tail per R9. */
+static void transpose_block(const uint8_t *in, uint8_t *out, size_t B, size_t es)
+{
+    memset(out, 0, B * es);
+    for (size_t e = 0; e < B; e++) {
+        for (size_t r = 0; r < 8 * es; r++) {
+            unsigned bit = (in[e * es + r / 8] >> (r % 8)) & 1u;
+            out[r * (B / 8) + e / 8] |= (uint8_t)(bit << (e % 8));
+        }
+    }
+}
+
+static void untranspose_block(const uint8_t *in, uint8_t *out, size_t B, size_t es)
+{
+    memset(out, 0, B * es);
+    for (size_t e = 0; e < B; e++) {
+        for (size_t r = 0; r < 8 * es; r++) {
+            unsigned bit = (in[r * (B / 8) + e / 8] >> (e % 8)) & 1u;
+            out[e * es + r / 8] |= (uint8_t)(bit << (r % 8));
+        }
+    }
+}
+
+static size_t default_block(size_t es, size_t block_elems)
+{
+    /* Sec. 4.2.1: the default block is 4096 bytes */
+    return block_elems ? block_elems : 4096 / es;
+}
+
+int orc_bitshuffle(const void *vin, void *vout, size_t n, size_t es, size_t block_elems,
+                   int inverse)
+{
+    const uint8_t *in = (const uint8_t *)vin;
+    uint8_t *out = (uint8_t *)vout;
+    if (!(es == 1 || es == 2 || es == 4 || es == 8)) return -1;
+    size_t B = default_block(es, block_elems);
+    if (B % 8 != 0) return -1;
+    size_t done = 0;
+    while (done < n) {
+        size_t Bb = n - done >= B ? B : (n - done) - (n - done) % 8;
+        if (Bb == 0) break;
+        if (inverse) untranspose_block(in + done * es, out + done * es, Bb, es);
+        else transpose_block(in + done * es, out + done * es, Bb, es);
+        done += Bb;
+    }
+    memcpy(out + done * es, in + done * es, (n - done) * es);   /* R9 tail */
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.1: LZ4 block codec (LZ77 class: literals + (offset, length) pairs) */
+/* ------------------------------------------------------------------------ */
+
+#define LZ4_MINMATCH 4
+#define LZ4_LASTLITERALS 5    /* the last 5 bytes of a block are literals */
+#define LZ4_MFLIMIT 12        /* a match starts at least 12 bytes before the end */
+
+size_t orc_lz4_bound(size_t n) { return n + n / 255 + 16; }
+
+static size_t put_len(uint8_t *op, size_t v)
+{
+    size_t w = 0;
+    while (v >= 255) { op[w++] = 255; v -= 255; }
+    op[w++] = (uint8_t)v;
+    return w;
+}
+
+static uint32_t read32le(const uint8_t *p)
+{
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) |
+           ((uint32_t)p[3] << 24);
+}
+
+/* Greedy LZ4 encoder: a 4096-entry table of the last position of each 4-byte
+ * hash, every position probed (step 1), the first verified match taken and
+ * extended forward.  Returns the compressed size, or 0 if cap is too small. */
+size_t orc_lz4_compress_block(const uint8_t *src, size_t n, uint8_t *dst, size_t cap)
+{
+    int32_t table[4096];
+    for (int h = 0; h < 4096; h++) table[h] = -1;
+    size_t anchor = 0, i = 0, o = 0;
+    if (cap < orc_lz4_bound(n)) return 0;
+    if (n >= LZ4_MFLIMIT + 1) {
+        while (i + LZ4_MFLIMIT <= n) {
+            uint32_t w = read32le(src + i);
+            uint32_t h = (w * 2654435761u) >> 20;
+            int32_t c = table[h];
+            table[h] = (int32_t)i;
+            if (c >= 0 && i - (size_t)c <= 65535 && read32le(src + c) == w) {
+                size_t L = LZ4_MINMATCH;
+                while (i + L < n - LZ4_LASTLITERALS && src[c + L] == src[i + L]) L++;
+                size_t LL = i - anchor, ML = L - LZ4_MINMATCH;
+                uint8_t *tok = dst + o++;
+                *tok = (uint8_t)(((LL < 15 ? LL : 15) << 4) | (ML < 15 ? ML : 15));
+                if (LL >= 15) o += put_len(dst + o, LL - 15);
+                memcpy(dst + o, src + anchor, LL);
+                o += LL;
+                size_t off = i - (size_t)c;
+                dst[o++] = (uint8_t)(off & 255);
+                dst[o++] = (uint8_t)(off >> 8);
+                if (ML >= 15) o += put_len(dst + o, ML - 15);
+                i += L;
+                anchor = i;
+            } else {
+                i++;
+            }
+        }
+    }
+    size_t LL = n - anchor;
+    dst[o++] = (uint8_t)((LL < 15 ? LL : 15) << 4);
+    if (LL >= 15) o += put_len(dst + o, LL - 15);
+    memcpy(dst + o, src + anchor, LL);
+    o += LL;
+    return o;
+}
+
+/* Strict LZ4 block decoder.  Returns 0 when src decodes to exactly dst_len
+ * bytes; a negative code otherwise:
+ *   -1 input ended early       -2 literal run overruns the output
+ *   -3 offset 0                -4 offset reaches before the block start
+ *   -5 match overruns output   -6 output shorter than expected
+ *   -7 a match breaks the end-of-block rules (starts later than 12 bytes
+ *      before the end, or ends inside the last 5 bytes)                    */
+int orc_lz4_decompress_block(const uint8_t *src, size_t src_len, uint8_t *dst, size_t dst_len)
+{
+    size_t ip = 0, op = 0;
+    for (;;) {
+        if (ip >= src_len) return -1;
+        unsigned token = src[ip++];
+        size_t LL = token >> 4;
+        if (LL == 15) {
+            unsigned b;
+            do {
+                if (ip >= src_len) return -1;
+                b = src[ip++];
+                LL += b;
+            } while (b == 255);
+        }
+        if (LL > src_len - ip) return -1;
+        if (LL > dst_len - op) return -2;
+        memcpy(dst + op, src + ip, LL);
+        ip += LL;
+        op += LL;
+        if (ip == src_len) break;              /* last sequence: literals only */
+        if (src_len - ip < 2) return -1;
+        size_t off = (size_t)src[ip] | ((size_t)src[ip + 1] << 8);
+        ip += 2;
+        if (off == 0) return -3;
+        if (off > op) return -4;
+        size_t ML = token & 15u;
+        if (ML == 15) {
+            unsigned b;
+            do {
+                if (ip >= src_len) return -1;
+                b = src[ip++];
+                ML += b;
+            } while (b == 255);
+        }
+        ML += LZ4_MINMATCH;
+        if (ML > dst_len - op) return -5;
+        if (op + LZ4_MFLIMIT > dst_len || op + ML + LZ4_LASTLITERALS > dst_len) return -7;
+        for (size_t k = 0; k < ML; k++) dst[op + k] = dst[op + k - off];   /* overlap = RLE */
+        op += ML;
+    }
+    return op == dst_len ? 0 : -6;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bitshuffle + LZ4 per block with the framing of reading R11                */
+/* ------------------------------------------------------------------------ */
+
+static void put_be64(uint8_t *p, uint64_t v) { for (int k = 7; k >= 0; k--) { p[k] = (uint8_t)v; v >>= 8; } }
+static void put_be32(uint8_t *p, uint32_t v) { for (int k = 3; k >= 0; k--) { p[k] = (uint8_t)v; v >>= 8; } }
+static uint64_t get_be64(const uint8_t *p) { uint64_t v = 0; for (int k = 0; k < 8; k++) v = (v << 8) | p[k]; return v; }
+static uint32_t get_be32(const uint8_t *p) { uint32_t v = 0; for (int k = 0; k < 4; k++) v = (v << 8) | p[k]; return v; }
+
+size_t orc_compress_bound(size_t n, size_t es, size_t block_elems)
+{
+    size_t B = default_block(es, block_elems);
+    size_t nb = n / B, rem = n % B, last = rem - rem % 8;
+    size_t bound = 12 + nb * (4 + orc_lz4_bound(B * es));
+    if (last) bound += 4 + orc_lz4_bound(last * es);
+    return bound + (rem % 8) * es;
+}
+
+/* Returns the compressed size, or 0 on a bad argument / small capacity.
+ * block_sizes (may be NULL) receives the compressed length of every block. */
+size_t orc_compress(const void *vin, size_t n, size_t es, size_t block_elems,
+                    void *vout, size_t cap, uint32_t *block_sizes)
+{
+    const uint8_t *in = (const uint8_t *)vin;
+    uint8_t *out = (uint8_t *)vout;
+    if (!(es == 1 || es == 2 || es == 4 || es == 8)) return 0;
+    size_t B = default_block(es, block_elems);
+    if (B % 8 != 0 || B * es > 65536) return 0;
+    if (cap < orc_compress_bound(n, es, block_elems)) return 0;
+    put_be64(out, (uint64_t)(n * es));
+    put_be32(out + 8, (uint32_t)(B * es));
+    size_t o = 12, done = 0, b = 0;
+    uint8_t shuf[65536];
+    while (done < n) {
+        size_t Bb = n - done >= B ? B : (n - done) - (n - done) % 8;
+        if (Bb == 0) break;
+        transpose_block(in + done * es, shuf, Bb, es);
+        size_t c = orc_lz4_compress_block(shuf, Bb * es, out + o + 4, orc_lz4_bound(Bb * es));
+        put_be32(out + o, (uint32_t)c);
+        if (block_sizes) block_sizes[b] = (uint32_t)c;
+        o += 4 + c;
+        done += Bb;
+        b++;
+    }
+    memcpy(out + o, in + done * es, (n - done) * es);
+    return o + (n - done) * es;
+}
+
+/* Returns 0 on success, or a negative code: -10 bad argument, -11 header does
+ * not match (n, es, block size), -12 stream truncated, -13 trailing bytes,
+ * or the block decoder's code. */
+int orc_decompress(const void *vin, size_t in_len, void *vout, size_t n, size_t es,
+                   size_t block_elems)
+{
+    const uint8_t *in = (const uint8_t *)vin;
+    uint8_t *out = (uint8_t *)vout;
+    if (!(es == 1 || es == 2 || es == 4 || es == 8)) return -10;
+    size_t B = default_block(es, block_elems);
+    if (B % 8 != 0 || B * es > 65536) return -10;
+    if (in_len < 12) return -12;
+    if (get_be64(in) != (uint64_t)(n * es) || get_be32(in + 8) != (uint32_t)(B * es)) return -11;
+    size_t ip = 12, done = 0;
+    uint8_t shuf[65536];
+    while (done < n) {
+        size_t Bb = n - done >= B ? B : (n - done) - (n - done) % 8;
+        if (Bb == 0) break;
+        if (in_len - ip < 4) return -12;
+        size_t c = get_be32(in + ip);
+        ip += 4;
+        if (c > in_len - ip) return -12;
+        int rc = orc_lz4_decompress_block(in + ip, c, shuf, Bb * es);
+        if (rc) return rc;
+        untranspose_block(shuf, out + done * es, Bb, es);
+        ip += c;
+        done += Bb;
+    }
+    size_t tail = (n - done) * es;
+    if (in_len - ip < tail) return -12;
+    memcpy(out + done * es, in + ip, tail);
+    if (ip + tail != in_len) return -13;
+    return 0;
+}

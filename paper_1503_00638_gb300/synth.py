@@ -1,0 +1,127 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only *makes* data; it holds none of the compression arithmetic.
+The same bytes feed the CUDA path and the CPU oracle.
+
+Visibility cubes stand in for the CHIME Pathfinder data of Sec. 5 (shape
+[freq][product][time], time fastest, products in upper-triangle row-major
+order, complex64).  Each (freq, time) sample is made like a correlator output:
+
+* autos V_ii: a per-input, per-frequency system power A_i(f), plus its own
+  thermal scatter of variance A_i^2 / N_samp; the imaginary part is +0.0;
+* crosses V_ij: a sky term rho * sqrt(A_i A_j) * exp(i(2 pi t (j - i) / (n T_s) + phi_ij))
+  (rho = 0.05: the sky adds well under 40 % of the power, as Sec. 3.1 says of
+  CHIME) plus thermal scatter of variance A_i A_j / (2 N_samp) per component.
+
+The thermal scatter levels are the physics of a synthetic instrument that
+integrates N_samp samples; ``tests/test_synth.py`` checks them against a
+brute-force simulation of voltages.  Random walks (Sec. 5's "highly
+correlated along time" regime, without rounding) feed the codec-only cases.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["VisConfig", "CONFIG_SMALL", "CONFIG_CHIME", "visibilities", "random_walk",
+           "n_products", "auto_product_index"]
+
+
+class VisConfig:
+    def __init__(self, n_freq, n_inputs, n_time, n_samp, f, seed=0, drift=False,
+                 rho=0.05, t_sky=64.0):
+        self.n_freq, self.n_inputs, self.n_time = n_freq, n_inputs, n_time
+        self.n_samp, self.f, self.seed, self.drift = float(n_samp), f, seed, drift
+        self.rho, self.t_sky = rho, t_sky
+
+    @property
+    def n_prod(self):
+        return n_products(self.n_inputs)
+
+    @property
+    def shape(self):
+        return (self.n_freq, self.n_prod, self.n_time)
+
+    @property
+    def nbytes(self):
+        return self.n_freq * self.n_prod * self.n_time * 8
+
+    def describe(self):
+        return (f"{self.n_freq} freq x {self.n_prod} products ({self.n_inputs} inputs) x "
+                f"{self.n_time} time, complex64, N=2^{int(np.log2(self.n_samp))}, f={self.f}, "
+                f"seed {self.seed}")
+
+
+# 16 freq x 136 products (16 inputs) x 64 time, N = 2^16, f = 0.01
+CONFIG_SMALL = VisConfig(16, 16, 64, 2 ** 16, 0.01, seed=0)
+# CHIME-Pathfinder-shaped: 1024 freq x 8256 products (128 inputs) x 16 time, N = 2^17
+CONFIG_CHIME = VisConfig(1024, 128, 16, 2 ** 17, 0.01, seed=0, drift=True)
+
+
+def n_products(n_inputs: int) -> int:
+    return n_inputs * (n_inputs + 1) // 2
+
+
+def auto_product_index(i: int, n_inputs: int) -> int:
+    """Index of product (i, i) in upper-triangle row-major order."""
+    return i * n_inputs - i * (i - 1) // 2
+
+
+def _pairs(n):
+    ii, jj = np.triu_indices(n)
+    return ii, jj
+
+
+def visibilities(cfg: VisConfig, freq_lo: int = 0, freq_hi: int | None = None) -> np.ndarray:
+    """The [freq][prod][time] complex64 cube of ``cfg`` (frequencies
+    [freq_lo, freq_hi) only, identical to slicing the full cube)."""
+    F, n, T = cfg.n_freq, cfg.n_inputs, cfg.n_time
+    freq_hi = F if freq_hi is None else freq_hi
+    ii, jj = _pairs(n)
+    P = ii.size
+    g0 = np.random.Generator(np.random.PCG64(cfg.seed))
+    base = g0.uniform(50.0, 150.0, size=(n, F))          # A_i(f) before drift
+    phase_in = g0.uniform(0.0, 2 * np.pi, size=n)
+    phi = g0.uniform(0.0, 2 * np.pi, size=P)              # sky phase per product
+    fr = np.arange(F)
+    if cfg.drift:
+        # smooth bandpass drift with frequency, one phase per input
+        A = base[:, :1] * (1.0 + 0.2 * np.sin(2 * np.pi * 3.0 * fr[None, :] / F
+                                              + phase_in[:, None]))
+    else:
+        A = base
+    t = np.arange(T)
+    out = np.empty((freq_hi - freq_lo, P, T), dtype=np.complex64)
+    cross = ii != jj
+    for k, fi in enumerate(range(freq_lo, freq_hi)):
+        g = np.random.Generator(np.random.PCG64([cfg.seed, 1 + fi]))
+        Af = A[:, fi]
+        z = g.standard_normal(size=(P, T, 2))
+        # autos: power plus thermal scatter of variance A^2 / N_samp
+        auto_re = Af[ii][:, None] * (1.0 + z[..., 0] / np.sqrt(cfg.n_samp))
+        # crosses: sky term plus thermal scatter of variance A_i A_j / (2 N_samp)
+        amp = np.sqrt(Af[ii] * Af[jj])
+        ang = (2 * np.pi * t[None, :] * (jj - ii)[:, None] / (n * cfg.t_sky)
+               + phi[:, None])
+        sig = amp[:, None] / np.sqrt(2.0 * cfg.n_samp)
+        re = cfg.rho * amp[:, None] * np.cos(ang) + sig * z[..., 0]
+        im = cfg.rho * amp[:, None] * np.sin(ang) + sig * z[..., 1]
+        v = np.where(cross[:, None], re, auto_re)
+        w = np.where(cross[:, None], im, 0.0)
+        out[k].real = v
+        out[k].imag = w
+    return out
+
+
+def random_walk(n: int, dtype, seed: int = 0) -> np.ndarray:
+    """x_{t+1} = x_t +- 2^k with k ~ U{0..6} and a fair sign; integers wrap."""
+    dtype = np.dtype(dtype)
+    g = np.random.Generator(np.random.PCG64([seed, 7]))
+    k = g.integers(0, 7, size=n, dtype=np.int64)
+    s = g.integers(0, 2, size=n, dtype=np.int64) * 2 - 1
+    steps = s << k
+    if dtype.kind in "ui":
+        walk = np.cumsum(steps, dtype=np.int64)
+        if dtype.itemsize < 8:
+            walk = walk & ((1 << (8 * dtype.itemsize)) - 1)
+        return walk.astype(np.dtype(f"u{dtype.itemsize}")).view(dtype)
+    return np.cumsum(steps.astype(np.float64)).astype(dtype)

@@ -1,0 +1,46 @@
+"""The synthetic visibilities carry the thermal scatter of Sec. 3.1 (S2)."""
+import numpy as np
+
+from paper_1503_00638_gb300 import synth
+
+
+def test_cross_and_auto_scatter_match_radiometer(orc):
+    cfg = synth.VisConfig(2, 4, 8192, 2 ** 12, 0.01, seed=3, rho=0.0)
+    v = synth.visibilities(cfg)
+    n, N, T = cfg.n_inputs, cfg.n_samp, cfg.n_time
+    pii = [synth.auto_product_index(i, n) for i in range(n)]
+    p = 0
+    for i in range(n):
+        for j in range(i, n):
+            for fr in range(cfg.n_freq):
+                Ai, Aj = v[fr, pii[i]].real.mean(), v[fr, pii[j]].real.mean()
+                for a, comp in ((0, v[fr, p].real), (1, v[fr, p].imag)):
+                    model = orc.rad_simple_var(i, j, a, Ai, Aj, N)
+                    if model == 0:
+                        assert np.all(comp == 0)
+                        continue
+                    assert abs(comp.var() - model) < 5 * np.sqrt(2.0 / T) * model
+            p += 1
+
+
+def test_shapes_and_slices():
+    cfg = synth.CONFIG_SMALL
+    v = synth.visibilities(cfg)
+    assert v.shape == (16, 136, 64) and v.dtype == np.complex64 and v.nbytes == 1114112
+    assert np.array_equal(synth.visibilities(cfg, 5, 9), v[5:9])
+    n = cfg.n_inputs
+    for i in range(n):
+        p = synth.auto_product_index(i, n)
+        assert np.all(v[:, p].imag == 0) and np.all(v[:, p].real > 30)
+    assert synth.CONFIG_CHIME.nbytes == 1024 * 8256 * 16 * 8
+
+
+def test_random_walk_steps():
+    for dt in (np.uint8, np.uint16, np.int32, np.float64):
+        w = synth.random_walk(10000, dt, seed=1)
+        assert w.dtype == dt
+        d = np.diff(w.astype(np.int64) if dt != np.float64 else w)
+        if dt in (np.uint8, np.uint16):
+            d = (d + 2 ** (8 * w.itemsize - 1)) % 2 ** (8 * w.itemsize) - 2 ** (8 * w.itemsize - 1)
+        a = np.abs(d)
+        assert set(np.unique(a).astype(int).tolist()) <= {1, 2, 4, 8, 16, 32, 64}
