@@ -1,0 +1,163 @@
+/*
+ * bsgpu -- GB300 (sm_103a) implementation of the compression scheme of
+ * Masui et al., "A compression scheme for radio data in high performance
+ * computing" (arXiv:1503.00638): noise-relative precision reduction
+ * (Sec. 3), Bitshuffle (Sec. 4.2) and per-block LZ4 (Sec. 4.1, 4.2.1), and
+ * the inverse path.
+ *
+ * Conventions for every entry point below:
+ *  - Pointers named d_* / in / out / ws are DEVICE pointers owned by the
+ *    caller.  The library never allocates device or host memory: scratch
+ *    space ("workspace") is sized by bsgpu_workspace_size() and passed in.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*,
+ *    NULL = the legacy default stream).  Argument errors are detected on the
+ *    host and returned before anything is enqueued.
+ *  - Errors found on the device (a corrupt stream, a bounded wait that ran
+ *    out) are written to a status word at the start of the workspace; read it
+ *    with bsgpu_status() once the stream has reached that point.
+ *  - Input and output buffers must not overlap, and must start on a 16-byte
+ *    boundary (device allocations from cudaMalloc or PyTorch always do).
+ *  - No global mutable state: calls on different streams with different
+ *    workspaces may run concurrently (Sec. 2.2 asks for a thread-safe
+ *    library); two in-flight calls must not share one workspace.
+ */
+#ifndef BSGPU_H
+#define BSGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes (host return values and the device status word). */
+#define BSGPU_OK 0
+#define BSGPU_ERR_ARG (-1)      /* bad size, element size, block size or null pointer   */
+#define BSGPU_ERR_SPACE (-2)    /* output capacity or workspace too small               */
+#define BSGPU_ERR_CORRUPT (-3)  /* compressed stream fails validation                   */
+#define BSGPU_ERR_CUDA (-4)     /* a CUDA runtime call failed                           */
+#define BSGPU_ERR_TIMEOUT (-5)  /* a bounded device-side wait gave up                   */
+#define BSGPU_ERR_ALIGN (-6)    /* a buffer does not start on a 16-byte boundary        */
+
+/* Operations for bsgpu_workspace_size(). */
+#define BSGPU_OP_COMPRESS 1
+#define BSGPU_OP_DECOMPRESS 2
+#define BSGPU_OP_COMPRESS_VIS 3
+#define BSGPU_OP_REDUCE_PRECISION 4
+
+/* Library version string. */
+const char *bsgpu_version(void);
+
+/* Worst-case size in bytes of the framed stream that bsgpu_compress()
+ * produces for n_elem elements of elem_size bytes in blocks of block_elems
+ * elements (0 = the paper's default block of 4096 bytes, Sec. 4.2.1).
+ * Framing (a reading of the paper, which fixes none): 8-byte big-endian
+ * uncompressed byte count, 4-byte big-endian block size in bytes, then per
+ * block a 4-byte big-endian compressed length and the LZ4 block, then the
+ * (n_elem mod 8) trailing elements verbatim.  Returns 0 for bad arguments. */
+size_t bsgpu_compress_bound(size_t n_elem, size_t elem_size, size_t block_elems);
+
+/* Number of blocks the stream holds: full blocks of block_elems elements plus
+ * one shortened block of the remaining elements rounded down to a multiple
+ * of 8 (when that is not zero).  Size of the optional block-offset index. */
+size_t bsgpu_num_blocks(size_t n_elem, size_t elem_size, size_t block_elems);
+
+/* Device workspace bytes needed by bsgpu_compress (op = BSGPU_OP_COMPRESS)
+ * or bsgpu_decompress (BSGPU_OP_DECOMPRESS) for these arguments; 0 for bad
+ * arguments.  The workspace starts with the device status word. */
+size_t bsgpu_workspace_size(int op, size_t n_elem, size_t elem_size, size_t block_elems);
+
+/* Device workspace bytes needed by bsgpu_compress_vis (BSGPU_OP_COMPRESS_VIS)
+ * or bsgpu_reduce_precision_c64 (BSGPU_OP_REDUCE_PRECISION) for a cube of
+ * n_freq x n_inputs (n_inputs + 1) / 2 x n_time complex64 samples; it holds
+ * the table of autocorrelations and of product indices.  block_elems as for
+ * bsgpu_compress (ignored by BSGPU_OP_REDUCE_PRECISION).  0 for bad arguments. */
+size_t bsgpu_vis_workspace_size(int op, int64_t n_freq, int64_t n_inputs, int64_t n_time,
+                                size_t block_elems);
+
+/* Read the device status word of a workspace: waits for `stream`, then
+ * copies the word to *status (BSGPU_OK or a negative BSGPU_ERR_*).  Returns
+ * BSGPU_OK, or BSGPU_ERR_CUDA if the copy itself failed. */
+int bsgpu_status(const void *ws, void *stream, int *status);
+
+/* Sec. 3 (Eq. rad_simple, Eq. noise, Eq. trunc_error) and Sec. 6 steps 1-3:
+ * noise-relative precision reduction of a visibility cube.
+ *   in, out : [n_freq][n_prod][n_time] complex64 (interleaved float32 re, im),
+ *             time fastest; n_prod = n_inputs (n_inputs + 1) / 2 products in
+ *             upper-triangle row-major order (0,0),(0,1)..(0,n-1),(1,1),...
+ *   N       : samples per integration (Eq. rad_simple), > 0
+ *   f       : maximum fractional increase of the noise variance, >= 0
+ *             (f = 0 leaves the data unchanged)
+ * Each real and imaginary part x of V_ij is rounded to the nearest multiple
+ * of g = 2^k, ties to even, where g is the largest power of two with
+ * g^2 < q = 12 f s^2; s^2 = V_ii V_jj / (2N) for i != j and V_ii^2 / N for
+ * the real part of an autocorrelation, whose imaginary part is left alone.
+ * q is evaluated in float32 as (fl(6f/N) * A_i) * A_j (autos:
+ * (2 fl(6f/N) * A_i) * A_i) from the UNROUNDED autos A_i = Re V_ii; no
+ * rounding where q is not a positive normal float.  Out of place only.
+ * ws: bsgpu_vis_workspace_size(BSGPU_OP_REDUCE_PRECISION, ...) bytes. */
+int bsgpu_reduce_precision_c64(const void *in, void *out, int64_t n_freq, int64_t n_inputs,
+                               int64_t n_time, double N, double f, void *ws, size_t ws_bytes,
+                               void *stream);
+
+/* Sec. 4.2 and Sec. 6 step 4: Bitshuffle.  Within each block of block_elems
+ * elements (a multiple of 8; 0 = 4096 bytes), bit r of element e (r = 8 *
+ * byte + bit of the little-endian element, bit 0 = least significant) moves
+ * to byte r * (block_elems / 8) + e / 8, bit e % 8.  A trailing partial block
+ * is shortened to a multiple of 8 elements and transposed the same way; the
+ * last (n_elem mod 8) elements are copied unchanged.  elem_size is 1, 2, 4
+ * or 8.  in and out hold n_elem * elem_size bytes. */
+int bsgpu_bitshuffle(const void *in, void *out, size_t n_elem, size_t elem_size,
+                     size_t block_elems, void *stream);
+
+/* Inverse of bsgpu_bitshuffle with the same arguments. */
+int bsgpu_bitunshuffle(const void *in, void *out, size_t n_elem, size_t elem_size,
+                       size_t block_elems, void *stream);
+
+/* Sec. 4.2.1 and Sec. 6 steps 4-5: Bitshuffle each block and compress it
+ * with LZ4 while it is on chip, writing the framed stream described at
+ * bsgpu_compress_bound().
+ *   in              : n_elem * elem_size bytes
+ *   out, out_cap    : at least bsgpu_compress_bound() bytes
+ *   d_out_bytes     : device uint64, receives the stream length
+ *   d_block_offsets : NULL, or bsgpu_num_blocks() device uint64s that
+ *                     receive the byte offset of each block's length field
+ *                     (lets bsgpu_decompress() start every block at once)
+ * Block sizes up to 65536 bytes (LZ4 offsets are 16-bit).  The LZ4 encoding
+ * is deterministic but is not byte-identical to other encoders' (LZ4 output
+ * is not unique); any conforming LZ4 block decoder reads it. */
+int bsgpu_compress(const void *in, size_t n_elem, size_t elem_size, size_t block_elems,
+                   void *out, size_t out_cap, uint64_t *d_out_bytes, uint64_t *d_block_offsets,
+                   void *ws, size_t ws_bytes, void *stream);
+
+/* Inverse of bsgpu_compress: decode in_bytes of framed stream into n_elem
+ * elements.  d_block_offsets is the index written by bsgpu_compress (or
+ * NULL: the block chain is then walked on the device by one thread first,
+ * which is slow for large streams).  A stream whose header does not match
+ * (n_elem, elem_size, block_elems), or that fails LZ4 validation (offset 0
+ * or before the block start, a length running past either buffer, a block
+ * that does not decode to exactly its size), sets BSGPU_ERR_CORRUPT in the
+ * status word; the output is then unspecified but nothing outside the given
+ * buffers is touched. */
+int bsgpu_decompress(const void *in, size_t in_bytes, void *out, size_t n_elem, size_t elem_size,
+                     size_t block_elems, const uint64_t *d_block_offsets, void *ws,
+                     size_t ws_bytes, void *stream);
+
+/* Sec. 6 steps 1-5 fused: precision reduction of a visibility cube (as in
+ * bsgpu_reduce_precision_c64) followed by Bitshuffle + LZ4 of the rounded
+ * float32 values (elem_size 4), in one pass over the input.  The stream is
+ * the one bsgpu_compress() would write for the rounded cube viewed as
+ * 2 * n_freq * n_prod * n_time float32 elements; decode it with
+ * bsgpu_decompress(elem_size = 4).
+ * ws: bsgpu_vis_workspace_size(BSGPU_OP_COMPRESS_VIS, ...) bytes. */
+int bsgpu_compress_vis(const void *vis, int64_t n_freq, int64_t n_inputs, int64_t n_time,
+                       double N, double f, size_t block_elems, void *out, size_t out_cap,
+                       uint64_t *d_out_bytes, uint64_t *d_block_offsets, void *ws,
+                       size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSGPU_H */

@@ -1,0 +1,234 @@
+"""Thin Python binding of libbsgpu (include/bsgpu.h): argument marshalling only.
+
+Every function here passes device pointers of PyTorch CUDA tensors, the
+current CUDA stream and sizes to the C entry point of the same name (without
+the ``bsgpu_`` prefix) and raises :class:`BsgpuError` on a nonzero status.
+All computation happens in the CUDA kernels of libbsgpu; there is no CPU
+fallback: importing this module fails if the library has not been built.
+PyTorch provides device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libbsgpu.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                      "`python -m paper_1503_00638_gb300.build` (needs nvcc)")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+OK, ERR_ARG, ERR_SPACE, ERR_CORRUPT, ERR_CUDA, ERR_TIMEOUT, ERR_ALIGN = 0, -1, -2, -3, -4, -5, -6
+OP_COMPRESS, OP_DECOMPRESS, OP_COMPRESS_VIS, OP_REDUCE_PRECISION = 1, 2, 3, 4
+_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_SPACE", -3: "ERR_CORRUPT", -4: "ERR_CUDA",
+          -5: "ERR_TIMEOUT", -6: "ERR_ALIGN"}
+
+_sz, _vp, _i, _i64, _d = ctypes.c_size_t, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+_SIGS = {
+    "bsgpu_version": ([], ctypes.c_char_p),
+    "bsgpu_compress_bound": ([_sz, _sz, _sz], _sz),
+    "bsgpu_num_blocks": ([_sz, _sz, _sz], _sz),
+    "bsgpu_workspace_size": ([_i, _sz, _sz, _sz], _sz),
+    "bsgpu_vis_workspace_size": ([_i, _i64, _i64, _i64, _sz], _sz),
+    "bsgpu_status": ([_vp, _vp, ctypes.POINTER(_i)], _i),
+    "bsgpu_reduce_precision_c64": ([_vp, _vp, _i64, _i64, _i64, _d, _d, _vp, _sz, _vp], _i),
+    "bsgpu_bitshuffle": ([_vp, _vp, _sz, _sz, _sz, _vp], _i),
+    "bsgpu_bitunshuffle": ([_vp, _vp, _sz, _sz, _sz, _vp], _i),
+    "bsgpu_compress": ([_vp, _sz, _sz, _sz, _vp, _sz, _vp, _vp, _vp, _sz, _vp], _i),
+    "bsgpu_decompress": ([_vp, _sz, _vp, _sz, _sz, _sz, _vp, _vp, _sz, _vp], _i),
+    "bsgpu_compress_vis": ([_vp, _i64, _i64, _i64, _d, _d, _sz, _vp, _sz, _vp, _vp, _vp, _sz,
+                            _vp], _i),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class BsgpuError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {_NAMES.get(code, code)} ({code})")
+        self.code = code
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise BsgpuError(code, where)
+
+
+def _stream(stream) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _bytes_view(t: torch.Tensor) -> torch.Tensor:
+    return t.reshape(-1).view(torch.uint8)
+
+
+# -- queries -----------------------------------------------------------------
+
+def version() -> str:
+    return _lib.bsgpu_version().decode()
+
+
+def compress_bound(n_elem: int, elem_size: int, block_elems: int = 0) -> int:
+    return _lib.bsgpu_compress_bound(n_elem, elem_size, block_elems)
+
+
+def num_blocks(n_elem: int, elem_size: int, block_elems: int = 0) -> int:
+    return _lib.bsgpu_num_blocks(n_elem, elem_size, block_elems)
+
+
+def workspace_size(op: int, n_elem: int, elem_size: int, block_elems: int = 0) -> int:
+    return _lib.bsgpu_workspace_size(op, n_elem, elem_size, block_elems)
+
+
+def vis_workspace_size(op: int, n_freq: int, n_inputs: int, n_time: int,
+                       block_elems: int = 0) -> int:
+    return _lib.bsgpu_vis_workspace_size(op, n_freq, n_inputs, n_time, block_elems)
+
+
+def status(ws: torch.Tensor, stream=None) -> int:
+    """Device status word of a workspace (waits for the stream)."""
+    st = ctypes.c_int(0)
+    _check(_lib.bsgpu_status(_ptr(ws), _stream(stream), ctypes.byref(st)), "bsgpu_status")
+    return st.value
+
+
+def new_workspace(nbytes: int, device=None) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8,
+                       device=device or torch.cuda.current_device())
+
+
+# -- Sec. 3: precision reduction ---------------------------------------------
+
+def reduce_precision_c64(vis: torch.Tensor, N: float, f: float, out: torch.Tensor | None = None,
+                         ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Round a [n_freq][n_prod][n_time] complex64 cube (returns out)."""
+    F, P, T = vis.shape
+    n = _n_inputs(P)
+    out = torch.empty_like(vis) if out is None else out
+    need = vis_workspace_size(OP_REDUCE_PRECISION, F, n, T)
+    ws = new_workspace(need, vis.device) if ws is None else ws
+    _check(_lib.bsgpu_reduce_precision_c64(_ptr(vis), _ptr(out), F, n, T, float(N), float(f),
+                                           _ptr(ws), ws.numel(), _stream(stream)),
+           "bsgpu_reduce_precision_c64")
+    return out
+
+
+def _n_inputs(P: int) -> int:
+    n = int(round(((8 * P + 1) ** 0.5 - 1) / 2))
+    if n * (n + 1) // 2 != P:
+        raise ValueError(f"{P} products is not n(n+1)/2")
+    return n
+
+
+# -- Sec. 4.2: Bitshuffle ----------------------------------------------------
+
+def bitshuffle(x: torch.Tensor, block_elems: int = 0, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    out = torch.empty_like(x) if out is None else out
+    _check(_lib.bsgpu_bitshuffle(_ptr(x), _ptr(out), x.numel(), x.element_size(), block_elems,
+                                 _stream(stream)), "bsgpu_bitshuffle")
+    return out
+
+
+def bitunshuffle(x: torch.Tensor, block_elems: int = 0, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    out = torch.empty_like(x) if out is None else out
+    _check(_lib.bsgpu_bitunshuffle(_ptr(x), _ptr(out), x.numel(), x.element_size(), block_elems,
+                                   _stream(stream)), "bsgpu_bitunshuffle")
+    return out
+
+
+# -- Sec. 4.1 / 4.2.1: compress / decompress ----------------------------------
+
+class Compressed:
+    """A compressed stream on the device: `buf[:nbytes]` is the framed stream,
+    `offsets` the per-block index (or None); `nbytes` is read lazily."""
+
+    def __init__(self, buf, nbytes_dev, offsets, n_elem, elem_size, block_elems, ws):
+        self.buf, self.nbytes_dev, self.offsets = buf, nbytes_dev, offsets
+        self.n_elem, self.elem_size, self.block_elems, self.ws = n_elem, elem_size, block_elems, ws
+
+    @property
+    def nbytes(self) -> int:
+        return int(self.nbytes_dev.item())
+
+    def stream_bytes(self) -> torch.Tensor:
+        return self.buf[: self.nbytes]
+
+
+def compress(x: torch.Tensor, block_elems: int = 0, elem_size: int | None = None,
+             out: torch.Tensor | None = None, with_offsets: bool = True,
+             ws: torch.Tensor | None = None, stream=None) -> Compressed:
+    es = elem_size or x.element_size()
+    n = x.numel() * x.element_size() // es
+    cap = compress_bound(n, es, block_elems)
+    if cap == 0:
+        raise BsgpuError(ERR_ARG, "bsgpu_compress_bound")
+    out = torch.empty(cap, dtype=torch.uint8, device=x.device) if out is None else out
+    nb_dev = torch.zeros(1, dtype=torch.int64, device=x.device)
+    nblk = num_blocks(n, es, block_elems)
+    offs = torch.empty(max(nblk, 1), dtype=torch.int64, device=x.device) if with_offsets else None
+    need = workspace_size(OP_COMPRESS, n, es, block_elems)
+    ws = new_workspace(need, x.device) if ws is None else ws
+    _check(_lib.bsgpu_compress(_ptr(x), n, es, block_elems, _ptr(out), out.numel(), _ptr(nb_dev),
+                               _ptr(offs), _ptr(ws), ws.numel(), _stream(stream)),
+           "bsgpu_compress")
+    return Compressed(out, nb_dev, offs, n, es, block_elems, ws)
+
+
+def compress_vis(vis: torch.Tensor, N: float, f: float, block_elems: int = 0,
+                 out: torch.Tensor | None = None, with_offsets: bool = True,
+                 ws: torch.Tensor | None = None, stream=None) -> Compressed:
+    """Precision reduction + Bitshuffle + LZ4 of a complex64 cube (Sec. 6)."""
+    F, P, T = vis.shape
+    n_in = _n_inputs(P)
+    n = 2 * F * P * T
+    cap = compress_bound(n, 4, block_elems)
+    if cap == 0:
+        raise BsgpuError(ERR_ARG, "bsgpu_compress_bound")
+    out = torch.empty(cap, dtype=torch.uint8, device=vis.device) if out is None else out
+    nb_dev = torch.zeros(1, dtype=torch.int64, device=vis.device)
+    nblk = num_blocks(n, 4, block_elems)
+    offs = torch.empty(max(nblk, 1), dtype=torch.int64, device=vis.device) if with_offsets else None
+    need = vis_workspace_size(OP_COMPRESS_VIS, F, n_in, T, block_elems)
+    ws = new_workspace(need, vis.device) if ws is None else ws
+    _check(_lib.bsgpu_compress_vis(_ptr(vis), F, n_in, T, float(N), float(f), block_elems,
+                                   _ptr(out), out.numel(), _ptr(nb_dev), _ptr(offs), _ptr(ws),
+                                   ws.numel(), _stream(stream)), "bsgpu_compress_vis")
+    return Compressed(out, nb_dev, offs, n, 4, block_elems, ws)
+
+
+def decompress(stream_buf: torch.Tensor, in_bytes: int, n_elem: int, elem_size: int,
+               block_elems: int = 0, offsets: torch.Tensor | None = None,
+               out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """Decode a framed stream into a uint8 tensor of n_elem * elem_size bytes."""
+    dev = stream_buf.device
+    out = torch.empty(n_elem * elem_size, dtype=torch.uint8, device=dev) if out is None else out
+    need = workspace_size(OP_DECOMPRESS, n_elem, elem_size, block_elems)
+    if need == 0:
+        raise BsgpuError(ERR_ARG, "bsgpu_workspace_size")
+    ws = new_workspace(need, dev) if ws is None else ws
+    _check(_lib.bsgpu_decompress(_ptr(stream_buf), in_bytes, _ptr(out), n_elem, elem_size,
+                                 block_elems, _ptr(offsets), _ptr(ws), ws.numel(),
+                                 _stream(stream)), "bsgpu_decompress")
+    return out

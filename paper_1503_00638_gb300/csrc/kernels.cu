@@ -1,0 +1,781 @@
+// bsgpu kernels for sm_103a: precision reduction (Sec. 3.2), Bitshuffle
+// (Sec. 4.2) and per-block LZ4 with framing (Sec. 4.1, 4.2.1), and the
+// inverse path.  One warp per CTA; each warp owns one block (the unit the
+// paper threads over, Sec. 4.2.1) at a time, staged in shared memory by the
+// bulk-copy (TMA) engine with the next block prefetched.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "lz4_warp.cuh"
+#include "shuffle.cuh"
+
+namespace bsg {
+
+// ---------------------------------------------------------------------------
+// Shared-memory plans
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr uint32_t r16(uint32_t x) { return (x + 15u) & ~15u; }
+__host__ __device__ constexpr uint32_t r128(uint32_t x) { return (x + 127u) & ~127u; }
+__host__ __device__ constexpr uint32_t cmax(uint32_t a, uint32_t b) { return a > b ? a : b; }
+__host__ __device__ constexpr uint32_t lz4b(uint32_t n) { return n + n / 255u + 16u; }
+
+template <uint32_t MAXB>
+struct CompPlan {
+    // LZ4 output with its 4-byte length field in front, plus read slack
+    static constexpr uint32_t CAP = r16(4 + lz4b(MAXB) + 48);
+    static constexpr uint32_t BUF = r128(cmax(CAP, MAXB + 32));
+    static constexpr uint32_t TMP = r128(MAXB + 32);
+    static constexpr int HBITS = MAXB <= 8192 ? 10 : (MAXB <= 16384 ? 11 : 12);
+    static constexpr uint32_t HASH = 4u << HBITS;
+    static constexpr uint32_t BYTES = 2 * BUF + TMP + HASH + 16;
+};
+
+template <uint32_t MAXB>
+struct DecPlan {
+    static constexpr uint32_t CAPD = r16(16 + 4 + lz4b(MAXB) + 48);
+    static constexpr uint32_t BUF = r128(cmax(CAPD, MAXB + 32));
+    static constexpr uint32_t DEC = r128(MAXB + 32);
+    static constexpr uint32_t BYTES = 2 * BUF + DEC + 16;
+};
+
+template <uint32_t MAXB>
+struct ShufPlan {
+    static constexpr uint32_t BUF = r128(MAXB + 32);
+    static constexpr uint32_t BYTES = 3 * BUF + 16;
+};
+
+uint32_t compress_smem_bytes(uint32_t maxb)
+{
+    return maxb <= 8192 ? CompPlan<8192>::BYTES
+                        : (maxb <= 16384 ? CompPlan<16384>::BYTES : CompPlan<65536>::BYTES);
+}
+uint32_t decompress_smem_bytes(uint32_t maxb)
+{
+    return maxb <= 8192 ? DecPlan<8192>::BYTES
+                        : (maxb <= 16384 ? DecPlan<16384>::BYTES : DecPlan<65536>::BYTES);
+}
+uint32_t shuffle_smem_bytes(uint32_t maxb)
+{
+    return maxb <= 8192 ? ShufPlan<8192>::BYTES
+                        : (maxb <= 16384 ? ShufPlan<16384>::BYTES : ShufPlan<65536>::BYTES);
+}
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+BSG_D uint32_t grab_tile(uint32_t *counter, uint32_t lane)
+{
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1u);
+    return __shfl_sync(FULL, t, 0);
+}
+
+BSG_D uint32_t block_elems_of(const CodecArgs &a, uint32_t tile)
+{
+    return tile + 1 == a.nb ? a.last_B : a.B;
+}
+
+// Start moving `bytes` from global `src` to shared `dst`: one bulk copy when
+// both ends are 16-byte aligned (returns true: wait on `bar`), otherwise a
+// plain warp copy (returns false: done).
+BSG_D bool load_block(uint8_t *dst, const uint8_t *src, uint32_t bytes, uint64_t *bar,
+                      uint32_t lane)
+{
+    if ((bytes & 15u) == 0 && ((uintptr_t)src & 15u) == 0 && bytes > 0) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_g2s(dst, src, bytes, bar);
+        }
+        return true;
+    }
+    for (uint32_t k = lane; k < bytes; k += 32) dst[k] = src[k];
+    __syncwarp();
+    return false;
+}
+
+// Copy len bytes from 16-byte aligned shared `s` to global `g` (any alignment):
+// byte stores up to g's next 16-byte boundary, then 16-byte stores assembled
+// from two aligned shared vectors and a funnel shift, then the ragged end.
+// Reads up to 32 bytes past s + len.
+BSG_D void copy_out(const uint8_t *s, uint8_t *g, uint32_t len, uint32_t lane)
+{
+    uint32_t head = (uint32_t)((16u - ((uintptr_t)g & 15u)) & 15u);
+    if (head > len) head = len;
+    if (lane < head) g[lane] = s[lane];
+    const uint32_t nchunk = (len - head) / 16u;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(s);
+    const uint32_t q = (head >> 2) & 3u, sh = (head & 3u) * 8u;
+    for (uint32_t c = lane; c < nchunk; c += 32) {
+        uint32_t so = head + 16u * c;
+        uint4 A = s4[so >> 4], B = s4[(so >> 4) + 1];
+        uint4 v;
+        switch (q) {  // uniform across the warp
+        case 0:
+            v = make_uint4(funnel_r(A.x, A.y, sh), funnel_r(A.y, A.z, sh), funnel_r(A.z, A.w, sh),
+                           funnel_r(A.w, B.x, sh));
+            break;
+        case 1:
+            v = make_uint4(funnel_r(A.y, A.z, sh), funnel_r(A.z, A.w, sh), funnel_r(A.w, B.x, sh),
+                           funnel_r(B.x, B.y, sh));
+            break;
+        case 2:
+            v = make_uint4(funnel_r(A.z, A.w, sh), funnel_r(A.w, B.x, sh), funnel_r(B.x, B.y, sh),
+                           funnel_r(B.y, B.z, sh));
+            break;
+        default:
+            v = make_uint4(funnel_r(A.w, B.x, sh), funnel_r(B.x, B.y, sh), funnel_r(B.y, B.z, sh),
+                           funnel_r(B.z, B.w, sh));
+            break;
+        }
+        *reinterpret_cast<uint4 *>(g + so) = v;
+    }
+    for (uint32_t k = head + 16u * nchunk + lane; k < len; k += 32) g[k] = s[k];
+}
+
+BSG_D void put_be32(uint8_t *p, uint32_t v)
+{
+    p[0] = (uint8_t)(v >> 24);
+    p[1] = (uint8_t)(v >> 16);
+    p[2] = (uint8_t)(v >> 8);
+    p[3] = (uint8_t)v;
+}
+
+BSG_D uint32_t get_be32(const uint8_t *p)
+{
+    return ((uint32_t)p[0] << 24) | ((uint32_t)p[1] << 16) | ((uint32_t)p[2] << 8) | p[3];
+}
+
+// 12-byte chunk header: big-endian total bytes, big-endian block bytes
+BSG_D void write_chunk_header(uint8_t *out, uint64_t total, uint32_t block_bytes, uint32_t lane)
+{
+    if (lane < 8) out[lane] = (uint8_t)(total >> (8 * (7 - lane)));
+    else if (lane < 12) out[lane] = (uint8_t)(block_bytes >> (8 * (11 - lane)));
+}
+
+// ---------------------------------------------------------------------------
+// Precision reduction of complex samples (Sec. 3.2, Sec. 6 steps 1-3)
+// ---------------------------------------------------------------------------
+// Round one complex sample (re, im) of product p = (i, j) at (f, t).
+BSG_D float2 reduce_sample(float2 v, uint32_t ij, uint32_t f, uint32_t t, const VisParams &P)
+{
+    const uint32_t i = ij & 0xffffu, j = ij >> 16;
+    const uint32_t row = f * P.n_in;
+    const float Ai = __ldg(P.autos + (size_t)(row + i) * P.T + t);
+    if (i == j) {
+        // s^2 = V_ii^2 / N: q = (2 c A_i) A_i; Im V_ii has no noise and stays
+        const float q = __fmul_rn(__fmul_rn(P.c2, Ai), Ai);
+        v.x = reduce_one(v.x, q);
+    } else {
+        // s^2 = V_ii V_jj / (2N): q = (c A_i) A_j for both components
+        const float Aj = __ldg(P.autos + (size_t)(row + j) * P.T + t);
+        const float q = __fmul_rn(__fmul_rn(P.c, Ai), Aj);
+        v.x = reduce_one(v.x, q);
+        v.y = reduce_one(v.y, q);
+    }
+    return v;
+}
+
+// Round `ncplx` consecutive complex samples starting at global complex index
+// c0, lane k taking samples c0 + k, c0 + k + 32, ...  src and dst may be the
+// same (in-place) and may be shared or global memory.
+BSG_D void reduce_run(const float2 *src, float2 *dst, uint32_t c0, uint32_t ncplx,
+                      const VisParams &P, uint32_t lane)
+{
+    uint32_t c = c0 + lane;
+    uint32_t fp = c / P.T;
+    uint32_t t = c - fp * P.T;
+    uint32_t f = fp / P.P;
+    uint32_t p = fp - f * P.P;
+    for (uint32_t k = lane; k < ncplx; k += 32) {
+        const uint32_t ij = __ldg(P.pairs + p);
+        dst[k] = reduce_sample(src[k], ij, f, t, P);
+        t += P.rT;
+        p += P.qT;
+        if (t >= P.T) {
+            t -= P.T;
+            p++;
+        }
+        while (p >= P.P) {
+            p -= P.P;
+            f++;
+        }
+    }
+}
+
+// Round the float at global float index fi (used for the verbatim tail).
+BSG_D float reduce_float_at(float x, uint64_t fi, const VisParams &P)
+{
+    uint32_t c = (uint32_t)(fi >> 1);
+    uint32_t fp = c / P.T, t = c - fp * P.T;
+    uint32_t f = fp / P.P, p = fp - f * P.P;
+    float2 v = (fi & 1) ? make_float2(0.f, x) : make_float2(x, 0.f);
+    uint32_t ij = __ldg(P.pairs + p);
+    uint32_t i = ij & 0xffffu, j = ij >> 16;
+    // the imaginary part of an auto is never rounded; everything else as usual
+    float2 r = reduce_sample(v, ij, f, t, P);
+    if ((fi & 1) && i == j) return x;
+    return (fi & 1) ? r.y : r.x;
+}
+
+// Tables for the rounding: autos[f][i][t] = Re V(f, (i,i), t) and
+// pairs[p] = i | j << 16 for the upper-triangle product order.
+__global__ void vis_tables_kernel(const float *__restrict__ vis, float *__restrict__ autos,
+                                  uint32_t *__restrict__ pairs, uint32_t n_freq, uint32_t n_in,
+                                  uint32_t T)
+{
+    const uint32_t P = n_in * (n_in + 1) / 2;
+    const uint64_t n_auto = (uint64_t)n_freq * n_in * T;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_auto; x += stride) {
+        uint32_t t = (uint32_t)(x % T);
+        uint64_t fi = x / T;
+        uint32_t i = (uint32_t)(fi % n_in);
+        uint64_t f = fi / n_in;
+        uint64_t pii = (uint64_t)i * n_in - (uint64_t)i * (i - 1) / 2;
+        autos[x] = vis[((f * P + pii) * T + t) * 2];
+    }
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+        // row i holds products [i n - i (i-1)/2, (i+1) n - (i+1) i / 2)
+        uint32_t lo = 0, hi = n_in - 1;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi + 1) / 2;
+            uint64_t start = (uint64_t)mid * n_in - (uint64_t)mid * (mid - 1) / 2;
+            if (start <= p) lo = mid; else hi = mid - 1;
+        }
+        uint64_t start = (uint64_t)lo * n_in - (uint64_t)lo * (lo - 1) / 2;
+        uint32_t j = lo + (uint32_t)(p - start);
+        pairs[p] = lo | (j << 16);
+    }
+}
+
+// Standalone precision reduction: each warp rounds runs of 1024 samples.
+__global__ void __launch_bounds__(256) reduce_precision_kernel(const float2 *__restrict__ in,
+                                                               float2 *__restrict__ out,
+                                                               uint64_t n_cplx, VisParams P)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr uint32_t RUN = 1024;
+    for (uint64_t r = warp * RUN; r < n_cplx; r += nwarps * RUN) {
+        uint32_t cnt = (uint32_t)(n_cplx - r < RUN ? n_cplx - r : RUN);
+        reduce_run(in + r, out + r, (uint32_t)r, cnt, P, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Decoupled look-back over per-block compressed sizes (single-pass output
+// placement).  state[t]: 0 = not ready, (1 << 62) | aggregate, (2 << 62) |
+// inclusive prefix.  Tiles are taken in order from a counter, so every
+// predecessor is held by a running warp; waits are bounded all the same.
+// ---------------------------------------------------------------------------
+BSG_D uint64_t lookback(uint64_t *state, uint32_t tile, uint64_t agg, int *status,
+                        uint32_t lane)
+{
+    constexpr uint64_t FA = 1ull << 62, FP = 2ull << 62, VM = (1ull << 62) - 1;
+    if (tile == 0) {
+        if (lane == 0) st_relaxed_u64(state, FP | agg);
+        return 0;
+    }
+    if (lane == 0) st_relaxed_u64(state + tile, FA | agg);
+    uint64_t excl = 0;
+    int64_t base = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    for (;;) {
+        int64_t idx = base - (int64_t)lane;
+        uint64_t v = idx >= 0 ? ld_relaxed_u64(state + idx) : FP;
+        uint32_t flag = (uint32_t)(v >> 62);
+        uint32_t pm = __ballot_sync(FULL, flag == 2);
+        uint32_t im = __ballot_sync(FULL, flag == 0);
+        uint32_t first = pm ? (uint32_t)(__ffs(pm) - 1) : 31u;
+        uint32_t need = first >= 31 ? FULL : ((2u << first) - 1u);
+        if (im & need) {
+            if (++spins > (1u << 21)) {
+                if (lane == 0) set_status(status, BSGPU_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(40);
+            continue;
+        }
+        uint64_t x = lane <= first ? (v & VM) : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+        excl += x;
+        if (pm) break;
+        base -= 32;
+    }
+    if (lane == 0) st_relaxed_u64(state + tile, FP | (excl + agg));
+    return excl;
+}
+
+// ---------------------------------------------------------------------------
+// Compress: [round ->] bitshuffle -> LZ4 -> placed by look-back
+// ---------------------------------------------------------------------------
+template <uint32_t MAXB>
+BSG_D void compress_tile(const CodecArgs &a, uint32_t tile, uint8_t *buf, uint8_t *tmp,
+                         uint32_t *table, uint32_t lane)
+{
+    using L = CompPlan<MAXB>;
+    const uint32_t Bb = block_elems_of(a, tile);
+    const uint32_t S = Bb * a.es;
+    if (a.vis.enabled) {
+        // float index tile * B is even: whole complex samples
+        float2 *b2 = reinterpret_cast<float2 *>(buf);
+        reduce_run(b2, b2, (uint32_t)(((uint64_t)tile * a.B) >> 1), Bb / 2, a.vis, lane);
+        __syncwarp();
+    }
+    shuffle_block(buf, tmp, Bb, a.es, lane);
+    __syncwarp();
+    uint32_t cs = lz4_encode_warp<L::HBITS>(tmp, S, buf + 4, table);
+    if (cs == 0xffffffffu) {  // progress guard (not reachable for valid sizes)
+        if (lane == 0) set_status(a.status, BSGPU_ERR_CUDA);
+        cs = 0;
+    }
+    if (lane == 0) put_be32(buf, cs);
+    __syncwarp();
+    const uint64_t excl = lookback(a.tile_state, tile, 4ull + cs, a.status, lane);
+    const uint64_t D = 12 + excl;
+    if (D + 4 + cs > a.out_cap) {
+        if (lane == 0) set_status(a.status, BSGPU_ERR_SPACE);
+        return;
+    }
+    copy_out(buf, a.out + D, 4 + cs, lane);
+    if (a.block_offsets && lane == 0) a.block_offsets[tile] = D;
+    if (tile == 0) write_chunk_header(a.out, a.n_elem * a.es, a.B * a.es, lane);
+    if (tile + 1 == a.nb) {
+        // the (n mod 8) trailing elements follow the last block verbatim
+        const uint64_t end = D + 4 + cs;
+        const uint64_t first = a.n_elem - a.tail_elems;
+        const uint32_t tb = a.tail_elems * a.es;
+        if (end + tb > a.out_cap) {
+            if (lane == 0) set_status(a.status, BSGPU_ERR_SPACE);
+            return;
+        }
+        if (a.vis.enabled) {
+            if (lane < a.tail_elems) {
+                const float *src = reinterpret_cast<const float *>(a.in);
+                float x = reduce_float_at(src[first + lane], first + lane, a.vis);
+                uint32_t u = __float_as_uint(x);
+                for (int k = 0; k < 4; k++) a.out[end + 4 * lane + k] = (uint8_t)(u >> (8 * k));
+            }
+        } else {
+            for (uint32_t k = lane; k < tb; k += 32) a.out[end + k] = a.in[first * a.es + k];
+        }
+        if (lane == 0) *a.out_bytes = end + tb;
+    }
+}
+
+template <uint32_t MAXB>
+__global__ void __launch_bounds__(32) compress_kernel(const __grid_constant__ CodecArgs a)
+{
+    using L = CompPlan<MAXB>;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *buf[2] = {sm, sm + L::BUF};
+    uint8_t *tmp = sm + 2 * L::BUF;
+    uint32_t *table = reinterpret_cast<uint32_t *>(tmp + L::TMP);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(table) + L::HASH);
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t parity = 0, pend = 0;  // bit c: phase / load in flight of buffer c
+    uint32_t tile = grab_tile(a.tile_counter, lane);
+    if (tile < a.nb && load_block(buf[0], a.in + (uint64_t)tile * a.B * a.es,
+                                  block_elems_of(a, tile) * a.es, &bar[0], lane))
+        pend |= 1u;
+    uint32_t cur = 0;
+    while (tile < a.nb) {
+        const uint32_t nxt = grab_tile(a.tile_counter, lane);
+        if (pend & (1u << cur)) {
+            if (!mbar_wait_bounded(&bar[cur], (parity >> cur) & 1u) && lane == 0)
+                set_status(a.status, BSGPU_ERR_TIMEOUT);
+            parity ^= 1u << cur;
+            pend &= ~(1u << cur);
+        }
+        if (nxt < a.nb) {
+            // the other buffer's last reads (generic proxy) precede the async write
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (load_block(buf[cur ^ 1], a.in + (uint64_t)nxt * a.B * a.es,
+                           block_elems_of(a, nxt) * a.es, &bar[cur ^ 1], lane))
+                pend |= 1u << (cur ^ 1);
+        }
+        compress_tile<MAXB>(a, tile, buf[cur], tmp, table, lane);
+        __syncwarp();
+        tile = nxt;
+        cur ^= 1;
+    }
+}
+
+// n_elem < 8: no block; header plus the elements verbatim (rounded for a cube).
+__global__ void compress_small_kernel(const __grid_constant__ CodecArgs a)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    write_chunk_header(a.out, a.n_elem * a.es, a.B * a.es, lane);
+    const uint32_t tb = a.tail_elems * a.es;
+    if (a.vis.enabled) {
+        if (lane < a.tail_elems) {
+            const float *src = reinterpret_cast<const float *>(a.in);
+            uint32_t u = __float_as_uint(reduce_float_at(src[lane], lane, a.vis));
+            for (int k = 0; k < 4; k++) a.out[12 + 4 * lane + k] = (uint8_t)(u >> (8 * k));
+        }
+    } else {
+        for (uint32_t k = lane; k < tb; k += 32) a.out[12 + k] = a.in[k];
+    }
+    if (lane == 0) *a.out_bytes = 12 + tb;
+}
+
+// ---------------------------------------------------------------------------
+// Decompress: LZ4 decode -> bit un-transpose, every block at once
+// ---------------------------------------------------------------------------
+struct DecLoad {
+    bool bulk;       // a bulk copy is in flight on the barrier
+    bool ok;         // offsets passed the range checks
+    uint32_t delta;  // shared index of the first stream byte (D & 15)
+    uint32_t clen;   // LZ4 bytes of the block
+    uint32_t eidx;   // shared index this lane's edge byte goes to (or ~0)
+    uint8_t ebyte;
+};
+
+// Bytes [D, Dn) of the stream go to shared index x - (D & ~15): the 16-byte
+// aligned middle by one bulk copy, the ragged head and tail (< 16 bytes each)
+// by plain loads held in registers until the block is processed.
+BSG_D DecLoad dec_issue(const CodecArgs &a, uint32_t tile, uint8_t *dst, uint64_t *bar,
+                        uint32_t lane)
+{
+    DecLoad r;
+    r.bulk = false;
+    r.ok = false;
+    r.eidx = ~0u;
+    r.ebyte = 0;
+    r.delta = 0;
+    r.clen = 0;
+    const uint32_t Bb = block_elems_of(a, tile);
+    const uint64_t tail_b = (uint64_t)a.tail_elems * a.es;
+    if (a.in_bytes < 12 + tail_b) return r;
+    const uint64_t D = a.block_offsets[tile];
+    const uint64_t Dn = tile + 1 < a.nb ? a.block_offsets[tile + 1] : a.in_bytes - tail_b;
+    if (D < 12 || Dn < D + 4 || Dn > a.in_bytes || Dn - D - 4 > lz4b(Bb * a.es)) return r;
+    r.ok = true;
+    r.clen = (uint32_t)(Dn - D - 4);
+    const uint64_t base = D & ~15ull;
+    r.delta = (uint32_t)(D - base);
+    const uint64_t A0 = (D + 15) & ~15ull, A1 = Dn & ~15ull;
+    const uint64_t head_end = A0 < Dn ? A0 : Dn;
+    const uint64_t tail_beg = A1 > A0 ? A1 : A0;
+    if (A1 > A0) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar, (uint32_t)(A1 - A0));
+            bulk_g2s(dst + (A0 - base), a.in + A0, (uint32_t)(A1 - A0), bar);
+        }
+        r.bulk = true;
+    }
+    if (lane < 16) {
+        uint64_t x = D + lane;
+        if (x < head_end) {
+            r.ebyte = a.in[x];
+            r.eidx = (uint32_t)(x - base);
+        }
+    } else {
+        uint64_t x = tail_beg + (lane - 16);
+        if (x < Dn) {
+            r.ebyte = a.in[x];
+            r.eidx = (uint32_t)(x - base);
+        }
+    }
+    return r;
+}
+
+template <uint32_t MAXB>
+__global__ void __launch_bounds__(32) decompress_kernel(const __grid_constant__ CodecArgs a)
+{
+    using L = DecPlan<MAXB>;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *buf[2] = {sm, sm + L::BUF};
+    uint8_t *dec = sm + 2 * L::BUF;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(dec + L::DEC);
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t parity[2] = {0u, 0u};
+    bool header_checked = false;
+    uint32_t tile = grab_tile(a.tile_counter, lane);
+    DecLoad ld[2];
+    int cur = 0;
+    if (tile < a.nb) ld[0] = dec_issue(a, tile, buf[0], &bar[0], lane);
+    while (tile < a.nb) {
+        const uint32_t nxt = grab_tile(a.tile_counter, lane);
+        DecLoad L0 = cur ? ld[1] : ld[0];
+        if (L0.bulk) {
+            if (!mbar_wait_bounded(&bar[cur], parity[cur]) && lane == 0)
+                set_status(a.status, BSGPU_ERR_TIMEOUT);
+            parity[cur] ^= 1u;
+        }
+        if (nxt < a.nb) {
+            // the other buffer last fed a bulk store; let it finish reading
+            if (lane == 0) bulk_wait_read0();
+            __syncwarp();
+            fence_proxy_async_smem();
+            DecLoad n = dec_issue(a, nxt, buf[cur ^ 1], &bar[cur ^ 1], lane);
+            if (cur) ld[0] = n; else ld[1] = n;
+        }
+        uint8_t *cb = buf[cur];
+        if (!header_checked) {
+            header_checked = true;
+            uint32_t ok = 1;
+            if (lane < 12) {
+                uint8_t want = lane < 8 ? (uint8_t)((a.n_elem * a.es) >> (8 * (7 - lane)))
+                                        : (uint8_t)(((uint64_t)a.B * a.es) >> (8 * (11 - lane)));
+                ok = a.in_bytes >= 12 && a.in[lane] == want;
+            }
+            if (__ballot_sync(FULL, !ok) && lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);
+        }
+        const uint32_t Bb = block_elems_of(a, tile);
+        const uint32_t S = Bb * a.es;
+        bool good = L0.ok;
+        if (good) {
+            if (L0.eidx != ~0u) cb[L0.eidx] = L0.ebyte;
+            __syncwarp();
+            good = get_be32(cb + L0.delta) == L0.clen &&
+                   lz4_decode_warp(cb + L0.delta + 4, L0.clen, dec, S) == 0;
+        }
+        if (!good) {
+            if (lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);
+        } else {
+            unshuffle_block(dec, cb, Bb, a.es, lane);
+            __syncwarp();
+            uint8_t *dst = a.out + (uint64_t)tile * a.B * a.es;
+            if ((S & 15u) == 0 && ((uintptr_t)dst & 15u) == 0) {
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    bulk_s2g(dst, cb, S);
+                    bulk_commit();
+                }
+            } else {
+                for (uint32_t k = lane; k < S; k += 32) dst[k] = cb[k];
+            }
+        }
+        if (tile + 1 == a.nb) {
+            const uint32_t tb = a.tail_elems * a.es;
+            const uint64_t first = (a.n_elem - a.tail_elems) * a.es;
+            if (a.in_bytes >= tb)
+                for (uint32_t k = lane; k < tb; k += 32)
+                    a.out[first + k] = a.in[a.in_bytes - tb + k];
+        }
+        __syncwarp();
+        tile = nxt;
+        cur ^= 1;
+    }
+    if (lane == 0) bulk_wait0();
+    __syncwarp();
+}
+
+// Block offsets by walking the chain of 4-byte length fields (one thread).
+__global__ void chain_walk_kernel(const __grid_constant__ CodecArgs a, uint64_t *offsets)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint64_t tail_b = (uint64_t)a.tail_elems * a.es;
+    uint64_t D = 12;
+    uint32_t b = 0;
+    bool bad = false;
+    for (; b < a.nb; b++) {
+        if (D + 4 > a.in_bytes) {
+            bad = true;
+            break;
+        }
+        offsets[b] = D;
+        D += 4 + (uint64_t)get_be32(a.in + D);
+    }
+    for (; b < a.nb; b++) offsets[b] = a.in_bytes;  // fails the range check
+    if (bad || D + tail_b != a.in_bytes) set_status(a.status, BSGPU_ERR_CORRUPT);
+}
+
+// n_elem < 8: the elements sit verbatim after the header.
+__global__ void decompress_small_kernel(const __grid_constant__ CodecArgs a)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t tb = a.tail_elems * a.es;
+    bool ok = a.in_bytes == 12ull + tb;
+    if (ok && lane < 12) {
+        uint8_t want = lane < 8 ? (uint8_t)((a.n_elem * a.es) >> (8 * (7 - lane)))
+                                : (uint8_t)(((uint64_t)a.B * a.es) >> (8 * (11 - lane)));
+        ok = a.in[lane] == want;
+    }
+    if (__ballot_sync(FULL, !ok)) {
+        if (lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);
+        return;
+    }
+    for (uint32_t k = lane; k < tb; k += 32) a.out[k] = a.in[12 + k];
+}
+
+// ---------------------------------------------------------------------------
+// Standalone Bitshuffle / un-Bitshuffle (no LZ4): static tiles per warp
+// ---------------------------------------------------------------------------
+template <uint32_t MAXB, bool INV>
+__global__ void __launch_bounds__(32) shuffle_kernel(const __grid_constant__ CodecArgs a)
+{
+    using L = ShufPlan<MAXB>;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *buf[2] = {sm, sm + L::BUF};
+    uint8_t *ob = sm + 2 * L::BUF;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ob + L::BUF);
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (a.nb == 0) {  // fewer than 8 elements: plain copy
+        if (blockIdx.x == 0)
+            for (uint32_t k = lane; k < a.n_elem * a.es; k += 32) a.out[k] = a.in[k];
+        return;
+    }
+    uint32_t parity[2] = {0u, 0u};
+    bool pend[2] = {false, false};
+    uint32_t tile = blockIdx.x;
+    int cur = 0;
+    if (tile < a.nb)
+        pend[0] = load_block(buf[0], a.in + (uint64_t)tile * a.B * a.es,
+                             block_elems_of(a, tile) * a.es, &bar[0], lane);
+    while (tile < a.nb) {
+        const uint32_t nxt = tile + gridDim.x;
+        if (pend[cur]) {
+            if (!mbar_wait_bounded(&bar[cur], parity[cur]) && lane == 0)
+                set_status(a.status, BSGPU_ERR_TIMEOUT);
+            parity[cur] ^= 1u;
+            pend[cur] = false;
+        }
+        if (nxt < a.nb) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            pend[cur ^ 1] = load_block(buf[cur ^ 1], a.in + (uint64_t)nxt * a.B * a.es,
+                                       block_elems_of(a, nxt) * a.es, &bar[cur ^ 1], lane);
+        }
+        const uint32_t Bb = block_elems_of(a, tile);
+        const uint32_t S = Bb * a.es;
+        // the previous bulk store from `ob` must have finished reading it
+        if (lane == 0) bulk_wait_read0();
+        __syncwarp();
+        if (INV)
+            unshuffle_block(buf[cur], ob, Bb, a.es, lane);
+        else
+            shuffle_block(buf[cur], ob, Bb, a.es, lane);
+        __syncwarp();
+        uint8_t *dst = a.out + (uint64_t)tile * a.B * a.es;
+        if ((S & 15u) == 0 && ((uintptr_t)dst & 15u) == 0) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                bulk_s2g(dst, ob, S);
+                bulk_commit();
+            }
+        } else {
+            for (uint32_t k = lane; k < S; k += 32) dst[k] = ob[k];
+        }
+        if (tile + 1 == a.nb) {
+            const uint64_t first = (a.n_elem - a.tail_elems) * a.es;
+            for (uint32_t k = lane; k < a.tail_elems * a.es; k += 32)
+                a.out[first + k] = a.in[first + k];
+        }
+        __syncwarp();
+        tile = nxt;
+        cur ^= 1;
+    }
+    if (lane == 0) bulk_wait0();
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename K>
+static cudaError_t launch_warp_kernel(K kernel, uint32_t smem, uint32_t grid, cudaStream_t s,
+                                      const CodecArgs &a)
+{
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kernel<<<grid, 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vis_tables(const float *vis, float *autos, uint32_t *pairs, uint32_t n_freq,
+                              uint32_t n_in, uint32_t T, cudaStream_t s)
+{
+    uint64_t n = (uint64_t)n_freq * n_in * T;
+    uint64_t P = (uint64_t)n_in * (n_in + 1) / 2;
+    uint64_t work = n > P ? n : P;
+    uint32_t blocks = (uint32_t)((work + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks == 0) blocks = 1;
+    vis_tables_kernel<<<blocks, 256, 0, s>>>(vis, autos, pairs, n_freq, n_in, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_precision(const float *in, float *out, uint64_t n_cplx,
+                                    const VisParams &v, uint32_t grid, cudaStream_t s)
+{
+    reduce_precision_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float2 *>(in),
+                                                 reinterpret_cast<float2 *>(out), n_cplx, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shuffle(const CodecArgs &a, bool inverse, uint32_t maxb, uint32_t grid,
+                           cudaStream_t s)
+{
+    uint32_t smem = shuffle_smem_bytes(maxb);
+    if (maxb <= 8192)
+        return inverse ? launch_warp_kernel(shuffle_kernel<8192, true>, smem, grid, s, a)
+                       : launch_warp_kernel(shuffle_kernel<8192, false>, smem, grid, s, a);
+    if (maxb <= 16384)
+        return inverse ? launch_warp_kernel(shuffle_kernel<16384, true>, smem, grid, s, a)
+                       : launch_warp_kernel(shuffle_kernel<16384, false>, smem, grid, s, a);
+    return inverse ? launch_warp_kernel(shuffle_kernel<65536, true>, smem, grid, s, a)
+                   : launch_warp_kernel(shuffle_kernel<65536, false>, smem, grid, s, a);
+}
+
+cudaError_t launch_compress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s)
+{
+    uint32_t smem = compress_smem_bytes(maxb);
+    if (maxb <= 8192) return launch_warp_kernel(compress_kernel<8192>, smem, grid, s, a);
+    if (maxb <= 16384) return launch_warp_kernel(compress_kernel<16384>, smem, grid, s, a);
+    return launch_warp_kernel(compress_kernel<65536>, smem, grid, s, a);
+}
+
+cudaError_t launch_compress_small(const CodecArgs &a, cudaStream_t s)
+{
+    compress_small_kernel<<<1, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s)
+{
+    if (a.nb == 0) {
+        decompress_small_kernel<<<1, 32, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    uint32_t smem = decompress_smem_bytes(maxb);
+    if (maxb <= 8192) return launch_warp_kernel(decompress_kernel<8192>, smem, grid, s, a);
+    if (maxb <= 16384) return launch_warp_kernel(decompress_kernel<16384>, smem, grid, s, a);
+    return launch_warp_kernel(decompress_kernel<65536>, smem, grid, s, a);
+}
+
+cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, cudaStream_t s)
+{
+    chain_walk_kernel<<<1, 32, 0, s>>>(a, offsets);
+    return cudaGetLastError();
+}
+
+}  // namespace bsg

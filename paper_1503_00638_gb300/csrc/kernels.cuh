@@ -1,0 +1,59 @@
+// Kernel argument blocks and launcher declarations shared by the kernel
+// translation units and the C-ABI layer.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bsg {
+
+// Visibility-cube geometry for the precision reduction (Sec. 3).
+struct VisParams {
+    const float *autos;     // [n_freq][n_in][n_time] unrounded Re V_ii
+    const uint32_t *pairs;  // [n_prod]: i | (j << 16), upper-triangle row-major
+    uint32_t n_in, T, P;    // inputs, time samples, products
+    uint32_t qT, rT;        // 32 / T and 32 % T (advance of a lane by 32 samples)
+    float c, c2;            // fl32(6 f / N) and 2 c
+    int enabled;
+};
+
+// One framed stream (compress / decompress / bitshuffle).
+struct CodecArgs {
+    const uint8_t *in;
+    uint8_t *out;
+    uint64_t in_bytes;       // decompress: stream length
+    uint64_t out_cap;        // compress: output capacity
+    uint64_t *out_bytes;     // compress: stream length (device)
+    uint64_t *block_offsets; // compress: written if non-null; decompress: read
+    uint64_t *tile_state;    // compress: decoupled look-back state, zeroed
+    uint32_t *tile_counter;  // dynamic tile counter, zeroed
+    int *status;             // device status word, zeroed
+    uint64_t n_elem;
+    uint32_t es, B, nb, last_B, tail_elems;
+    VisParams vis;
+};
+
+// Shared-memory bytes per warp-CTA for each kernel family and block-size class.
+uint32_t compress_smem_bytes(uint32_t maxb);
+uint32_t decompress_smem_bytes(uint32_t maxb);
+uint32_t shuffle_smem_bytes(uint32_t maxb);
+
+// Launchers (return cudaGetLastError()).  `grid` warps of 32 threads.
+cudaError_t launch_vis_tables(const float *vis, float *autos, uint32_t *pairs, uint32_t n_freq,
+                              uint32_t n_in, uint32_t T, cudaStream_t s);
+cudaError_t launch_reduce_precision(const float *in, float *out, uint64_t n_cplx,
+                                    const VisParams &v, uint32_t grid, cudaStream_t s);
+cudaError_t launch_shuffle(const CodecArgs &a, bool inverse, uint32_t maxb, uint32_t grid,
+                           cudaStream_t s);
+cudaError_t launch_compress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s);
+cudaError_t launch_compress_small(const CodecArgs &a, cudaStream_t s);
+cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s);
+cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, cudaStream_t s);
+
+// Block-size class: the smallest supported shared-memory plan for `bytes`.
+inline uint32_t maxb_class(uint32_t bytes)
+{
+    return bytes <= 8192 ? 8192u : (bytes <= 16384 ? 16384u : 65536u);
+}
+
+}  // namespace bsg

@@ -1,0 +1,174 @@
+// Bitshuffle transposes of one block in shared memory (Sec. 4.2, Sec. 6
+// step 4).  Element e's bit r (r = 8 * byte + bit, little-endian, LSB first
+// as in the caption of Fig. f:bits) goes to bit-row r: byte r * (B/8) + e/8,
+// bit e % 8.
+//
+// Fast paths (es = 4 and es = 8, B a multiple of 32): each lane takes a group
+// of 32 consecutive elements, reads them from shared memory in 16-byte chunks
+// in a lane-rotated order (conflict-free banks), transposes 32 x 32 bits in
+// registers and undoes the rotation with one funnel shift per output word.
+// Other element sizes and shapes take the byte-by-byte generic path.
+#pragma once
+
+#include "common.cuh"
+
+namespace bsg {
+
+BSG_HD bool shuffle_fast_ok(uint32_t es, uint32_t Bb)
+{
+    return (es == 4 || es == 8) && (Bb % 32u) == 0;
+}
+
+// src: Bb elements of 4 bytes (16-byte aligned); dst: 32 bit-rows of Bb/8 bytes
+BSG_HD void shuffle4_fast(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t G = Bb / 32;  // groups of 32 elements; also words per bit-row
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t g = lane; g < G; g += 32) {
+        const uint8_t *grp = src + 128u * g;
+        const uint32_t rot = g & 7u;
+        uint32_t a[32];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            uint4 v = *reinterpret_cast<const uint4 *>(grp + 16u * ((k + rot) & 7u));
+            a[4 * k] = v.x;
+            a[4 * k + 1] = v.y;
+            a[4 * k + 2] = v.z;
+            a[4 * k + 3] = v.w;
+        }
+        // a[m] holds element (m + 4 rot) mod 32
+        transpose32(a);
+#pragma unroll
+        for (int r = 0; r < 32; r++) d32[r * G + g] = rotl(a[r], 4u * rot);
+    }
+}
+
+// src: 32 bit-rows of Bb/8 bytes; dst: Bb elements of 4 bytes
+BSG_HD void unshuffle4_fast(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t G = Bb / 32;
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
+    for (uint32_t g = lane; g < G; g += 32) {
+        const uint32_t rot = g & 7u;
+        uint32_t a[32];
+#pragma unroll
+        for (int r = 0; r < 32; r++) a[r] = rotr(s32[r * G + g], 4u * rot);
+        // after the transpose a[m] holds element (m + 4 rot) mod 32
+        transpose32(a);
+        uint8_t *grp = dst + 128u * g;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            *reinterpret_cast<uint4 *>(grp + 16u * ((k + rot) & 7u)) =
+                make_uint4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+        }
+    }
+}
+
+// 8-byte elements: the low and high words of a group transpose separately
+// into bit-rows 0..31 and 32..63.
+BSG_HD void shuffle8_fast(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t G = Bb / 32;
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t g = lane; g < G; g += 32) {
+        const uint8_t *grp = src + 256u * g;
+        const uint32_t rot = g & 15u;
+        uint32_t lo[32], hi[32];
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            uint4 v = *reinterpret_cast<const uint4 *>(grp + 16u * ((k + rot) & 15u));
+            lo[2 * k] = v.x;
+            hi[2 * k] = v.y;
+            lo[2 * k + 1] = v.z;
+            hi[2 * k + 1] = v.w;
+        }
+        // lo[m], hi[m] hold element (m + 2 rot) mod 32
+        transpose32(lo);
+#pragma unroll
+        for (int r = 0; r < 32; r++) d32[r * G + g] = rotl(lo[r], 2u * rot);
+        transpose32(hi);
+#pragma unroll
+        for (int r = 0; r < 32; r++) d32[(32 + r) * G + g] = rotl(hi[r], 2u * rot);
+    }
+}
+
+BSG_HD void unshuffle8_fast(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t G = Bb / 32;
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
+    for (uint32_t g = lane; g < G; g += 32) {
+        const uint32_t rot = g & 15u;
+        uint32_t lo[32], hi[32];
+#pragma unroll
+        for (int r = 0; r < 32; r++) {
+            lo[r] = rotr(s32[r * G + g], 2u * rot);
+            hi[r] = rotr(s32[(32 + r) * G + g], 2u * rot);
+        }
+        transpose32(lo);
+        transpose32(hi);
+        uint8_t *grp = dst + 256u * g;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            *reinterpret_cast<uint4 *>(grp + 16u * ((k + rot) & 15u)) =
+                make_uint4(lo[2 * k], hi[2 * k], lo[2 * k + 1], hi[2 * k + 1]);
+        }
+    }
+}
+
+// Generic paths: any es in {1,2,4,8} and Bb a multiple of 8.  One output byte
+// per lane step, gathered from 8 input bytes.
+BSG_HD void shuffle_generic(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t es,
+                            uint32_t lane)
+{
+    const uint32_t rowb = Bb / 8;
+    const uint32_t S = Bb * es;
+    for (uint32_t o = lane; o < S; o += 32) {
+        uint32_t r = o / rowb, col = o - r * rowb;
+        uint32_t byte = r >> 3, bit = r & 7u;
+        uint32_t v = 0;
+#pragma unroll
+        for (uint32_t e = 0; e < 8; e++)
+            v |= ((uint32_t)(src[(8 * col + e) * es + byte] >> bit) & 1u) << e;
+        dst[o] = (uint8_t)v;
+    }
+}
+
+BSG_HD void unshuffle_generic(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t es,
+                            uint32_t lane)
+{
+    const uint32_t rowb = Bb / 8;
+    const uint32_t S = Bb * es;
+    for (uint32_t o = lane; o < S; o += 32) {
+        uint32_t e = o / es, byte = o - e * es;
+        uint32_t v = 0;
+#pragma unroll
+        for (uint32_t bit = 0; bit < 8; bit++)
+            v |= ((uint32_t)(src[(8 * byte + bit) * rowb + e / 8] >> (e & 7u)) & 1u) << bit;
+        dst[o] = (uint8_t)v;
+    }
+}
+
+// One lane's share of a block transpose; a warp calls it with lanes 0..31.
+BSG_HD void shuffle_block(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t es,
+                          uint32_t lane)
+{
+    if (es == 4 && Bb % 32u == 0)
+        shuffle4_fast(src, dst, Bb, lane);
+    else if (es == 8 && Bb % 32u == 0)
+        shuffle8_fast(src, dst, Bb, lane);
+    else
+        shuffle_generic(src, dst, Bb, es, lane);
+}
+
+BSG_HD void unshuffle_block(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t es,
+                            uint32_t lane)
+{
+    if (es == 4 && Bb % 32u == 0)
+        unshuffle4_fast(src, dst, Bb, lane);
+    else if (es == 8 && Bb % 32u == 0)
+        unshuffle8_fast(src, dst, Bb, lane);
+    else
+        unshuffle_generic(src, dst, Bb, es, lane);
+}
+
+}  // namespace bsg
