@@ -35,6 +35,7 @@ import numpy as np  # noqa: E402
 METRIC = "compress+decompress GB/s (uncompressed bytes) & % HBM roofline; served p50/p99 latency"
 WORKLOAD = "chime-pathfinder-shaped visibilities 1024 freq x 8256 prod (128 inputs) x 16 time c64"
 BLOCK_ELEMS = 2048   # 8192-byte blocks of float32 components
+LEVEL = 0            # LZ4 search level
 
 
 def parse():
@@ -243,7 +244,7 @@ def main():
         if ev:
             ev[0].record(stream)
         bsgpu._check(bsgpu._lib.bsgpu_compress_vis(
-            vis.data_ptr(), F, n_in, T, cfg.n_samp, cfg.f, BLOCK_ELEMS, comp.data_ptr(), cap,
+            vis.data_ptr(), F, n_in, T, cfg.n_samp, cfg.f, BLOCK_ELEMS, LEVEL, comp.data_ptr(), cap,
             nb_dev.data_ptr(), offs.data_ptr(), ws_c.data_ptr(), ws_c.numel(),
             stream.cuda_stream), "compress_vis")
         if ev:
@@ -258,7 +259,7 @@ def main():
     # first compression fixes the stream length the decompressions read
     stream_len = [cap]
     bsgpu._check(bsgpu._lib.bsgpu_compress_vis(
-        vis.data_ptr(), F, n_in, T, cfg.n_samp, cfg.f, BLOCK_ELEMS, comp.data_ptr(), cap,
+        vis.data_ptr(), F, n_in, T, cfg.n_samp, cfg.f, BLOCK_ELEMS, LEVEL, comp.data_ptr(), cap,
         nb_dev.data_ptr(), offs.data_ptr(), ws_c.data_ptr(), ws_c.numel(), stream.cuda_stream),
         "compress_vis")
     stream_len[0] = int(nb_dev.item())
@@ -326,7 +327,7 @@ def main():
         vis.view(torch.uint8).reshape(-1).copy_(vis_pin.view(torch.uint8).reshape(-1),
                                                non_blocking=True)
         bsgpu._check(bsgpu._lib.bsgpu_compress_vis(
-            vis.data_ptr(), F, n_in, T, cfg.n_samp, cfg.f, BLOCK_ELEMS, comp.data_ptr(), cap,
+            vis.data_ptr(), F, n_in, T, cfg.n_samp, cfg.f, BLOCK_ELEMS, LEVEL, comp.data_ptr(), cap,
             nb_dev.data_ptr(), offs.data_ptr(), ws_c.data_ptr(), ws_c.numel(),
             stream.cuda_stream), "compress_vis")
         slen = int(nb_dev.item())          # the stream length (8-byte read)

@@ -119,6 +119,11 @@ int bsgpu_bitunshuffle(const void *in, void *out, size_t n_elem, size_t elem_siz
  * with LZ4 while it is on chip, writing the framed stream described at
  * bsgpu_compress_bound().
  *   in              : n_elem * elem_size bytes
+ *   level           : LZ4 match search.  0: matches of 8 or more bytes
+ *                     against the same column of the previous bit-row and
+ *                     runs (fastest to encode and to decode); 1: also a hash
+ *                     table of earlier positions (better ratio on data with
+ *                     other repeats, slower).
  *   out, out_cap    : at least bsgpu_compress_bound() bytes
  *   d_out_bytes     : device uint64, receives the stream length
  *   d_block_offsets : NULL, or bsgpu_num_blocks() device uint64s that
@@ -127,7 +132,7 @@ int bsgpu_bitunshuffle(const void *in, void *out, size_t n_elem, size_t elem_siz
  * Block sizes up to 65536 bytes (LZ4 offsets are 16-bit).  The LZ4 encoding
  * is deterministic but is not byte-identical to other encoders' (LZ4 output
  * is not unique); any conforming LZ4 block decoder reads it. */
-int bsgpu_compress(const void *in, size_t n_elem, size_t elem_size, size_t block_elems,
+int bsgpu_compress(const void *in, size_t n_elem, size_t elem_size, size_t block_elems, int level,
                    void *out, size_t out_cap, uint64_t *d_out_bytes, uint64_t *d_block_offsets,
                    void *ws, size_t ws_bytes, void *stream);
 
@@ -149,10 +154,11 @@ int bsgpu_decompress(const void *in, size_t in_bytes, void *out, size_t n_elem, 
  * float32 values (elem_size 4), in one pass over the input.  The stream is
  * the one bsgpu_compress() would write for the rounded cube viewed as
  * 2 * n_freq * n_prod * n_time float32 elements; decode it with
- * bsgpu_decompress(elem_size = 4).
+ * bsgpu_decompress(elem_size = 4).  level as for bsgpu_compress.
  * ws: bsgpu_vis_workspace_size(BSGPU_OP_COMPRESS_VIS, ...) bytes. */
 int bsgpu_compress_vis(const void *vis, int64_t n_freq, int64_t n_inputs, int64_t n_time,
-                       double N, double f, size_t block_elems, void *out, size_t out_cap,
+                       double N, double f, size_t block_elems, int level, void *out,
+                       size_t out_cap,
                        uint64_t *d_out_bytes, uint64_t *d_block_offsets, void *ws,
                        size_t ws_bytes, void *stream);
 

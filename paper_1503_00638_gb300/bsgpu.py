@@ -36,10 +36,10 @@ _SIGS = {
     "bsgpu_reduce_precision_c64": ([_vp, _vp, _i64, _i64, _i64, _d, _d, _vp, _sz, _vp], _i),
     "bsgpu_bitshuffle": ([_vp, _vp, _sz, _sz, _sz, _vp], _i),
     "bsgpu_bitunshuffle": ([_vp, _vp, _sz, _sz, _sz, _vp], _i),
-    "bsgpu_compress": ([_vp, _sz, _sz, _sz, _vp, _sz, _vp, _vp, _vp, _sz, _vp], _i),
+    "bsgpu_compress": ([_vp, _sz, _sz, _sz, _i, _vp, _sz, _vp, _vp, _vp, _sz, _vp], _i),
     "bsgpu_decompress": ([_vp, _sz, _vp, _sz, _sz, _sz, _vp, _vp, _sz, _vp], _i),
-    "bsgpu_compress_vis": ([_vp, _i64, _i64, _i64, _d, _d, _sz, _vp, _sz, _vp, _vp, _vp, _sz,
-                            _vp], _i),
+    "bsgpu_compress_vis": ([_vp, _i64, _i64, _i64, _d, _d, _sz, _i, _vp, _sz, _vp, _vp, _vp,
+                            _sz, _vp], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -177,7 +177,7 @@ class Compressed:
 
 def compress(x: torch.Tensor, block_elems: int = 0, elem_size: int | None = None,
              out: torch.Tensor | None = None, with_offsets: bool = True,
-             ws: torch.Tensor | None = None, stream=None) -> Compressed:
+             ws: torch.Tensor | None = None, stream=None, level: int = 0) -> Compressed:
     es = elem_size or x.element_size()
     n = x.numel() * x.element_size() // es
     cap = compress_bound(n, es, block_elems)
@@ -189,7 +189,8 @@ def compress(x: torch.Tensor, block_elems: int = 0, elem_size: int | None = None
     offs = torch.empty(max(nblk, 1), dtype=torch.int64, device=x.device) if with_offsets else None
     need = workspace_size(OP_COMPRESS, n, es, block_elems)
     ws = new_workspace(need, x.device) if ws is None else ws
-    _check(_lib.bsgpu_compress(_ptr(x), n, es, block_elems, _ptr(out), out.numel(), _ptr(nb_dev),
+    _check(_lib.bsgpu_compress(_ptr(x), n, es, block_elems, level, _ptr(out), out.numel(),
+                               _ptr(nb_dev),
                                _ptr(offs), _ptr(ws), ws.numel(), _stream(stream)),
            "bsgpu_compress")
     return Compressed(out, nb_dev, offs, n, es, block_elems, ws)
@@ -197,7 +198,7 @@ def compress(x: torch.Tensor, block_elems: int = 0, elem_size: int | None = None
 
 def compress_vis(vis: torch.Tensor, N: float, f: float, block_elems: int = 0,
                  out: torch.Tensor | None = None, with_offsets: bool = True,
-                 ws: torch.Tensor | None = None, stream=None) -> Compressed:
+                 ws: torch.Tensor | None = None, stream=None, level: int = 0) -> Compressed:
     """Precision reduction + Bitshuffle + LZ4 of a complex64 cube (Sec. 6)."""
     F, P, T = vis.shape
     n_in = _n_inputs(P)
@@ -212,7 +213,7 @@ def compress_vis(vis: torch.Tensor, N: float, f: float, block_elems: int = 0,
     need = vis_workspace_size(OP_COMPRESS_VIS, F, n_in, T, block_elems)
     ws = new_workspace(need, vis.device) if ws is None else ws
     _check(_lib.bsgpu_compress_vis(_ptr(vis), F, n_in, T, float(N), float(f), block_elems,
-                                   _ptr(out), out.numel(), _ptr(nb_dev), _ptr(offs), _ptr(ws),
+                                   level, _ptr(out), out.numel(), _ptr(nb_dev), _ptr(offs), _ptr(ws),
                                    ws.numel(), _stream(stream)), "bsgpu_compress_vis")
     return Compressed(out, nb_dev, offs, n, 4, block_elems, ws)
 

@@ -252,11 +252,12 @@ int bsgpu_bitunshuffle(const void *in, void *out, size_t n_elem, size_t elem_siz
     return shuffle_common(in, out, n_elem, elem_size, block_elems, stream, true);
 }
 
-static int compress_common(const void *in, const Geometry &g, void *out, size_t out_cap,
-                           uint64_t *d_out_bytes, uint64_t *d_block_offsets, void *ws,
-                           size_t ws_bytes, void *stream, const VisParams *vis,
+static int compress_common(const void *in, const Geometry &g, int level, void *out,
+                           size_t out_cap, uint64_t *d_out_bytes, uint64_t *d_block_offsets,
+                           void *ws, size_t ws_bytes, void *stream, const VisParams *vis,
                            const WsLayout &L)
 {
+    if (level < 0 || level > 1) return BSGPU_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (out_cap < stream_bound(g)) return BSGPU_ERR_SPACE;
     if (ws_bytes < L.total) return BSGPU_ERR_SPACE;
@@ -275,6 +276,7 @@ static int compress_common(const void *in, const Geometry &g, void *out, size_t 
     a.nb = g.nb;
     a.last_B = g.last_B;
     a.tail_elems = g.tail;
+    a.level = level;
     if (vis) a.vis = *vis;
     if (cudaMemsetAsync(ws, 0, L.state + (size_t)g.nb * 8, s) != cudaSuccess)
         return BSGPU_ERR_CUDA;
@@ -285,7 +287,7 @@ static int compress_common(const void *in, const Geometry &g, void *out, size_t 
 }
 
 int bsgpu_compress(const void *in, size_t n_elem, size_t elem_size, size_t block_elems,
-                   void *out, size_t out_cap, uint64_t *d_out_bytes, uint64_t *d_block_offsets,
+                   int level, void *out, size_t out_cap, uint64_t *d_out_bytes, uint64_t *d_block_offsets,
                    void *ws, size_t ws_bytes, void *stream)
 {
     Geometry g;
@@ -296,12 +298,13 @@ int bsgpu_compress(const void *in, size_t n_elem, size_t elem_size, size_t block
         ((uintptr_t)d_block_offsets & 7u))
         return BSGPU_ERR_ALIGN;
     WsLayout L = ws_layout(BSGPU_OP_COMPRESS, g, 0, 0);
-    return compress_common(in, g, out, out_cap, d_out_bytes, d_block_offsets, ws, ws_bytes,
-                           stream, nullptr, L);
+    return compress_common(in, g, level, out, out_cap, d_out_bytes, d_block_offsets, ws,
+                           ws_bytes, stream, nullptr, L);
 }
 
 int bsgpu_compress_vis(const void *vis, int64_t n_freq, int64_t n_inputs, int64_t n_time,
-                       double N, double f, size_t block_elems, void *out, size_t out_cap,
+                       double N, double f, size_t block_elems, int level, void *out,
+                       size_t out_cap,
                        uint64_t *d_out_bytes, uint64_t *d_block_offsets, void *ws,
                        size_t ws_bytes, void *stream)
 {
@@ -325,8 +328,8 @@ int bsgpu_compress_vis(const void *vis, int64_t n_freq, int64_t n_inputs, int64_
                                       const_cast<uint32_t *>(v.pairs), (uint32_t)n_freq,
                                       (uint32_t)n_inputs, (uint32_t)n_time, s);
     if (e != cudaSuccess) return BSGPU_ERR_CUDA;
-    return compress_common(vis, g, out, out_cap, d_out_bytes, d_block_offsets, ws, ws_bytes,
-                           stream, &v, L);
+    return compress_common(vis, g, level, out, out_cap, d_out_bytes, d_block_offsets, ws,
+                           ws_bytes, stream, &v, L);
 }
 
 int bsgpu_decompress(const void *in, size_t in_bytes, void *out, size_t n_elem, size_t elem_size,

@@ -26,8 +26,9 @@ struct CompPlan {
     static constexpr uint32_t CAP = r16(4 + lz4b(MAXB) + 48);
     static constexpr uint32_t BUF = r128(cmax(CAP, MAXB + 32));
     static constexpr uint32_t TMP = r128(MAXB + 32);
-    static constexpr int HBITS = MAXB <= 8192 ? 10 : (MAXB <= 16384 ? 11 : 12);
-    static constexpr uint32_t HASH = 4u << HBITS;
+    // one 16-bit entry per probed word position of the largest block
+    static constexpr int HBITS = MAXB <= 8192 ? 11 : (MAXB <= 16384 ? 12 : 13);
+    static constexpr uint32_t HASH = 2u << HBITS;
     static constexpr uint32_t BYTES = 2 * BUF + TMP + HASH + 16;
 };
 
@@ -314,7 +315,7 @@ BSG_D uint64_t lookback(uint64_t *state, uint32_t tile, uint64_t agg, int *statu
 // ---------------------------------------------------------------------------
 template <uint32_t MAXB>
 BSG_D void compress_tile(const CodecArgs &a, uint32_t tile, uint8_t *buf, uint8_t *tmp,
-                         uint32_t *table, uint32_t lane)
+                         uint16_t *table, uint32_t lane)
 {
     using L = CompPlan<MAXB>;
     const uint32_t Bb = block_elems_of(a, tile);
@@ -327,7 +328,9 @@ BSG_D void compress_tile(const CodecArgs &a, uint32_t tile, uint8_t *buf, uint8_
     }
     shuffle_block(buf, tmp, Bb, a.es, lane);
     __syncwarp();
-    uint32_t cs = lz4_encode_warp<L::HBITS>(tmp, S, buf + 4, table);
+    // bit-rows are Bb/8 bytes long: the previous row is one of the candidates
+    uint32_t cs = a.level >= 1 ? lz4_encode_warp<1, L::HBITS>(tmp, S, Bb / 8, buf + 4, table)
+                               : lz4_encode_warp<0, L::HBITS>(tmp, S, Bb / 8, buf + 4, table);
     if (cs == 0xffffffffu) {  // progress guard (not reachable for valid sizes)
         if (lane == 0) set_status(a.status, BSGPU_ERR_CUDA);
         cs = 0;
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(32) compress_kernel(const __grid_constant__ Co
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t *buf[2] = {sm, sm + L::BUF};
     uint8_t *tmp = sm + 2 * L::BUF;
-    uint32_t *table = reinterpret_cast<uint32_t *>(tmp + L::TMP);
+    uint16_t *table = reinterpret_cast<uint16_t *>(tmp + L::TMP);
     uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(table) + L::HASH);
     const uint32_t lane = threadIdx.x & 31u;
     if (lane == 0) {
@@ -462,30 +465,25 @@ BSG_D DecLoad dec_issue(const CodecArgs &a, uint32_t tile, uint8_t *dst, uint64_
     if (D < 12 || Dn < D + 4 || Dn > a.in_bytes || Dn - D - 4 > lz4b(Bb * a.es)) return r;
     r.ok = true;
     r.clen = (uint32_t)(Dn - D - 4);
-    const uint64_t base = D & ~15ull;
-    r.delta = (uint32_t)(D - base);
-    const uint64_t A0 = (D + 15) & ~15ull, A1 = Dn & ~15ull;
-    const uint64_t head_end = A0 < Dn ? A0 : Dn;
+    // alignment is a property of the absolute address, not of the offset
+    const uint64_t g0 = (uint64_t)(uintptr_t)(a.in + D), gn = g0 + (Dn - D);
+    const uint64_t base = g0 & ~15ull;
+    r.delta = (uint32_t)(g0 - base);
+    const uint64_t A0 = (g0 + 15) & ~15ull, A1 = gn & ~15ull;
+    const uint64_t head_end = A0 < gn ? A0 : gn;
     const uint64_t tail_beg = A1 > A0 ? A1 : A0;
     if (A1 > A0) {
         if (lane == 0) {
             mbar_arrive_expect_tx(bar, (uint32_t)(A1 - A0));
-            bulk_g2s(dst + (A0 - base), a.in + A0, (uint32_t)(A1 - A0), bar);
+            bulk_g2s(dst + (A0 - base), reinterpret_cast<const void *>(A0), (uint32_t)(A1 - A0),
+                     bar);
         }
         r.bulk = true;
     }
-    if (lane < 16) {
-        uint64_t x = D + lane;
-        if (x < head_end) {
-            r.ebyte = a.in[x];
-            r.eidx = (uint32_t)(x - base);
-        }
-    } else {
-        uint64_t x = tail_beg + (lane - 16);
-        if (x < Dn) {
-            r.ebyte = a.in[x];
-            r.eidx = (uint32_t)(x - base);
-        }
+    uint64_t x = lane < 16 ? g0 + lane : tail_beg + (lane - 16);
+    if ((lane < 16 && x < head_end) || (lane >= 16 && x < gn)) {
+        r.ebyte = *reinterpret_cast<const uint8_t *>(x);
+        r.eidx = (uint32_t)(x - base);
     }
     return r;
 }
@@ -545,7 +543,7 @@ __global__ void __launch_bounds__(32) decompress_kernel(const __grid_constant__ 
             if (L0.eidx != ~0u) cb[L0.eidx] = L0.ebyte;
             __syncwarp();
             good = get_be32(cb + L0.delta) == L0.clen &&
-                   lz4_decode_warp(cb + L0.delta + 4, L0.clen, dec, S) == 0;
+                   lz4_decode_warp(cb, L0.delta + 4, L0.clen, dec, S) == 0;
         }
         if (!good) {
             if (lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);

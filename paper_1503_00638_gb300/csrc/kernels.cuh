@@ -30,6 +30,7 @@ struct CodecArgs {
     int *status;             // device status word, zeroed
     uint64_t n_elem;
     uint32_t es, B, nb, last_B, tail_elems;
+    int level;               // compress: LZ4 search level (0 structural, 1 + hash)
     VisParams vis;
 };
 

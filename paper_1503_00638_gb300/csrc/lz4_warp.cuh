@@ -25,15 +25,72 @@ BSG_HD uint32_t lz4_bound(uint32_t n) { return n + n / 255u + 16u; }
 // bytes): skips quickly through incompressible bit rows.
 constexpr uint32_t LZ4_ACCEL_WINDOWS = 4;
 
+// Shortest match the GPU encoder emits (the format allows 4).
+constexpr uint32_t LZ4_GPU_MINMATCH = 8;
+
 #if defined(__CUDACC__) || defined(BSG_WARP_EMU)
 
 // 4 bytes starting at byte q of a word-aligned shared buffer (little endian);
 // reads the aligned words at q & ~3 and the next one
 BSG_D uint32_t ld32u(const uint8_t *base, uint32_t q)
 {
+#ifdef BSG_WARP_EMU
+    emu_check_aligned4(base);
+#endif
     const uint32_t *w = reinterpret_cast<const uint32_t *>(base);
     uint32_t i = q >> 2;
     return funnel_r(w[i], w[i + 1], (q & 3u) * 8u);
+}
+
+// Warp copy of len bytes src[s..] -> dst[d..] (word-aligned shared buffers,
+// the ranges must not overlap): bytes up to dst's next word boundary, whole
+// words assembled by funnel shifts, then the ragged end.  src is read up to
+// 7 bytes past s + len.
+BSG_D void warp_copy(uint8_t *dst, uint32_t d, const uint8_t *src, uint32_t s, uint32_t len,
+                     uint32_t lane)
+{
+#ifdef BSG_WARP_EMU
+    emu_check_aligned4(dst);
+    emu_check_aligned4(src);
+#endif
+    if (len <= 32) {
+        if (lane < len) dst[d + lane] = src[s + lane];
+        return;
+    }
+    const uint32_t a0 = (d + 3u) & ~3u, a1 = (d + len) & ~3u;
+    const uint32_t head = a0 - d, tail = d + len - a1;
+    if (lane < head) dst[d + lane] = src[s + lane];
+    if (lane >= 28 && lane - 28 < tail) dst[a1 + lane - 28] = src[s + (a1 - d) + lane - 28];
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t w = (a0 >> 2) + lane; w < (a1 >> 2); w += 32) d32[w] = ld32u(src, s + 4 * w - d);
+}
+
+// Warp fill of len bytes at dst[d..] with the byte b.
+BSG_D void warp_fill(uint8_t *dst, uint32_t d, uint32_t b, uint32_t len, uint32_t lane)
+{
+#ifdef BSG_WARP_EMU
+    emu_check_aligned4(dst);
+#endif
+    if (len <= 32) {
+        if (lane < len) dst[d + lane] = (uint8_t)b;
+        return;
+    }
+    const uint32_t a0 = (d + 3u) & ~3u, a1 = (d + len) & ~3u;
+    const uint32_t head = a0 - d, tail = d + len - a1;
+    if (lane < head) dst[d + lane] = (uint8_t)b;
+    if (lane >= 28 && lane - 28 < tail) dst[a1 + lane - 28] = (uint8_t)b;
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    const uint32_t v = b * 0x01010101u;
+    for (uint32_t w = (a0 >> 2) + lane; w < (a1 >> 2); w += 32) d32[w] = v;
+}
+
+// Length bytes of an LZ4 field: v >= 15 is 15 in the nibble, then
+// (v - 15) / 255 bytes of 255 and one byte of (v - 15) % 255.
+BSG_D uint32_t lz4_ext_count(uint32_t v) { return v >= 15 ? (v - 15) / 255 + 1 : 0; }
+
+BSG_D void lz4_put_ext(uint8_t *dst, uint32_t o, uint32_t v, uint32_t n, uint32_t lane)
+{
+    for (uint32_t k = lane; k < n; k += 32) dst[o + k] = k + 1 < n ? 255u : (uint8_t)((v - 15) % 255u);
 }
 
 // Write one sequence (literals [anchor, mp), match of `len` bytes at
@@ -41,135 +98,144 @@ BSG_D uint32_t ld32u(const uint8_t *base, uint32_t q)
 BSG_D uint32_t lz4_emit(uint8_t *dst, uint32_t o, const uint8_t *src, uint32_t anchor,
                         uint32_t mp, uint32_t off, uint32_t len, uint32_t lane)
 {
-    uint32_t LL = mp - anchor;
-    uint32_t ML = len - LZ4_MINMATCH;
-    uint32_t nll = LL >= 15 ? (LL - 15) / 255 + 1 : 0;
-    uint32_t nml = ML >= 15 ? (ML - 15) / 255 + 1 : 0;
-    uint32_t hdr = 1 + nll;
-    uint32_t total = hdr + LL + 2 + nml;
-    uint32_t token = ((LL < 15 ? LL : 15) << 4) | (ML < 15 ? ML : 15);
-    for (uint32_t idx = lane; idx < total; idx += 32) {
-        uint32_t b;
-        if (idx == 0) {
-            b = token;
-        } else if (idx < hdr) {
-            b = (idx < hdr - 1) ? 255u : (LL - 15) % 255u;
-        } else if (idx < hdr + LL) {
-            b = src[anchor + idx - hdr];
-        } else if (idx == hdr + LL) {
-            b = off & 255u;
-        } else if (idx == hdr + LL + 1) {
-            b = off >> 8;
-        } else {
-            uint32_t j = idx - hdr - LL - 2;
-            b = (j < nml - 1) ? 255u : (ML - 15) % 255u;
-        }
-        dst[o + idx] = (uint8_t)b;
-    }
-    return o + total;
+    const uint32_t LL = mp - anchor;
+    const uint32_t ML = len - LZ4_MINMATCH;
+    const uint32_t nll = lz4_ext_count(LL), nml = lz4_ext_count(ML);
+    if (lane == 0) dst[o] = (uint8_t)(((LL < 15 ? LL : 15) << 4) | (ML < 15 ? ML : 15));
+    lz4_put_ext(dst, o + 1, LL, nll, lane);
+    const uint32_t lo = o + 1 + nll;
+    warp_copy(dst, lo, src, anchor, LL, lane);
+    const uint32_t oo = lo + LL;
+    if (lane == 1) dst[oo] = (uint8_t)(off & 255u);
+    if (lane == 2) dst[oo + 1] = (uint8_t)(off >> 8);
+    lz4_put_ext(dst, oo + 2, ML, nml, lane);
+    return oo + 2 + nml;
 }
 
 // Literals-only last sequence [anchor, S).
 BSG_D uint32_t lz4_emit_last(uint8_t *dst, uint32_t o, const uint8_t *src, uint32_t anchor,
                              uint32_t S, uint32_t lane)
 {
-    uint32_t LL = S - anchor;
-    uint32_t nll = LL >= 15 ? (LL - 15) / 255 + 1 : 0;
-    uint32_t hdr = 1 + nll;
-    uint32_t total = hdr + LL;
-    uint32_t token = (LL < 15 ? LL : 15) << 4;
-    for (uint32_t idx = lane; idx < total; idx += 32) {
-        uint32_t b;
-        if (idx == 0)
-            b = token;
-        else if (idx < hdr)
-            b = (idx < hdr - 1) ? 255u : (LL - 15) % 255u;
-        else
-            b = src[anchor + idx - hdr];
-        dst[o + idx] = (uint8_t)b;
-    }
-    return o + total;
+    const uint32_t LL = S - anchor;
+    const uint32_t nll = lz4_ext_count(LL);
+    if (lane == 0) dst[o] = (uint8_t)((LL < 15 ? LL : 15) << 4);
+    lz4_put_ext(dst, o + 1, LL, nll, lane);
+    warp_copy(dst, o + 1 + nll, src, anchor, LL, lane);
+    return o + 1 + nll + LL;
 }
 
 // Encode src[0, S) (word aligned, readable up to S + 8) into dst (capacity
-// lz4_bound(S)).  Probes 32 word-aligned positions per step with a table of
-// the last aligned position of each 4-byte hash (cleared here) plus the
-// nearest earlier lane holding the same word; takes the first verified
-// match, extends it back by up to 3 bytes and forward warp-wide.  The result
-// depends only on the bytes of the block.  Returns the compressed size, or
-// 0xffffffff if the progress guard tripped (cannot happen for valid sizes).
-template <int HBITS>
-BSG_D uint32_t lz4_encode_warp(const uint8_t *src, uint32_t S, uint8_t *dst, uint32_t *table)
+// lz4_bound(S)), taking only matches of at least LZ4_GPU_MINMATCH bytes:
+// short matches save a byte or two each but cost a whole sequence, and the
+// sequence count is what bounds the decoder's speed.
+//
+// Each step probes 32 word-aligned positions p at once.  Candidates:
+//  * the same column of the previous bit-row, p - rowlen (a bit-row repeating
+//    the one before it, as the most significant rows of two's-complement or
+//    sign/exponent data do, Sec. 4.2); rowlen = 0 disables it;
+//  * p - 4, a run (all-zero rows of the bits rounded away, Sec. 3.2);
+//  * LEVEL >= 1 only: the last probed position with the same 4-byte hash
+//    (nearest earlier lane of this step, else a 16-bit table entry written by
+//    the highest lane of each hash group, so nothing depends on scheduling);
+//    after LZ4_ACCEL_WINDOWS fruitless steps the probe stride doubles (to 16
+//    bytes at most).
+// The first position whose candidate agrees on 8 bytes is taken, extended
+// back by up to 3 bytes and forward warp-wide.  Returns the compressed size,
+// or 0xffffffff if the progress guard tripped (cannot happen for valid sizes).
+template <int LEVEL, int HBITS>
+BSG_D uint32_t lz4_encode_warp(const uint8_t *src, uint32_t S, uint32_t rowlen, uint8_t *dst,
+                               uint16_t *table)
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t lt = lanemask_lt();
-    for (uint32_t i = lane; i < (1u << HBITS); i += 32) table[i] = 0;
-    __syncwarp();
+    const uint32_t le = lt | (1u << lane);
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
+    if (LEVEL >= 1) {
+        uint4 *t4 = reinterpret_cast<uint4 *>(table);
+        for (uint32_t i = lane; i < (2u << HBITS) / 16u; i += 32) t4[i] = make_uint4(0, 0, 0, 0);
+        __syncwarp();
+    }
+    if (rowlen & 3u) rowlen = 0;
     uint32_t anchor = 0, o = 0;
     if (S >= LZ4_MFLIMIT + 1) {
-        const uint32_t mflimit = S - LZ4_MFLIMIT;       // last allowed match start
+        const uint32_t mflimit = S - LZ4_MFLIMIT;          // last allowed match start
         const uint32_t matchlimit = S - LZ4_LASTLITERALS;  // match end bound
         uint32_t pos = 0, fails = 0;
         const uint32_t guard = S / 4 + 8;
         uint32_t it = 0;
         while (pos <= mflimit) {
             if (++it > guard) return 0xffffffffu;
-            uint32_t sh = fails / LZ4_ACCEL_WINDOWS;
-            uint32_t step = 4u << (sh < 2 ? sh : 2);
-            uint32_t p = pos + step * lane;
-            bool valid = p <= mflimit;
-            uint32_t w = valid ? *reinterpret_cast<const uint32_t *>(src + p) : 0u;
-            uint32_t h = (w * 2654435761u) >> (32 - HBITS);
-            int32_t cand = valid ? (int32_t)table[h] - 1 : -1;
-            uint32_t vmask = __ballot_sync(FULL, valid);
-            uint32_t same = __match_any_sync(FULL, w) & vmask & lt;
-            bool intra = valid && same != 0;
-            if (intra) cand = (int32_t)(pos + step * (31 - __clz(same)));
-            bool ok = valid && cand >= 0 &&
-                      (intra || *reinterpret_cast<const uint32_t *>(src + cand) == w);
-            uint32_t mm = __ballot_sync(FULL, ok);
-            if (mm == 0) {
-                if (valid) atomicMax(&table[h], p + 1);
+            uint32_t step = 4;
+            if (LEVEL >= 1) {
+                const uint32_t sh = fails / LZ4_ACCEL_WINDOWS;
+                step = 4u << (sh < 2 ? sh : 2);
+            }
+            const uint32_t p = pos + step * lane;
+            const bool valid = p <= mflimit;
+            const uint32_t wi = p >> 2;
+            const uint32_t w0 = valid ? s32[wi] : 0u;
+            const uint32_t w1 = valid ? s32[wi + 1] : 0u;
+            uint32_t off = 0;
+            if (valid && rowlen && p >= rowlen) {
+                const uint32_t ri = (p - rowlen) >> 2;
+                if (s32[ri] == w0 && s32[ri + 1] == w1) off = rowlen;
+            }
+            if (valid && off == 0 && p >= 4 && w1 == w0 && s32[wi - 1] == w0) off = 4;
+            if (LEVEL >= 1) {
+                const uint32_t h = (w0 * 2654435761u) >> (32 - HBITS);
+                const uint32_t grp = __match_any_sync(FULL, valid ? h : 0x80000000u);
+                const uint32_t lower = grp & lt;
+                int32_t cand = valid ? (int32_t)table[h] * 4 - 4 : -1;
+                if (valid && lower) cand = (int32_t)(pos + step * (31 - __clz(lower)));
+                if (valid && off == 0 && cand >= 0 && s32[cand >> 2] == w0 &&
+                    s32[(cand >> 2) + 1] == w1)
+                    off = p - (uint32_t)cand;
+                const uint32_t mm0 = __ballot_sync(FULL, off != 0);
+                const uint32_t vm = __ballot_sync(FULL, valid);
+                // insert the probed positions up to the match (all of them if none)
+                const uint32_t upto = mm0 ? ((2u << (__ffs(mm0) - 1)) - 1u) : FULL;
+                const uint32_t mine = grp & upto & vm;
+                if (valid && (upto >> lane & 1u) && (mine & ~le) == 0)
+                    table[h] = (uint16_t)((p >> 2) + 1);
                 __syncwarp();
+            }
+            const uint32_t mm = __ballot_sync(FULL, off != 0);
+            if (mm == 0) {
                 fails++;
                 pos += step * 32;
                 continue;
             }
-            uint32_t fl = __ffs(mm) - 1;
-            if (valid && lane <= fl) atomicMax(&table[h], p + 1);
-            uint32_t p0 = pos + step * fl;
+            const uint32_t fl = __ffs(mm) - 1;
+            const uint32_t p0 = pos + step * fl;
+            const uint32_t moff = __shfl_sync(FULL, off, fl);
             uint32_t mp = p0;
-            uint32_t mc = (uint32_t)__shfl_sync(FULL, cand, fl);
             // back up over up to 3 equal bytes (never before the literal anchor)
 #pragma unroll
             for (int b = 0; b < 3; b++) {
-                if (mp > anchor && mc > 0 && src[mp - 1] == src[mc - 1]) {
-                    mp--;
-                    mc--;
-                }
+                if (mp > anchor && mp > moff && src[mp - 1] == src[mp - 1 - moff]) mp--;
             }
-            uint32_t len = p0 + 4 - mp;
+            const uint32_t mc = mp - moff;
+            uint32_t len = p0 + 8 - mp;
             // extend forward, 128 bytes per step
             for (uint32_t g2 = 0; g2 < S; g2 += 128) {
-                uint32_t q = mp + len + 4 * lane;
-                int room = (int)matchlimit - (int)q;
+                const uint32_t q = mp + len + 4 * lane;
+                const int room = (int)matchlimit - (int)q;
                 uint32_t eq = 0;
                 if (room > 0) {
-                    uint32_t x = ld32u(src, q) ^ ld32u(src, mc + len + 4 * lane);
+                    const uint32_t x = ld32u(src, q) ^ ld32u(src, mc + len + 4 * lane);
                     eq = x ? ((uint32_t)(__ffs(x) - 1) >> 3) : 4u;
                     if ((int)eq > room) eq = (uint32_t)room;
                 }
-                uint32_t stop = __ballot_sync(FULL, eq < 4);
+                const uint32_t stop = __ballot_sync(FULL, eq < 4);
                 if (stop == 0) {
                     len += 128;
                     continue;
                 }
-                uint32_t sl = __ffs(stop) - 1;
+                const uint32_t sl = __ffs(stop) - 1;
                 len += 4 * sl + __shfl_sync(FULL, eq, sl);
                 break;
             }
-            __syncwarp();
-            o = lz4_emit(dst, o, src, anchor, mp, mp - mc, len, lane);
+            o = lz4_emit(dst, o, src, anchor, mp, moff, len, lane);
             anchor = mp + len;
             pos = (anchor + 3u) & ~3u;
             fails = 0;
@@ -181,7 +247,7 @@ BSG_D uint32_t lz4_encode_warp(const uint8_t *src, uint32_t S, uint8_t *dst, uin
 }
 
 // Warp-parallel read of 255-continued length bytes at src[ip..]; adds them to
-// *len.  Returns false if the bytes run past clen.
+// *len.  Returns false if the bytes run past index `clen` (the stream end).
 BSG_D bool lz4_read_len(const uint8_t *src, uint32_t clen, uint32_t &ip, uint32_t &len,
                         uint32_t lane)
 {
@@ -203,51 +269,65 @@ BSG_D bool lz4_read_len(const uint8_t *src, uint32_t clen, uint32_t &ip, uint32_
     return false;
 }
 
-// Strict decode of src[0, clen) into exactly S bytes of dst.  Returns 0, or
-// a nonzero code for: input ending early, a literal run or match overrunning
-// the output, offset 0 or before the block start, a match breaking the
-// end-of-block rules, or a final length other than S.
-BSG_D int lz4_decode_warp(const uint8_t *src, uint32_t clen, uint8_t *dst, uint32_t S)
+// Copy a match of ML bytes at distance off to dst[op..] (off <= op).  Reads
+// of an overlapping match (off < ML) only see bytes written in earlier rounds.
+BSG_D void lz4_match_copy(uint8_t *dst, uint32_t op, uint32_t off, uint32_t ML, uint32_t lane)
+{
+    if (off >= ML) {
+        warp_copy(dst, op, dst, op - off, ML, lane);
+    } else if (off == 1) {
+        warp_fill(dst, op, dst[op - 1], ML, lane);
+    } else if (off >= 32) {
+        const uint32_t W = off < 128u ? off : 128u;
+        for (uint32_t base = 0; base < ML; base += W) {
+            warp_copy(dst, op + base, dst, op + base - off, ML - base < W ? ML - base : W, lane);
+            __syncwarp();
+        }
+    } else {
+        // period off < 32: out[op + i] = out[op - off + i mod off]
+        const uint32_t W = off * (32u / off);
+        const uint8_t v = lane < W ? dst[op - off + lane % off] : 0;
+        __syncwarp();
+        for (uint32_t base = 0; base < ML; base += W) {
+            const uint32_t k = base + lane;
+            if (lane < W && k < ML) dst[op + k] = v;
+        }
+    }
+}
+
+// Strict decode of the clen bytes src[ip0 ..] into exactly S bytes of dst
+// (src and dst word-aligned shared buffers; src readable 8 bytes past the
+// end).  Returns 0, or a nonzero code for: input ending early (1), a literal
+// run overrunning the output (2), a bad offset or match length, or a match
+// breaking the end-of-block rules (3), a final length other than S (6).
+BSG_D int lz4_decode_warp(const uint8_t *src, uint32_t ip0, uint32_t clen, uint8_t *dst,
+                          uint32_t S)
 {
     const uint32_t lane = threadIdx.x & 31u;
-    uint32_t ip = 0, op = 0;
+    const uint32_t end = ip0 + clen;
+    uint32_t ip = ip0, op = 0;
     for (uint32_t guard = 0; guard <= clen; guard++) {
-        if (ip >= clen) return 1;
-        uint32_t token = src[ip++];
+        if (ip >= end) return 1;
+        const uint32_t token = src[ip++];
         uint32_t LL = token >> 4;
-        if (LL == 15 && !lz4_read_len(src, clen, ip, LL, lane)) return 1;
-        if (LL > clen - ip) return 1;
+        if (LL == 15 && !lz4_read_len(src, end, ip, LL, lane)) return 1;
+        if (LL > end - ip) return 1;
         if (LL > S - op) return 2;
-        for (uint32_t k = lane; k < LL; k += 32) dst[op + k] = src[ip + k];
+        warp_copy(dst, op, src, ip, LL, lane);
         ip += LL;
         op += LL;
-        if (ip == clen) break;
-        if (clen - ip < 2) return 1;
-        uint32_t off = (uint32_t)src[ip] | ((uint32_t)src[ip + 1] << 8);
+        if (ip == end) break;
+        if (end - ip < 2) return 1;
+        const uint32_t off = (uint32_t)src[ip] | ((uint32_t)src[ip + 1] << 8);
         ip += 2;
-        if (off == 0) return 3;
-        if (off > op) return 4;
         uint32_t ML = token & 15u;
-        if (ML == 15 && !lz4_read_len(src, clen, ip, ML, lane)) return 1;
+        if (ML == 15 && !lz4_read_len(src, end, ip, ML, lane)) return 1;
         ML += LZ4_MINMATCH;
-        if (ML > S - op) return 5;
-        if (op + LZ4_MFLIMIT > S || op + ML + LZ4_LASTLITERALS > S) return 7;
+        if (off == 0 || off > op || ML > S - op || op + LZ4_MFLIMIT > S ||
+            op + ML + LZ4_LASTLITERALS > S)
+            return 3;
         __syncwarp();
-        if (off >= 32) {
-            for (uint32_t base = 0; base < ML; base += 32) {
-                uint32_t k = base + lane;
-                if (k < ML) dst[op + k] = dst[op + k - off];
-                __syncwarp();
-            }
-        } else {
-            uint32_t W = off * (32u / off);
-            uint8_t v = lane < W ? dst[op - off + lane % off] : 0;
-            __syncwarp();
-            for (uint32_t base = 0; base < ML; base += W) {
-                uint32_t k = base + lane;
-                if (lane < W && k < ML) dst[op + k] = v;
-            }
-        }
+        lz4_match_copy(dst, op, off, ML, lane);
         op += ML;
         __syncwarp();
     }

@@ -1,0 +1,153 @@
+// CPU test of device code from paper_1503_00638_gb300/csrc: the register bit
+// transposes and shuffles (per lane, plain host calls) and the warp LZ4
+// encoder/decoder (on the warp emulator), checked against a naive bit loop
+// and the oracle's LZ4 block codec.
+#include "warp_emu.h"
+#include "../../paper_1503_00638_gb300/csrc/lz4_warp.cuh"
+#include "../../paper_1503_00638_gb300/csrc/shuffle.cuh"
+#include <cmath>
+#include <cstdio>
+#include <random>
+#include <vector>
+extern "C" {
+size_t orc_lz4_compress_block(const uint8_t *src, size_t n, uint8_t *dst, size_t cap);
+int orc_lz4_decompress_block(const uint8_t *src, size_t src_len, uint8_t *dst, size_t dst_len);
+int orc_bitshuffle(const void *vin, void *vout, size_t n, size_t es, size_t block_elems, int inverse);
+}
+using namespace bsg;
+alignas(16) static uint8_t A[70000], Bf[70000], C[70000], T[65536];
+alignas(16) static uint8_t D2[70000];
+
+static int test_transpose(std::mt19937 &rng)
+{
+    int bad = 0;
+    for (int it = 0; it < 2000; it++) {
+        uint32_t a[32], b[32];
+        for (int k = 0; k < 32; k++) a[k] = b[k] = (uint32_t)rng();
+        transpose32(a);
+        for (int r = 0; r < 32; r++)
+            for (int e = 0; e < 32; e++) bad += ((a[r] >> e) & 1) != ((b[e] >> r) & 1);
+    }
+    return bad;
+}
+
+static int test_granularity_bits(std::mt19937 &rng)
+{
+    int bad = 0;
+    for (int it = 0; it < 200000; it++) {
+        uint32_t Q = (uint32_t)rng() & 0x7fffffffu;
+        float q;
+        memcpy(&q, &Q, 4);
+        bool usable = q >= 1.17549435e-38f && std::isfinite(q);
+        if (q_usable(Q) != usable) bad++;
+        if (!usable) continue;
+        int k = 0;
+        while (ldexp(1.0, 2 * k) >= (double)q) k--;
+        while (ldexp(1.0, 2 * (k + 1)) < (double)q) k++;
+        uint32_t Tb = magic_bits(Q);
+        float Tm;
+        memcpy(&Tm, &Tb, 4);
+        if ((double)Tm != ldexp(1.0, k + 23)) bad++;
+    }
+    return bad;
+}
+
+static int test_shuffles(std::mt19937 &rng)
+{
+    int bad = 0;
+    for (int es : {1, 2, 4, 8})
+        for (int B : {8, 24, 32, 64, 96, 1024, 2048, 8192}) {
+            size_t S = (size_t)B * es;
+            if (S > 65536) continue;
+            for (size_t i = 0; i < S; i++) A[i] = (uint8_t)rng();
+            for (uint32_t l = 0; l < 32; l++) shuffle_block(A, Bf, B, es, l);
+            std::vector<uint8_t> ref(S);
+            orc_bitshuffle(A, ref.data(), B, es, B, 0);
+            bad += memcmp(Bf, ref.data(), S) != 0;
+            for (uint32_t l = 0; l < 32; l++) unshuffle_block(Bf, C, B, es, l);
+            bad += memcmp(A, C, S) != 0;
+        }
+    return bad;
+}
+
+static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc_ratio)
+{
+    int bad = 0;
+    std::vector<std::vector<uint8_t>> cases;
+    std::vector<uint32_t> rows;
+    for (int S : {0, 1, 12, 13, 17, 100, 8192}) {
+        std::vector<uint8_t> z(S, 0), r(S), m(S);
+        for (auto &x : r) x = (uint8_t)rng();
+        for (int i = 0; i < S; i++) m[i] = (i / 37) % 3 == 0 ? (uint8_t)rng() : (uint8_t)((i / 100) & 7);
+        for (auto *c : {&z, &r, &m}) {
+            cases.push_back(*c);
+            rows.push_back((uint32_t)(S / 32));
+        }
+    }
+    for (int t = 0; t < 4; t++) {
+        std::vector<int32_t> w(2048);
+        int32_t x = 0;
+        for (auto &v : w) {
+            x += (rng() & 1 ? 1 : -1) * (1 << (rng() % 7));
+            v = x;
+        }
+        std::vector<uint8_t> sh(8192);
+        orc_bitshuffle(w.data(), sh.data(), 2048, 4, 2048, 0);
+        cases.push_back(sh);
+        rows.push_back(256);
+    }
+    size_t tg = 0, to = 0, tin = 0;
+    for (size_t ci = 0; ci < cases.size(); ci++) {
+        auto &c = cases[ci];
+        uint32_t S = (uint32_t)c.size();
+        memset(A, 0xEE, S + 64);
+        memcpy(A, c.data(), S);
+        uint32_t cs = 0;
+        run_warp([&] {
+            uint32_t o = level ? lz4_encode_warp<1, 11>(A, S, rows[ci], Bf, (uint16_t *)T)
+                               : lz4_encode_warp<0, 11>(A, S, rows[ci], Bf, (uint16_t *)T);
+            if (threadIdx.x == 0) cs = o;
+        });
+        if (cs > lz4_bound(S)) { bad++; continue; }
+        std::vector<uint8_t> out(S + 1);
+        if (orc_lz4_decompress_block(Bf, cs, out.data(), S) || memcmp(out.data(), c.data(), S)) bad++;
+        int rc = -1;
+        // decode from every alignment of the stream start, as the kernel does
+        for (uint32_t sh = 0; sh < 4 && !bad; sh++) {
+            memset(D2, 0, cs + 32);
+            memcpy(D2 + sh, Bf, cs);
+            run_warp([&] {
+                int r = lz4_decode_warp(D2, sh, cs, C, S);
+                if (threadIdx.x == 0) rc = r;
+            });
+            if (rc || memcmp(C, c.data(), S)) bad++;
+        }
+        std::vector<uint8_t> oc(lz4_bound(S) + 16);
+        size_t ocs = orc_lz4_compress_block(c.data(), S, oc.data(), oc.size());
+        memset(D2, 0, ocs + 16);
+        memcpy(D2 + 3, oc.data(), ocs);
+        run_warp([&] {
+            int r = lz4_decode_warp(D2, 3, (uint32_t)ocs, C, S);
+            if (threadIdx.x == 0) rc = r;
+        });
+        if (rc || memcmp(C, c.data(), S)) bad++;
+        tg += cs;
+        to += ocs;
+        tin += S;
+    }
+    gpu_ratio = (double)tg / tin;
+    orc_ratio = (double)to / tin;
+    return bad;
+}
+
+int main()
+{
+    std::mt19937 rng(7);
+    int t = test_transpose(rng), g = test_granularity_bits(rng), s = test_shuffles(rng);
+    double gr0 = 0, gr1 = 0, orr = 0;
+    int l0 = test_lz4(rng, 0, gr0, orr);
+    int l1 = test_lz4(rng, 1, gr1, orr);
+    printf("transpose %d granularity %d shuffle %d lz4 %d %d ratio level0 %.4f level1 %.4f "
+           "oracle %.4f\n", t, g, s, l0, l1, gr0, gr1, orr);
+    return (t || g || s || l0 || l1) ? 1 : 0;
+}

@@ -143,11 +143,15 @@ def make(n, es, kind, seed):
     return rng.integers(0, 256, size=n * es, dtype=np.uint8).view(dt)
 
 
-@pytest.mark.parametrize("es,B,n,kind", CODEC)
-def test_compress_decodes_with_oracle(bs, orc, es, B, n, kind):
+CODEC_L = [(es, B, n, kind, 0) for (es, B, n, kind) in CODEC]
+CODEC_L += [(es, B, n, kind, 1) for (es, B, n, kind) in CODEC[::3]]
+
+
+@pytest.mark.parametrize("es,B,n,kind,level", CODEC_L)
+def test_compress_decodes_with_oracle(bs, orc, es, B, n, kind, level):
     a = make(n, es, kind, seed=n * 3 + es)
     d = to_dev(a)
-    c = bs.compress(d, B, elem_size=es)
+    c = bs.compress(d, B, elem_size=es, level=level)
     nbytes = c.nbytes
     assert bs.status(c.ws) == 0
     assert nbytes <= bs.compress_bound(n, es, B)
@@ -162,12 +166,20 @@ def test_compress_decodes_with_oracle(bs, orc, es, B, n, kind):
             assert offs[b] == pos
             pos += 4 + int.from_bytes(s[pos:pos + 4], "big")
     # deterministic: a second run writes the same bytes
-    c2 = bs.compress(d, B, elem_size=es)
+    c2 = bs.compress(d, B, elem_size=es, level=level)
     assert c2.nbytes == nbytes and torch.equal(c2.buf[:nbytes], c.buf[:nbytes])
-    # GPU decoder, with and without the index
-    for offs in (c.offsets if n >= 8 else None, None):
-        out = bs.decompress(c.buf, nbytes, n, es, B, offsets=offs)
-        assert np.array_equal(host_bytes(out), a.view(np.uint8))
+    # ... also into an output that does not start on a 16-byte boundary
+    raw = torch.zeros(c.buf.numel() + 16, dtype=torch.uint8, device="cuda")
+    c3 = bs.compress(d, B, elem_size=es, level=level, out=raw[5:5 + c.buf.numel()])
+    assert c3.nbytes == nbytes and torch.equal(raw[5:5 + nbytes], c.buf[:nbytes])
+    # GPU decoder, with and without the index, from an aligned and a
+    # misaligned copy of the stream
+    mis = torch.zeros(nbytes + 16, dtype=torch.uint8, device="cuda")
+    mis[3:3 + nbytes] = c.buf[:nbytes]
+    for src in (c.buf, mis[3:3 + nbytes]):
+        for offs in (c.offsets if n >= 8 else None, None):
+            out = bs.decompress(src, nbytes, n, es, B, offsets=offs)
+            assert np.array_equal(host_bytes(out), a.view(np.uint8))
     # GPU decoder on the oracle's stream
     o = orc.compress(a, B)
     od = torch.from_numpy(np.frombuffer(o, dtype=np.uint8).copy()).cuda()
@@ -194,13 +206,13 @@ def test_ratio_close_to_oracle(bs, orc):
 # -------------------------------------------------------- fused vis path --
 
 @pytest.mark.parametrize("name,cfg", VIS_CASES, ids=[c[0] for c in VIS_CASES])
-@pytest.mark.parametrize("B", [2048, 1024, 0])
-def test_compress_vis_matches_oracle(bs, orc, name, cfg, B):
+@pytest.mark.parametrize("B,level", [(2048, 0), (1024, 0), (0, 0), (2048, 1)])
+def test_compress_vis_matches_oracle(bs, orc, name, cfg, B, level):
     vis = synth.visibilities(cfg)
     rounded = orc.reduce_precision_c64(vis, cfg.n_samp, cfg.f)
     flat = rounded.view(np.float32).reshape(-1)
     d = torch.from_numpy(vis.copy()).cuda()
-    c = bs.compress_vis(d, cfg.n_samp, cfg.f, B)
+    c = bs.compress_vis(d, cfg.n_samp, cfg.f, B, level=level)
     assert bs.status(c.ws) == 0
     s = c.buf[:c.nbytes].cpu().numpy().tobytes()
     rc, back = orc.decompress(s, flat.size, np.float32, B)
@@ -209,7 +221,7 @@ def test_compress_vis_matches_oracle(bs, orc, name, cfg, B):
     assert np.array_equal(host_bytes(out), flat.view(np.uint8))
     # the fused stream equals compress() of the GPU-rounded cube
     rd = bs.reduce_precision_c64(d, cfg.n_samp, cfg.f)
-    c2 = bs.compress(rd.view(torch.float32).reshape(-1), B)
+    c2 = bs.compress(rd.view(torch.float32).reshape(-1), B, level=level)
     assert c2.nbytes == c.nbytes and torch.equal(c2.buf[:c.nbytes], c.buf[:c.nbytes])
 
 
