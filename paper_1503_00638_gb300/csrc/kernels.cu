@@ -204,6 +204,50 @@ BSG_D void reduce_run(const float2 *src, float2 *dst, uint32_t c0, uint32_t ncpl
     }
 }
 
+// Same for an even number of samples starting at an even index c0 when the
+// time axis is even: each lane takes two consecutive samples (t, t+1) of one
+// product per 16-byte access, so the product lookup and the two autos loads
+// serve both, and the auto / cross choice is a select (for an auto A_j = A_i,
+// the constant is 2c and the imaginary part is kept).
+BSG_D void reduce_run2(const float4 *src, float4 *dst, uint32_t c0, uint32_t ncplx,
+                       const VisParams &P, uint32_t lane)
+{
+    uint32_t c = c0 + 2 * lane;
+    uint32_t fp = c / P.T;
+    uint32_t t = c - fp * P.T;
+    uint32_t f = fp / P.P;
+    uint32_t p = fp - f * P.P;
+    const uint32_t q64 = 64 / P.T, r64 = 64 % P.T;
+    for (uint32_t k = lane; k < ncplx / 2; k += 32) {
+        const uint32_t ij = __ldg(P.pairs + p);
+        const uint32_t i = ij & 0xffffu, j = ij >> 16;
+        const uint32_t row = f * P.n_in;
+        const float2 Ai = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + i) * P.T + t));
+        const float2 Aj = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + j) * P.T + t));
+        const bool is_auto = i == j;
+        const float cc = is_auto ? P.c2 : P.c;
+        const float qa = __fmul_rn(__fmul_rn(cc, Ai.x), Aj.x);
+        const float qb = __fmul_rn(__fmul_rn(cc, Ai.y), Aj.y);
+        float4 v = src[k];
+        const float xi0 = reduce_one(v.y, qa), xi1 = reduce_one(v.w, qb);
+        v.x = reduce_one(v.x, qa);
+        v.z = reduce_one(v.z, qb);
+        v.y = is_auto ? v.y : xi0;
+        v.w = is_auto ? v.w : xi1;
+        dst[k] = v;
+        t += r64;
+        p += q64;
+        if (t >= P.T) {
+            t -= P.T;
+            p++;
+        }
+        while (p >= P.P) {
+            p -= P.P;
+            f++;
+        }
+    }
+}
+
 // Round the float at global float index fi (used for the verbatim tail).
 BSG_D float reduce_float_at(float x, uint64_t fi, const VisParams &P)
 {
@@ -261,7 +305,11 @@ __global__ void __launch_bounds__(256) reduce_precision_kernel(const float2 *__r
     constexpr uint32_t RUN = 1024;
     for (uint64_t r = warp * RUN; r < n_cplx; r += nwarps * RUN) {
         uint32_t cnt = (uint32_t)(n_cplx - r < RUN ? n_cplx - r : RUN);
-        reduce_run(in + r, out + r, (uint32_t)r, cnt, P, lane);
+        if ((P.T & 1u) == 0)  // r is even and so is cnt (n_cplx = F P T is even)
+            reduce_run2(reinterpret_cast<const float4 *>(in + r), reinterpret_cast<float4 *>(out + r),
+                        (uint32_t)r, cnt, P, lane);
+        else
+            reduce_run(in + r, out + r, (uint32_t)r, cnt, P, lane);
     }
 }
 
@@ -322,8 +370,14 @@ BSG_D void compress_tile(const CodecArgs &a, uint32_t tile, uint8_t *buf, uint8_
     const uint32_t S = Bb * a.es;
     if (a.vis.enabled) {
         // float index tile * B is even: whole complex samples
-        float2 *b2 = reinterpret_cast<float2 *>(buf);
-        reduce_run(b2, b2, (uint32_t)(((uint64_t)tile * a.B) >> 1), Bb / 2, a.vis, lane);
+        const uint32_t c0 = (uint32_t)(((uint64_t)tile * a.B) >> 1);
+        if ((a.vis.T & 1u) == 0) {  // c0 and Bb / 2 are even (Bb is a multiple of 8)
+            float4 *b4 = reinterpret_cast<float4 *>(buf);
+            reduce_run2(b4, b4, c0, Bb / 2, a.vis, lane);
+        } else {
+            float2 *b2 = reinterpret_cast<float2 *>(buf);
+            reduce_run(b2, b2, c0, Bb / 2, a.vis, lane);
+        }
         __syncwarp();
     }
     shuffle_block(buf, tmp, Bb, a.es, lane);

@@ -158,7 +158,9 @@ BSG_D uint32_t lz4_encode_warp(const uint8_t *src, uint32_t S, uint32_t rowlen, 
     if (rowlen & 3u) rowlen = 0;
     uint32_t anchor = 0, o = 0;
     if (S >= LZ4_MFLIMIT + 1) {
-        const uint32_t mflimit = S - LZ4_MFLIMIT;          // last allowed match start
+        // a probe at p verifies 8 bytes, so it must end by the match-end bound
+        // (p + 8 <= S - 5), which is also below the last allowed match start
+        const uint32_t mflimit = S - LZ4_LASTLITERALS - LZ4_GPU_MINMATCH;
         const uint32_t matchlimit = S - LZ4_LASTLITERALS;  // match end bound
         uint32_t pos = 0, fails = 0;
         const uint32_t guard = S / 4 + 8;

@@ -84,6 +84,15 @@ static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc
             rows.push_back((uint32_t)(S / 32));
         }
     }
+    // short low-entropy blocks: matches near the end-of-block limits
+    for (int t = 0; t < 150; t++) {
+        int S = 13 + (int)(rng() % 120);
+        std::vector<uint8_t> m(S);
+        int alpha = 1 + (int)(rng() % 3);
+        for (auto &x : m) x = (uint8_t)(rng() % alpha);
+        cases.push_back(m);
+        rows.push_back((uint32_t)(4 * (rng() % 8)));
+    }
     for (int t = 0; t < 4; t++) {
         std::vector<int32_t> w(2048);
         int32_t x = 0;
