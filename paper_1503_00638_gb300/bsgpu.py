@@ -233,3 +233,4 @@ def decompress(stream_buf: torch.Tensor, in_bytes: int, n_elem: int, elem_size: 
                                  block_elems, _ptr(offsets), _ptr(ws), ws.numel(),
                                  _stream(stream)), "bsgpu_decompress")
     return out
+

@@ -282,7 +282,7 @@ static int compress_common(const void *in, const Geometry &g, int level, void *o
         return BSGPU_ERR_CUDA;
     if (g.nb == 0) return cuda_err(launch_compress_small(a, s));
     uint32_t maxb = maxb_class(g.B * g.es);
-    uint32_t grid = persistent_grid(compress_smem_bytes(maxb), g.nb);
+    uint32_t grid = persistent_grid(compress_smem_bytes(maxb, level), g.nb);
     return cuda_err(launch_compress(a, maxb, grid, s));
 }
 

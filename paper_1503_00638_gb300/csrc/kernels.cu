@@ -20,24 +20,24 @@ __host__ __device__ constexpr uint32_t r128(uint32_t x) { return (x + 127u) & ~1
 __host__ __device__ constexpr uint32_t cmax(uint32_t a, uint32_t b) { return a > b ? a : b; }
 __host__ __device__ constexpr uint32_t lz4b(uint32_t n) { return n + n / 255u + 16u; }
 
-template <uint32_t MAXB>
+template <uint32_t MAXB, int LEVEL>
 struct CompPlan {
-    // LZ4 output with its 4-byte length field in front, plus read slack
-    static constexpr uint32_t CAP = r16(4 + lz4b(MAXB) + 48);
-    static constexpr uint32_t BUF = r128(cmax(CAP, MAXB + 32));
-    static constexpr uint32_t TMP = r128(MAXB + 32);
-    // one 16-bit entry per probed word position of the largest block
+    static constexpr uint32_t IN = r16(MAXB);          // staged block (bulk copy target)
+    static constexpr uint32_t TMP = r16(MAXB + 16);    // bit-rows (LZ4 input, read 8 past)
+    // LZ4 output with its 4-byte length field in front (write-out reads 16 past)
+    static constexpr uint32_t OUT = r16(4 + lz4b(MAXB) + 16);
+    // level 1: one 16-bit hash entry per probed word position of the largest block
     static constexpr int HBITS = MAXB <= 8192 ? 11 : (MAXB <= 16384 ? 12 : 13);
-    static constexpr uint32_t HASH = 2u << HBITS;
-    static constexpr uint32_t BYTES = 2 * BUF + TMP + HASH + 16;
+    static constexpr uint32_t HASH = LEVEL >= 1 ? (2u << HBITS) : 0u;
+    static constexpr uint32_t BYTES = IN + TMP + OUT + HASH + 16;
 };
 
 template <uint32_t MAXB>
 struct DecPlan {
-    static constexpr uint32_t CAPD = r16(16 + 4 + lz4b(MAXB) + 48);
-    static constexpr uint32_t BUF = r128(cmax(CAPD, MAXB + 32));
-    static constexpr uint32_t DEC = r128(MAXB + 32);
-    static constexpr uint32_t BYTES = 2 * BUF + DEC + 16;
+    // stream bytes of one block at their 16-byte phase, read 8 past the end
+    static constexpr uint32_t COMP = r16(16 + 4 + lz4b(MAXB) + 16);
+    static constexpr uint32_t DEC = r16(MAXB + 16);
+    static constexpr uint32_t BYTES = COMP + DEC + 16;
 };
 
 template <uint32_t MAXB>
@@ -46,10 +46,13 @@ struct ShufPlan {
     static constexpr uint32_t BYTES = 3 * BUF + 16;
 };
 
-uint32_t compress_smem_bytes(uint32_t maxb)
+uint32_t compress_smem_bytes(uint32_t maxb, int level)
 {
-    return maxb <= 8192 ? CompPlan<8192>::BYTES
-                        : (maxb <= 16384 ? CompPlan<16384>::BYTES : CompPlan<65536>::BYTES);
+    if (level >= 1)
+        return maxb <= 8192 ? CompPlan<8192, 1>::BYTES
+                            : (maxb <= 16384 ? CompPlan<16384, 1>::BYTES : CompPlan<65536, 1>::BYTES);
+    return maxb <= 8192 ? CompPlan<8192, 0>::BYTES
+                        : (maxb <= 16384 ? CompPlan<16384, 0>::BYTES : CompPlan<65536, 0>::BYTES);
 }
 uint32_t decompress_smem_bytes(uint32_t maxb)
 {
@@ -248,6 +251,67 @@ BSG_D void reduce_run2(const float4 *src, float4 *dst, uint32_t c0, uint32_t ncp
     }
 }
 
+// Precision reduction fused into the 32 x 32 register transpose of a block of
+// float32 components (elem size 4), for cubes whose time axis is a multiple
+// of 16: a group of 32 floats is 16 consecutive time samples of one product,
+// so one product lookup and 16 autos pairs serve the whole group.  Lane k of
+// the warp takes groups k, k + 32, ...; its 16-byte chunks are read in a
+// lane-rotated order (conflict-free banks) and the autos are loaded in the
+// same order; the rotation is undone on the transposed rows.
+BSG_D void round_shuffle4_vis(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t c_blk,
+                              const VisParams &P, uint32_t lane)
+{
+    const uint32_t G = Bb / 32;
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t g = lane; g < G; g += 32) {
+        const uint8_t *grp = src + 128u * g;
+        const uint32_t rot = g & 7u;
+        const uint32_t cg = c_blk + 16 * g;       // first sample of the group
+        const uint32_t fp = cg / P.T;
+        const uint32_t t0 = cg - fp * P.T;
+        const uint32_t f = fp / P.P;
+        const uint32_t p = fp - f * P.P;
+        const uint32_t ij = __ldg(P.pairs + p);
+        const uint32_t i = ij & 0xffffu, j = ij >> 16;
+        const bool is_auto = i == j;
+        const float cc = is_auto ? P.c2 : P.c;
+        const float *ai = P.autos + (size_t)(f * P.n_in + i) * P.T + t0;
+        const float *aj = P.autos + (size_t)(f * P.n_in + j) * P.T + t0;
+        uint32_t a[32];
+        float2 Ai[8], Aj[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t c = (k + rot) & 7u;  // chunk c holds samples t0 + 2c, t0 + 2c + 1
+            uint4 v = *reinterpret_cast<const uint4 *>(grp + 16u * c);
+            a[4 * k] = v.x;
+            a[4 * k + 1] = v.y;
+            a[4 * k + 2] = v.z;
+            a[4 * k + 3] = v.w;
+            Ai[k] = __ldg(reinterpret_cast<const float2 *>(ai + 2 * c));
+            Aj[k] = __ldg(reinterpret_cast<const float2 *>(aj + 2 * c));
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const float q0 = __fmul_rn(__fmul_rn(cc, Ai[k].x), Aj[k].x);
+            const float q1 = __fmul_rn(__fmul_rn(cc, Ai[k].y), Aj[k].y);
+            const float re0 = reduce_one(__uint_as_float(a[4 * k]), q0);
+            const float im0 = reduce_one(__uint_as_float(a[4 * k + 1]), q0);
+            const float re1 = reduce_one(__uint_as_float(a[4 * k + 2]), q1);
+            const float im1 = reduce_one(__uint_as_float(a[4 * k + 3]), q1);
+            a[4 * k] = __float_as_uint(re0);
+            a[4 * k + 2] = __float_as_uint(re1);
+            if (!is_auto) {
+                a[4 * k + 1] = __float_as_uint(im0);
+                a[4 * k + 3] = __float_as_uint(im1);
+            }
+        }
+        // a[m] holds float (m + 4 rot) mod 32 of the group
+        transpose32(a);
+#pragma unroll
+        for (int r = 0; r < 32; r++) d32[r * G + g] = rotl(a[r], 4u * rot);
+    }
+}
+
 // Round the float at global float index fi (used for the verbatim tail).
 BSG_D float reduce_float_at(float x, uint64_t fi, const VisParams &P)
 {
@@ -361,35 +425,47 @@ BSG_D uint64_t lookback(uint64_t *state, uint32_t tile, uint64_t agg, int *statu
 // ---------------------------------------------------------------------------
 // Compress: [round ->] bitshuffle -> LZ4 -> placed by look-back
 // ---------------------------------------------------------------------------
-template <uint32_t MAXB>
-BSG_D void compress_tile(const CodecArgs &a, uint32_t tile, uint8_t *buf, uint8_t *tmp,
-                         uint16_t *table, uint32_t lane)
+// Round (for a cube) and bit-transpose block `tile` from `in` into `tmp`.
+BSG_D void compress_prepare(const CodecArgs &a, uint32_t tile, uint8_t *in, uint8_t *tmp,
+                            uint32_t lane)
 {
-    using L = CompPlan<MAXB>;
     const uint32_t Bb = block_elems_of(a, tile);
-    const uint32_t S = Bb * a.es;
+    // float index tile * B is even: whole complex samples
+    const uint32_t c0 = (uint32_t)(((uint64_t)tile * a.B) >> 1);
+    if (a.vis.enabled && Bb % 32u == 0 && a.vis.T % 16u == 0) {
+        round_shuffle4_vis(in, tmp, Bb, c0, a.vis, lane);
+        return;
+    }
     if (a.vis.enabled) {
-        // float index tile * B is even: whole complex samples
-        const uint32_t c0 = (uint32_t)(((uint64_t)tile * a.B) >> 1);
         if ((a.vis.T & 1u) == 0) {  // c0 and Bb / 2 are even (Bb is a multiple of 8)
-            float4 *b4 = reinterpret_cast<float4 *>(buf);
+            float4 *b4 = reinterpret_cast<float4 *>(in);
             reduce_run2(b4, b4, c0, Bb / 2, a.vis, lane);
         } else {
-            float2 *b2 = reinterpret_cast<float2 *>(buf);
+            float2 *b2 = reinterpret_cast<float2 *>(in);
             reduce_run(b2, b2, c0, Bb / 2, a.vis, lane);
         }
         __syncwarp();
     }
-    shuffle_block(buf, tmp, Bb, a.es, lane);
-    __syncwarp();
+    shuffle_block(in, tmp, Bb, a.es, lane);
+}
+
+// LZ4-encode the bit-rows in `tmp` into `out`, place the block by look-back
+// and write it (plus the header, the index entry and, for the last block, the
+// verbatim tail).
+template <uint32_t MAXB, int LEVEL>
+BSG_D void compress_finish(const CodecArgs &a, uint32_t tile, uint8_t *tmp, uint8_t *out,
+                           uint16_t *table, uint32_t lane)
+{
+    using L = CompPlan<MAXB, LEVEL>;
+    const uint32_t Bb = block_elems_of(a, tile);
+    const uint32_t S = Bb * a.es;
     // bit-rows are Bb/8 bytes long: the previous row is one of the candidates
-    uint32_t cs = a.level >= 1 ? lz4_encode_warp<1, L::HBITS>(tmp, S, Bb / 8, buf + 4, table)
-                               : lz4_encode_warp<0, L::HBITS>(tmp, S, Bb / 8, buf + 4, table);
+    uint32_t cs = lz4_encode_warp<LEVEL, L::HBITS>(tmp, S, Bb / 8, out + 4, table);
     if (cs == 0xffffffffu) {  // progress guard (not reachable for valid sizes)
         if (lane == 0) set_status(a.status, BSGPU_ERR_CUDA);
         cs = 0;
     }
-    if (lane == 0) put_be32(buf, cs);
+    if (lane == 0) put_be32(out, cs);
     __syncwarp();
     const uint64_t excl = lookback(a.tile_state, tile, 4ull + cs, a.status, lane);
     const uint64_t D = 12 + excl;
@@ -397,7 +473,7 @@ BSG_D void compress_tile(const CodecArgs &a, uint32_t tile, uint8_t *buf, uint8_
         if (lane == 0) set_status(a.status, BSGPU_ERR_SPACE);
         return;
     }
-    copy_out(buf, a.out + D, 4 + cs, lane);
+    copy_out(out, a.out + D, 4 + cs, lane);
     if (a.block_offsets && lane == 0) a.block_offsets[tile] = D;
     if (tile == 0) write_chunk_header(a.out, a.n_elem * a.es, a.B * a.es, lane);
     if (tile + 1 == a.nb) {
@@ -423,48 +499,50 @@ BSG_D void compress_tile(const CodecArgs &a, uint32_t tile, uint8_t *buf, uint8_
     }
 }
 
-template <uint32_t MAXB>
-__global__ void __launch_bounds__(32) compress_kernel(const __grid_constant__ CodecArgs a)
+// One warp per CTA, persistent.  Per block: wait for its bulk copy into `in`,
+// round + transpose into `tmp`, start the next block's copy into `in`, then
+// LZ4 into `out`, look-back placement and the write-out, which overlap the
+// next block's copy.
+template <uint32_t MAXB, int LEVEL>
+__global__ void __launch_bounds__(32, MAXB <= 8192 ? 9 : 1)
+    compress_kernel(const __grid_constant__ CodecArgs a)
 {
-    using L = CompPlan<MAXB>;
+    using L = CompPlan<MAXB, LEVEL>;
     extern __shared__ __align__(128) uint8_t sm[];
-    uint8_t *buf[2] = {sm, sm + L::BUF};
-    uint8_t *tmp = sm + 2 * L::BUF;
-    uint16_t *table = reinterpret_cast<uint16_t *>(tmp + L::TMP);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(table) + L::HASH);
+    uint8_t *in = sm;
+    uint8_t *tmp = sm + L::IN;
+    uint8_t *out = tmp + L::TMP;
+    uint16_t *table = reinterpret_cast<uint16_t *>(out + L::OUT);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(out + L::OUT + L::HASH);
     const uint32_t lane = threadIdx.x & 31u;
     if (lane == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncwarp();
-    uint32_t parity = 0, pend = 0;  // bit c: phase / load in flight of buffer c
+    uint32_t parity = 0;
     uint32_t tile = grab_tile(a.tile_counter, lane);
-    if (tile < a.nb && load_block(buf[0], a.in + (uint64_t)tile * a.B * a.es,
-                                  block_elems_of(a, tile) * a.es, &bar[0], lane))
-        pend |= 1u;
-    uint32_t cur = 0;
+    bool pend = tile < a.nb && load_block(in, a.in + (uint64_t)tile * a.B * a.es,
+                                          block_elems_of(a, tile) * a.es, bar, lane);
     while (tile < a.nb) {
-        const uint32_t nxt = grab_tile(a.tile_counter, lane);
-        if (pend & (1u << cur)) {
-            if (!mbar_wait_bounded(&bar[cur], (parity >> cur) & 1u) && lane == 0)
-                set_status(a.status, BSGPU_ERR_TIMEOUT);
-            parity ^= 1u << cur;
-            pend &= ~(1u << cur);
+        if (pend) {
+            if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);
+            parity ^= 1u;
         }
+        compress_prepare(a, tile, in, tmp, lane);
+        __syncwarp();
+        const uint32_t nxt = grab_tile(a.tile_counter, lane);
+        pend = false;
         if (nxt < a.nb) {
-            // the other buffer's last reads (generic proxy) precede the async write
+            // the transpose's reads of `in` (generic proxy) precede the async write
             fence_proxy_async_smem();
             __syncwarp();
-            if (load_block(buf[cur ^ 1], a.in + (uint64_t)nxt * a.B * a.es,
-                           block_elems_of(a, nxt) * a.es, &bar[cur ^ 1], lane))
-                pend |= 1u << (cur ^ 1);
+            pend = load_block(in, a.in + (uint64_t)nxt * a.B * a.es, block_elems_of(a, nxt) * a.es,
+                              bar, lane);
         }
-        compress_tile<MAXB>(a, tile, buf[cur], tmp, table, lane);
+        compress_finish<MAXB, LEVEL>(a, tile, tmp, out, table, lane);
         __syncwarp();
         tile = nxt;
-        cur ^= 1;
     }
 }
 
@@ -489,6 +567,7 @@ __global__ void compress_small_kernel(const __grid_constant__ CodecArgs a)
 // ---------------------------------------------------------------------------
 // Decompress: LZ4 decode -> bit un-transpose, every block at once
 // ---------------------------------------------------------------------------
+
 struct DecLoad {
     bool bulk;       // a bulk copy is in flight on the barrier
     bool ok;         // offsets passed the range checks
@@ -542,44 +621,36 @@ BSG_D DecLoad dec_issue(const CodecArgs &a, uint32_t tile, uint8_t *dst, uint64_
     return r;
 }
 
+// One warp per CTA, persistent.  Per block: wait for its stream bytes in
+// `comp`, LZ4-decode into `dec`, start the next block's copy into `comp`,
+// un-transpose `dec` in place and bulk-store it (blocks the register paths
+// cannot take are un-transposed into `comp` and stored before the next copy).
 template <uint32_t MAXB>
-__global__ void __launch_bounds__(32) decompress_kernel(const __grid_constant__ CodecArgs a)
+__global__ void __launch_bounds__(32, MAXB <= 8192 ? 12 : 1)
+    decompress_kernel(const __grid_constant__ CodecArgs a)
 {
     using L = DecPlan<MAXB>;
     extern __shared__ __align__(128) uint8_t sm[];
-    uint8_t *buf[2] = {sm, sm + L::BUF};
-    uint8_t *dec = sm + 2 * L::BUF;
+    uint8_t *comp = sm;
+    uint8_t *dec = sm + L::COMP;
     uint64_t *bar = reinterpret_cast<uint64_t *>(dec + L::DEC);
     const uint32_t lane = threadIdx.x & 31u;
     if (lane == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncwarp();
-    uint32_t parity[2] = {0u, 0u};
+    uint32_t parity = 0;
     bool header_checked = false;
     uint32_t tile = grab_tile(a.tile_counter, lane);
-    DecLoad ld[2];
-    int cur = 0;
-    if (tile < a.nb) ld[0] = dec_issue(a, tile, buf[0], &bar[0], lane);
+    DecLoad ld;
+    if (tile < a.nb) ld = dec_issue(a, tile, comp, bar, lane);
     while (tile < a.nb) {
-        const uint32_t nxt = grab_tile(a.tile_counter, lane);
-        DecLoad L0 = cur ? ld[1] : ld[0];
-        if (L0.bulk) {
-            if (!mbar_wait_bounded(&bar[cur], parity[cur]) && lane == 0)
-                set_status(a.status, BSGPU_ERR_TIMEOUT);
-            parity[cur] ^= 1u;
+        const DecLoad cur = ld;
+        if (cur.bulk) {
+            if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);
+            parity ^= 1u;
         }
-        if (nxt < a.nb) {
-            // the other buffer last fed a bulk store; let it finish reading
-            if (lane == 0) bulk_wait_read0();
-            __syncwarp();
-            fence_proxy_async_smem();
-            DecLoad n = dec_issue(a, nxt, buf[cur ^ 1], &bar[cur ^ 1], lane);
-            if (cur) ld[0] = n; else ld[1] = n;
-        }
-        uint8_t *cb = buf[cur];
         if (!header_checked) {
             header_checked = true;
             uint32_t ok = 1;
@@ -592,28 +663,49 @@ __global__ void __launch_bounds__(32) decompress_kernel(const __grid_constant__ 
         }
         const uint32_t Bb = block_elems_of(a, tile);
         const uint32_t S = Bb * a.es;
-        bool good = L0.ok;
+        const uint32_t nxt = grab_tile(a.tile_counter, lane);
+        // the previous block's bulk store must have finished reading `dec`
+        if (lane == 0) bulk_wait_read0();
+        __syncwarp();
+        bool good = cur.ok;
         if (good) {
-            if (L0.eidx != ~0u) cb[L0.eidx] = L0.ebyte;
+            if (cur.eidx != ~0u) comp[cur.eidx] = cur.ebyte;
             __syncwarp();
-            good = get_be32(cb + L0.delta) == L0.clen &&
-                   lz4_decode_warp(cb, L0.delta + 4, L0.clen, dec, S) == 0;
+            good = get_be32(comp + cur.delta) == cur.clen &&
+                   lz4_decode_warp(comp, cur.delta + 4, cur.clen, dec, S) == 0;
         }
-        if (!good) {
-            if (lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);
-        } else {
-            unshuffle_block(dec, cb, Bb, a.es, lane);
+        if (!good && lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);
+        uint8_t *dst = a.out + (uint64_t)tile * a.B * a.es;
+        const bool inplace = MAXB <= 8192 && unshuffle_inplace_ok(a.es, Bb);
+        if (good && !inplace) {
+            unshuffle_block(dec, comp, Bb, a.es, lane);
             __syncwarp();
-            uint8_t *dst = a.out + (uint64_t)tile * a.B * a.es;
+            for (uint32_t k = lane; k < S; k += 32) dst[k] = comp[k];
+        }
+        __syncwarp();
+        ld.bulk = false;
+        ld.ok = false;
+        if (nxt < a.nb) {
+            // `comp` was last read by the generic proxy
+            fence_proxy_async_smem();
+            __syncwarp();
+            ld = dec_issue(a, nxt, comp, bar, lane);
+        }
+        if (good && inplace) {
+            if (a.es == 4)
+                unshuffle4_inplace<2>(dec, Bb, lane);
+            else
+                unshuffle8_inplace(dec, Bb, lane);
+            __syncwarp();
             if ((S & 15u) == 0 && ((uintptr_t)dst & 15u) == 0) {
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    bulk_s2g(dst, cb, S);
+                    bulk_s2g(dst, dec, S);
                     bulk_commit();
                 }
             } else {
-                for (uint32_t k = lane; k < S; k += 32) dst[k] = cb[k];
+                for (uint32_t k = lane; k < S; k += 32) dst[k] = dec[k];
             }
         }
         if (tile + 1 == a.nb) {
@@ -625,7 +717,6 @@ __global__ void __launch_bounds__(32) decompress_kernel(const __grid_constant__ 
         }
         __syncwarp();
         tile = nxt;
-        cur ^= 1;
     }
     if (lane == 0) bulk_wait0();
     __syncwarp();
@@ -800,10 +891,15 @@ cudaError_t launch_shuffle(const CodecArgs &a, bool inverse, uint32_t maxb, uint
 
 cudaError_t launch_compress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s)
 {
-    uint32_t smem = compress_smem_bytes(maxb);
-    if (maxb <= 8192) return launch_warp_kernel(compress_kernel<8192>, smem, grid, s, a);
-    if (maxb <= 16384) return launch_warp_kernel(compress_kernel<16384>, smem, grid, s, a);
-    return launch_warp_kernel(compress_kernel<65536>, smem, grid, s, a);
+    uint32_t smem = compress_smem_bytes(maxb, a.level);
+    if (a.level >= 1) {
+        if (maxb <= 8192) return launch_warp_kernel(compress_kernel<8192, 1>, smem, grid, s, a);
+        if (maxb <= 16384) return launch_warp_kernel(compress_kernel<16384, 1>, smem, grid, s, a);
+        return launch_warp_kernel(compress_kernel<65536, 1>, smem, grid, s, a);
+    }
+    if (maxb <= 8192) return launch_warp_kernel(compress_kernel<8192, 0>, smem, grid, s, a);
+    if (maxb <= 16384) return launch_warp_kernel(compress_kernel<16384, 0>, smem, grid, s, a);
+    return launch_warp_kernel(compress_kernel<65536, 0>, smem, grid, s, a);
 }
 
 cudaError_t launch_compress_small(const CodecArgs &a, cudaStream_t s)

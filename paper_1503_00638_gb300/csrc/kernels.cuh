@@ -35,7 +35,7 @@ struct CodecArgs {
 };
 
 // Shared-memory bytes per warp-CTA for each kernel family and block-size class.
-uint32_t compress_smem_bytes(uint32_t maxb);
+uint32_t compress_smem_bytes(uint32_t maxb, int level);
 uint32_t decompress_smem_bytes(uint32_t maxb);
 uint32_t shuffle_smem_bytes(uint32_t maxb);
 

@@ -171,4 +171,71 @@ BSG_HD void unshuffle_block(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint3
         unshuffle_generic(src, dst, Bb, es, lane);
 }
 
+#if defined(__CUDACC__) || defined(BSG_WARP_EMU)
+// Un-transpose a block of 4-byte elements in place (buf holds 32 bit-rows of
+// Bb/8 bytes; afterwards the Bb elements): every lane first reads all of its
+// groups (at most NG) into registers, then writes them back.
+template <int NG>
+BSG_D void unshuffle4_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t G = Bb / 32;
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(buf);
+    uint32_t a[NG][32];
+#pragma unroll
+    for (int q = 0; q < NG; q++) {
+        const uint32_t g = lane + 32u * q;
+        if (g < G) {
+#pragma unroll
+            for (int r = 0; r < 32; r++) a[q][r] = rotr(s32[r * G + g], 4u * (g & 7u));
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < NG; q++) {
+        const uint32_t g = lane + 32u * q;
+        if (g < G) {
+            transpose32(a[q]);  // a[q][m] holds element (m + 4 rot) mod 32
+            const uint32_t rot = g & 7u;
+            uint8_t *grp = buf + 128u * g;
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                *reinterpret_cast<uint4 *>(grp + 16u * ((k + rot) & 7u)) =
+                    make_uint4(a[q][4 * k], a[q][4 * k + 1], a[q][4 * k + 2], a[q][4 * k + 3]);
+        }
+    }
+}
+
+// Same for 8-byte elements and at most 32 groups (one per lane).
+BSG_D void unshuffle8_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t G = Bb / 32;
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(buf);
+    const uint32_t g = lane, rot = g & 15u;
+    uint32_t lo[32], hi[32];
+    if (g < G) {
+#pragma unroll
+        for (int r = 0; r < 32; r++) {
+            lo[r] = rotr(s32[r * G + g], 2u * rot);
+            hi[r] = rotr(s32[(32 + r) * G + g], 2u * rot);
+        }
+    }
+    __syncwarp();
+    if (g < G) {
+        transpose32(lo);
+        transpose32(hi);
+        uint8_t *grp = buf + 256u * g;
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            *reinterpret_cast<uint4 *>(grp + 16u * ((k + rot) & 15u)) =
+                make_uint4(lo[2 * k], hi[2 * k], lo[2 * k + 1], hi[2 * k + 1]);
+    }
+}
+
+// Whether a block can be un-transposed in place by the register paths above.
+BSG_D bool unshuffle_inplace_ok(uint32_t es, uint32_t Bb)
+{
+    return Bb % 32u == 0 && ((es == 4 && Bb <= 2048) || (es == 8 && Bb <= 1024));
+}
+#endif  // __CUDACC__ || BSG_WARP_EMU
+
 }  // namespace bsg

@@ -70,6 +70,28 @@ static int test_shuffles(std::mt19937 &rng)
     return bad;
 }
 
+static int test_inplace_unshuffle(std::mt19937 &rng)
+{
+    int bad = 0;
+    for (int es : {4, 8})
+        for (int B : {32, 64, 96, 512, 1024, 2048}) {
+            if (!unshuffle_inplace_ok(es, B)) continue;
+            size_t S = (size_t)B * es;
+            for (size_t i = 0; i < S; i++) A[i] = (uint8_t)rng();
+            std::vector<uint8_t> rows(S);
+            orc_bitshuffle(A, rows.data(), B, es, B, 0);
+            memcpy(C, rows.data(), S);
+            run_warp([&] {
+                if (es == 4)
+                    unshuffle4_inplace<2>(C, B, threadIdx.x);
+                else
+                    unshuffle8_inplace(C, B, threadIdx.x);
+            });
+            bad += memcmp(A, C, S) != 0;
+        }
+    return bad;
+}
+
 static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc_ratio)
 {
     int bad = 0;
@@ -153,6 +175,7 @@ int main()
 {
     std::mt19937 rng(7);
     int t = test_transpose(rng), g = test_granularity_bits(rng), s = test_shuffles(rng);
+    s += test_inplace_unshuffle(rng);
     double gr0 = 0, gr1 = 0, orr = 0;
     int l0 = test_lz4(rng, 0, gr0, orr);
     int l1 = test_lz4(rng, 1, gr1, orr);
