@@ -162,6 +162,31 @@ int bsgpu_compress_vis(const void *vis, int64_t n_freq, int64_t n_inputs, int64_
                        uint64_t *d_out_bytes, uint64_t *d_block_offsets, void *ws,
                        size_t ws_bytes, void *stream);
 
+/* bsgpu_compress for callers that cannot allocate device memory (the paper
+ * has no counterpart: this is a deployment variant).  Such callers are handed
+ * buffers but may not allocate: a filter callback of an I/O library receives
+ * only the chunk's input and output buffers; a real-time acquisition loop
+ * allocates everything at start-up and must not call cudaMalloc afterwards,
+ * since it synchronizes the device; a process whose device memory is wholly
+ * owned by a pool.
+ *   Arguments and output as for bsgpu_compress, without the workspace.  The
+ *   scratch (status word, tile counter, 8 bytes of look-back state per block)
+ *   lives in a fixed array inside the library of 256 + 8 * 131072 bytes
+ *   (about 1 MiB), held by every device that loads the library until the
+ *   process exits; inputs of more than 131072 blocks (1 GiB at 8 KiB blocks)
+ *   are rejected with BSGPU_ERR_SPACE before anything is enqueued.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any
+ *   stream capture.  No call allocates or frees memory.
+ *   Every call shares the one array: calls that overlap on the GPU (on
+ *   different streams, or from different threads) race and corrupt each
+ *   other's output; serialize them.
+ *   A device-side failure (a bounded wait that ran out) is reported by
+ *   writing 0 to *d_out_bytes (a valid stream is at least 12 bytes long). */
+int bsgpu_compress_noalloc(const void *in, size_t n_elem, size_t elem_size, size_t block_elems,
+                           int level, void *out, size_t out_cap, uint64_t *d_out_bytes,
+                           uint64_t *d_block_offsets, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,7 @@ _SIGS = {
     "bsgpu_decompress": ([_vp, _sz, _vp, _sz, _sz, _sz, _vp, _vp, _sz, _vp], _i),
     "bsgpu_compress_vis": ([_vp, _i64, _i64, _i64, _d, _d, _sz, _i, _vp, _sz, _vp, _vp, _vp,
                             _sz, _vp], _i),
+    "bsgpu_compress_noalloc": ([_vp, _sz, _sz, _sz, _i, _vp, _sz, _vp, _vp, _vp], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -234,3 +235,22 @@ def decompress(stream_buf: torch.Tensor, in_bytes: int, n_elem: int, elem_size: 
                                  _stream(stream)), "bsgpu_decompress")
     return out
 
+
+def compress_noalloc(x: torch.Tensor, block_elems: int = 0, elem_size: int | None = None,
+                     out: torch.Tensor | None = None, nbytes_dev: torch.Tensor | None = None,
+                     offsets: torch.Tensor | None = None, stream=None, level: int = 0):
+    """bsgpu_compress_noalloc: compress with the library's own fixed scratch
+    (for callers that cannot allocate).  Returns (out, nbytes_dev, offsets);
+    the caller may pass all three preallocated."""
+    es = elem_size or x.element_size()
+    n = x.numel() * x.element_size() // es
+    cap = compress_bound(n, es, block_elems)
+    if cap == 0:
+        raise BsgpuError(ERR_ARG, "bsgpu_compress_bound")
+    out = torch.empty(cap, dtype=torch.uint8, device=x.device) if out is None else out
+    if nbytes_dev is None:
+        nbytes_dev = torch.zeros(1, dtype=torch.int64, device=x.device)
+    _check(_lib.bsgpu_compress_noalloc(_ptr(x), n, es, block_elems, level, _ptr(out), out.numel(),
+                                       _ptr(nbytes_dev), _ptr(offsets), _stream(stream)),
+           "bsgpu_compress_noalloc")
+    return out, nbytes_dev, offsets
