@@ -26,10 +26,11 @@ struct CompPlan {
     static constexpr uint32_t TMP = r16(MAXB + 16);    // bit-rows (LZ4 input, read 8 past)
     // LZ4 output with its 4-byte length field in front (write-out reads 16 past)
     static constexpr uint32_t OUT = r16(4 + lz4b(MAXB) + 16);
-    // level 1: one 16-bit hash entry per probed word position of the largest block
+    // level 1: one 16-bit hash entry per probed word position of the largest
+    // block; level 0: two word-equality bitmaps
     static constexpr int HBITS = MAXB <= 8192 ? 11 : (MAXB <= 16384 ? 12 : 13);
-    static constexpr uint32_t HASH = LEVEL >= 1 ? (2u << HBITS) : 0u;
-    static constexpr uint32_t BYTES = IN + TMP + OUT + HASH + 16;
+    static constexpr uint32_t SCR = LEVEL >= 1 ? (2u << HBITS) : 2u * 4u * (MAXB / 128u + 2u);
+    static constexpr uint32_t BYTES = IN + TMP + OUT + r16(SCR) + 16;
 };
 
 template <uint32_t MAXB>
@@ -404,11 +405,13 @@ BSG_D uint64_t lookback(uint64_t *state, uint32_t tile, uint64_t agg, int *statu
         uint32_t first = pm ? (uint32_t)(__ffs(pm) - 1) : 31u;
         uint32_t need = first >= 31 ? FULL : ((2u << first) - 1u);
         if (im & need) {
+            // predecessors usually publish within a few polls (each poll is a
+            // round trip to L2); sleep only once the wait is clearly long
             if (++spins > (1u << 21)) {
                 if (lane == 0) set_status(status, BSGPU_ERR_TIMEOUT);
                 break;
             }
-            __nanosleep(40);
+            if (spins > 4096) __nanosleep(100);
             continue;
         }
         uint64_t x = lane <= first ? (v & VM) : 0;
@@ -454,13 +457,15 @@ BSG_D void compress_prepare(const CodecArgs &a, uint32_t tile, uint8_t *in, uint
 // verbatim tail).
 template <uint32_t MAXB, int LEVEL>
 BSG_D void compress_finish(const CodecArgs &a, uint32_t tile, uint8_t *tmp, uint8_t *out,
-                           uint16_t *table, uint32_t lane)
+                           void *scratch, uint32_t lane)
 {
     using L = CompPlan<MAXB, LEVEL>;
     const uint32_t Bb = block_elems_of(a, tile);
     const uint32_t S = Bb * a.es;
     // bit-rows are Bb/8 bytes long: the previous row is one of the candidates
-    uint32_t cs = lz4_encode_warp<LEVEL, L::HBITS>(tmp, S, Bb / 8, out + 4, table);
+    uint32_t cs = LEVEL >= 1
+        ? lz4_encode_warp<1, L::HBITS>(tmp, S, Bb / 8, out + 4, static_cast<uint16_t *>(scratch))
+        : lz4_encode_bitmap(tmp, S, Bb / 8, out + 4, static_cast<uint32_t *>(scratch));
     if (cs == 0xffffffffu) {  // progress guard (not reachable for valid sizes)
         if (lane == 0) set_status(a.status, BSGPU_ERR_CUDA);
         cs = 0;
@@ -512,8 +517,8 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 9 : 1)
     uint8_t *in = sm;
     uint8_t *tmp = sm + L::IN;
     uint8_t *out = tmp + L::TMP;
-    uint16_t *table = reinterpret_cast<uint16_t *>(out + L::OUT);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(out + L::OUT + L::HASH);
+    void *scratch = out + L::OUT;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(out + L::OUT + r16(L::SCR));
     const uint32_t lane = threadIdx.x & 31u;
     if (lane == 0) {
         mbar_init(bar, 1);
@@ -540,7 +545,7 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 9 : 1)
             pend = load_block(in, a.in + (uint64_t)nxt * a.B * a.es, block_elems_of(a, nxt) * a.es,
                               bar, lane);
         }
-        compress_finish<MAXB, LEVEL>(a, tile, tmp, out, table, lane);
+        compress_finish<MAXB, LEVEL>(a, tile, tmp, out, scratch, lane);
         __syncwarp();
         tile = nxt;
     }

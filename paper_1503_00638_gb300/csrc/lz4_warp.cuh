@@ -84,6 +84,37 @@ BSG_D void warp_fill(uint8_t *dst, uint32_t d, uint32_t b, uint32_t len, uint32_
     for (uint32_t w = (a0 >> 2) + lane; w < (a1 >> 2); w += 32) d32[w] = v;
 }
 
+// Warp fill of len bytes at dst[d..] repeating the off bytes before d, for
+// off in {1, 2, 4} (so the pattern repeats within every aligned word).
+BSG_D void warp_fill_pattern(uint8_t *dst, uint32_t d, uint32_t off, uint32_t len, uint32_t lane)
+{
+#ifdef BSG_WARP_EMU
+    emu_check_aligned4(dst);
+#endif
+    // byte i of the output is dst[d - off + i % off]
+    if (len <= 32) {
+        const uint8_t v = dst[d - off + (lane & (off - 1))];
+        __syncwarp();
+        if (lane < len) dst[d + lane] = v;
+        return;
+    }
+    const uint32_t a0 = (d + 3u) & ~3u, a1 = (d + len) & ~3u;
+    const uint32_t head = a0 - d, tail = d + len - a1;
+    // the aligned word at a0 starts with output byte (a0 - d), i.e. pattern
+    // byte (a0 - d) % off; the word is the same at every aligned address
+    uint32_t word = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < 4; k++) word |= (uint32_t)dst[d - off + ((head + k) & (off - 1))] << (8 * k);
+    uint8_t hv = 0, tv = 0;
+    if (lane < head) hv = dst[d - off + (lane & (off - 1))];
+    if (lane >= 28 && lane - 28 < tail) tv = dst[d - off + ((a1 - d + lane - 28) & (off - 1))];
+    __syncwarp();
+    if (lane < head) dst[d + lane] = hv;
+    if (lane >= 28 && lane - 28 < tail) dst[a1 + lane - 28] = tv;
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t w = (a0 >> 2) + lane; w < (a1 >> 2); w += 32) d32[w] = word;
+}
+
 // Length bytes of an LZ4 field: v >= 15 is 15 in the nibble, then
 // (v - 15) / 255 bytes of 255 and one byte of (v - 15) % 255.
 BSG_D uint32_t lz4_ext_count(uint32_t v) { return v >= 15 ? (v - 15) / 255 + 1 : 0; }
@@ -248,6 +279,133 @@ BSG_D uint32_t lz4_encode_warp(const uint8_t *src, uint32_t S, uint32_t rowlen, 
     return o;
 }
 
+// Smallest word index w >= start with bit w of the bitmap E clear, or cap if
+// none is below cap.  E has a clear bit at or before every index it covers.
+BSG_D uint32_t bitmap_first_zero(const uint32_t *E, uint32_t start, uint32_t cap, uint32_t lane)
+{
+    if (start >= cap) return cap;
+    for (uint32_t qb = start >> 5; qb * 32 < cap; qb += 32) {
+        const uint32_t q = qb + lane;
+        uint32_t z = 0;
+        if (q * 32 < cap) {
+            z = ~E[q];
+            if (q == (start >> 5)) z &= ~0u << (start & 31u);
+        }
+        const uint32_t m = __ballot_sync(FULL, z != 0);
+        if (m) {
+            const uint32_t fl = __ffs(m) - 1;
+            const uint32_t zz = __shfl_sync(FULL, z, fl);
+            const uint32_t w = (qb + fl) * 32 + (__ffs(zz) - 1);
+            return w < cap ? w : cap;
+        }
+    }
+    return cap;
+}
+
+// Level-0 encoder (same parse rule as lz4_encode_warp<0>: 8-byte matches at
+// word-aligned positions against the previous bit-row or the previous word,
+// extended back up to 3 bytes and forward), driven by two word-equality
+// bitmaps built in one parallel pass:
+//   Erow bit w: word w equals word w - rowlen/4;  Erun bit w: word w equals w - 1.
+// A candidate at word w needs bits w and w+1 (8 bytes); a match then covers
+// every following word whose bit is set, plus the equal leading bytes of the
+// first word that differs.  The serial part of the parse is a handful of
+// bitmap scans per sequence instead of a probe loop.  S must be a multiple of
+// 4; bm holds 2 * (S/128 + 2) words of shared scratch.
+BSG_D uint32_t lz4_encode_bitmap(const uint8_t *src, uint32_t S, uint32_t rowlen, uint8_t *dst,
+                                 uint32_t *bm)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
+    const uint32_t NW = S / 4;
+    const uint32_t NB = (NW + 31) / 32;
+    const uint32_t R = (rowlen & 3u) ? 0u : rowlen / 4;
+    uint32_t *Erow = bm, *Erun = bm + NB + 1;
+    for (uint32_t b = 0; b < NB; b++) {
+        const uint32_t w = 32 * b + lane;
+        const bool in = w < NW;
+        const uint32_t x = in ? s32[w] : 0u;
+        uint32_t xp = __shfl_up_sync(FULL, x, 1);
+        if (lane == 0) xp = w >= 1 ? s32[w - 1] : ~x;
+        const uint32_t xr = (in && R && w >= R) ? s32[w - R] : ~x;
+        const uint32_t row = __ballot_sync(FULL, in && R && w >= R && x == xr);
+        const uint32_t run = __ballot_sync(FULL, in && w >= 1 && x == xp);
+        if (lane == 0) {
+            Erow[b] = row;
+            Erun[b] = run;
+        }
+    }
+    if (lane == 0) {
+        Erow[NB] = 0;
+        Erun[NB] = 0;
+    }
+    __syncwarp();
+    uint32_t anchor = 0, o = 0;
+    if (S >= LZ4_MFLIMIT + 1) {
+        const uint32_t wlim = (S - LZ4_LASTLITERALS - LZ4_GPU_MINMATCH) / 4;  // last probe word
+        const uint32_t matchlimit = S - LZ4_LASTLITERALS;                    // match end bound
+        uint32_t pos = 0;
+        for (uint32_t guard = 0; guard <= NW; guard++) {
+            const uint32_t w0 = (pos + 3) / 4;
+            if (w0 > wlim) break;
+            // first candidate word in [w0, wlim]
+            uint32_t w = ~0u, isrow = 0;
+            for (uint32_t qb = w0 >> 5; qb <= (wlim >> 5); qb += 32) {
+                const uint32_t q = qb + lane;
+                uint32_t crow = 0, crun = 0;
+                if (q <= (wlim >> 5)) {
+                    const uint32_t r0 = Erow[q], r1 = Erow[q + 1], u0 = Erun[q], u1 = Erun[q + 1];
+                    crow = r0 & ((r0 >> 1) | (r1 << 31));
+                    crun = u0 & ((u0 >> 1) | (u1 << 31));
+                    uint32_t keep = ~0u;
+                    if (q == (w0 >> 5)) keep &= ~0u << (w0 & 31u);
+                    if (q == (wlim >> 5)) keep &= (wlim & 31u) == 31u ? ~0u : ((2u << (wlim & 31u)) - 1u);
+                    crow &= keep;
+                    crun &= keep;
+                }
+                const uint32_t m = __ballot_sync(FULL, (crow | crun) != 0);
+                if (m) {
+                    const uint32_t fl = __ffs(m) - 1;
+                    const uint32_t cr = __shfl_sync(FULL, crow, fl);
+                    const uint32_t cu = __shfl_sync(FULL, crun, fl);
+                    const uint32_t bit = __ffs(cr | cu) - 1;
+                    w = (qb + fl) * 32 + bit;
+                    isrow = (cr >> bit) & 1u;  // the previous bit-row wins a tie
+                    break;
+                }
+            }
+            if (w == ~0u) break;
+            const uint32_t off = isrow ? rowlen : 4u;
+            const uint32_t p0 = 4 * w;
+            // whole words that still agree, then the agreeing bytes of the next
+            const uint32_t cap = matchlimit / 4;
+            const uint32_t wz = bitmap_first_zero(isrow ? Erow : Erun, w + 2, cap, lane);
+            uint32_t len = 4 * (wz - w);
+            if (4 * wz < matchlimit) {
+                const uint32_t x = s32[wz] ^ s32[wz - off / 4];
+                uint32_t eq = x ? ((uint32_t)(__ffs(x) - 1) >> 3) : 4u;
+                if (eq > matchlimit - 4 * wz) eq = matchlimit - 4 * wz;
+                len += eq;
+            }
+            uint32_t mp = p0;
+            // back up over up to 3 equal bytes (never before the literal anchor)
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                if (mp > anchor && mp > off && src[mp - 1] == src[mp - 1 - off]) {
+                    mp--;
+                    len++;
+                }
+            }
+            o = lz4_emit(dst, o, src, anchor, mp, off, len, lane);
+            anchor = mp + len;
+            pos = anchor;
+        }
+    }
+    o = lz4_emit_last(dst, o, src, anchor, S, lane);
+    __syncwarp();
+    return o;
+}
+
 // Warp-parallel read of 255-continued length bytes at src[ip..]; adds them to
 // *len.  Returns false if the bytes run past index `clen` (the stream end).
 BSG_D bool lz4_read_len(const uint8_t *src, uint32_t clen, uint32_t &ip, uint32_t &len,
@@ -277,8 +435,9 @@ BSG_D void lz4_match_copy(uint8_t *dst, uint32_t op, uint32_t off, uint32_t ML, 
 {
     if (off >= ML) {
         warp_copy(dst, op, dst, op - off, ML, lane);
-    } else if (off == 1) {
-        warp_fill(dst, op, dst[op - 1], ML, lane);
+    } else if (off == 1 || off == 2 || off == 4) {
+        // period dividing 4: every aligned output word holds the same value
+        warp_fill_pattern(dst, op, off, ML, lane);
     } else if (off >= 32) {
         const uint32_t W = off < 128u ? off : 128u;
         for (uint32_t base = 0; base < ML; base += W) {

@@ -140,6 +140,20 @@ static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc
             if (threadIdx.x == 0) cs = o;
         });
         if (cs > lz4_bound(S)) { bad++; continue; }
+        if (level == 0 && S % 4 == 0) {
+            // the bitmap-driven encoder follows the same parse rule
+            uint32_t cs2 = 0;
+            static uint8_t E[70000];
+            memset(E, 0xCD, S + 64);
+            run_warp([&] {
+                uint32_t o = lz4_encode_bitmap(A, S, rows[ci], E, (uint32_t *)T);
+                if (threadIdx.x == 0) cs2 = o;
+            });
+            if (cs2 != cs || memcmp(E, Bf, cs)) {
+                fprintf(stderr, "bitmap encoder differs S=%u rows=%u %u vs %u\n", S, rows[ci], cs2, cs);
+                bad++;
+            }
+        }
         std::vector<uint8_t> out(S + 1);
         if (orc_lz4_decompress_block(Bf, cs, out.data(), S) || memcmp(out.data(), c.data(), S)) bad++;
         int rc = -1;
