@@ -8,6 +8,7 @@
 
 #include "../../include/bsgpu.h"
 #include "kernels.cuh"
+#include "shuffle.cuh"
 
 using namespace bsg;
 
@@ -75,16 +76,27 @@ uint32_t persistent_grid(uint32_t smem_per_cta, uint64_t work)
 }
 
 struct WsLayout {
-    size_t state, autos, pairs, offsets, total;
+    size_t state, autos, pairs, offsets, slots, total;
 };
 
-WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod)
+// Whether compress takes the fast kernel (full blocks of at most 8 KiB of 4-
+// or 8-byte elements; a cube also needs n_time % 16 == 0).
+bool fast_shape(const Geometry &g, uint64_t n_time)
+{
+    return shuffle_inplace_ok(g.es, g.B) && (n_time == 0 || n_time % 16 == 0);
+}
+
+WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint64_t n_time = 0)
 {
     WsLayout L{};
     size_t o = WS_HEADER;
     if (op == BSGPU_OP_COMPRESS || op == BSGPU_OP_COMPRESS_VIS) {
         L.state = o;
         o += r256((size_t)g.nb * 8);
+        if (g.nb && fast_shape(g, n_time)) {
+            L.slots = o;
+            o += (size_t)FAST_MAX_WARPS * 2 * FAST_SLOT_BYTES;
+        }
     }
     if (op == BSGPU_OP_COMPRESS_VIS || op == BSGPU_OP_REDUCE_PRECISION) {
         L.autos = o;
@@ -169,7 +181,7 @@ size_t bsgpu_vis_workspace_size(int op, int64_t n_freq, int64_t n_inputs, int64_
     Geometry g{};
     if (op == BSGPU_OP_COMPRESS_VIS && geometry(2 * n_cplx, 4, block_elems, g) != BSGPU_OK)
         return 0;
-    return ws_layout(op, g, (uint64_t)n_freq * n_inputs * n_time, n_prod).total;
+    return ws_layout(op, g, (uint64_t)n_freq * n_inputs * n_time, n_prod, (uint64_t)n_time).total;
 }
 
 int bsgpu_status(const void *ws, void *stream, int *status)
@@ -281,8 +293,34 @@ static int compress_common(const void *in, const Geometry &g, int level, void *o
     if (cudaMemsetAsync(ws, 0, L.state + (size_t)g.nb * 8, s) != cudaSuccess)
         return BSGPU_ERR_CUDA;
     if (g.nb == 0) return cuda_err(launch_compress_small(a, s));
+    // full blocks through the fast kernel when its slots are in the
+    // workspace, the rest (a shortened last block, other shapes) through the
+    // general one; both place blocks through the same look-back state
+    const uint32_t nfull = g.nb - (g.last_B != g.B ? 1u : 0u);
+    uint32_t done = 0;
+    if (L.slots && nfull) {
+        int dev = 0, sms = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        uint64_t grid = (uint64_t)sms * compress_fast_blocks_per_sm(level, g.es);
+        if (grid > nfull) grid = nfull;
+        if (grid > FAST_MAX_WARPS) grid = FAST_MAX_WARPS;
+        CodecArgs f = a;
+        f.tile_begin = 0;
+        f.tile_end = nfull;
+        f.slots = reinterpret_cast<uint8_t *>(ws) + L.slots;
+        f.nslot_warps = FAST_MAX_WARPS;
+        f.tile_counter = reinterpret_cast<uint32_t *>((uint8_t *)ws + 4);
+        cudaError_t e = launch_compress_fast(f, (uint32_t)grid, s);
+        if (e != cudaSuccess) return BSGPU_ERR_CUDA;
+        done = nfull;
+    }
+    if (done == g.nb) return BSGPU_OK;
+    a.tile_begin = done;
+    a.tile_end = g.nb;
+    a.tile_counter = reinterpret_cast<uint32_t *>((uint8_t *)ws + 8);
     uint32_t maxb = maxb_class(g.B * g.es);
-    uint32_t grid = persistent_grid(compress_smem_bytes(maxb, level), g.nb);
+    uint32_t grid = persistent_grid(compress_smem_bytes(maxb, level), g.nb - done);
     return cuda_err(launch_compress(a, maxb, grid, s));
 }
 
@@ -319,7 +357,7 @@ int bsgpu_compress_vis(const void *vis, int64_t n_freq, int64_t n_inputs, int64_
         ((uintptr_t)d_block_offsets & 7u))
         return BSGPU_ERR_ALIGN;
     uint64_t n_auto = (uint64_t)n_freq * n_inputs * n_time;
-    WsLayout L = ws_layout(BSGPU_OP_COMPRESS_VIS, g, n_auto, n_prod);
+    WsLayout L = ws_layout(BSGPU_OP_COMPRESS_VIS, g, n_auto, n_prod, (uint64_t)n_time);
     if (ws_bytes < L.total) return BSGPU_ERR_SPACE;
     VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f);
     cudaStream_t s = (cudaStream_t)stream;

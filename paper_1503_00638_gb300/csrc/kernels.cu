@@ -384,15 +384,22 @@ __global__ void __launch_bounds__(256) reduce_precision_kernel(const float2 *__r
 // inclusive prefix.  Tiles are taken in order from a counter, so every
 // predecessor is held by a running warp; waits are bounded all the same.
 // ---------------------------------------------------------------------------
-BSG_D uint64_t lookback(uint64_t *state, uint32_t tile, uint64_t agg, int *status,
-                        uint32_t lane)
+constexpr uint64_t LB_FA = 1ull << 62, LB_FP = 2ull << 62, LB_VM = (1ull << 62) - 1;
+
+// Make a block's compressed size visible to its successors (tile 0 publishes
+// its inclusive prefix directly).
+BSG_D void lookback_publish(uint64_t *state, uint32_t tile, uint64_t agg, uint32_t lane)
 {
-    constexpr uint64_t FA = 1ull << 62, FP = 2ull << 62, VM = (1ull << 62) - 1;
-    if (tile == 0) {
-        if (lane == 0) st_relaxed_u64(state, FP | agg);
-        return 0;
-    }
-    if (lane == 0) st_relaxed_u64(state + tile, FA | agg);
+    if (lane == 0) st_relaxed_u64(state + tile, (tile == 0 ? LB_FP : LB_FA) | agg);
+}
+
+// Exclusive prefix of a block whose size is already published; publishes its
+// inclusive prefix.
+BSG_D uint64_t lookback_resolve(uint64_t *state, uint32_t tile, uint64_t agg, int *status,
+                                uint32_t lane)
+{
+    constexpr uint64_t FP = LB_FP, VM = LB_VM;
+    if (tile == 0) return 0;
     uint64_t excl = 0;
     int64_t base = (int64_t)tile - 1;
     uint32_t spins = 0;
@@ -425,6 +432,13 @@ BSG_D uint64_t lookback(uint64_t *state, uint32_t tile, uint64_t agg, int *statu
     return excl;
 }
 
+BSG_D uint64_t lookback(uint64_t *state, uint32_t tile, uint64_t agg, int *status,
+                        uint32_t lane)
+{
+    lookback_publish(state, tile, agg, lane);
+    return lookback_resolve(state, tile, agg, status, lane);
+}
+
 // ---------------------------------------------------------------------------
 // Compress: [round ->] bitshuffle -> LZ4 -> placed by look-back
 // ---------------------------------------------------------------------------
@@ -452,33 +466,17 @@ BSG_D void compress_prepare(const CodecArgs &a, uint32_t tile, uint8_t *in, uint
     shuffle_block(in, tmp, Bb, a.es, lane);
 }
 
-// LZ4-encode the bit-rows in `tmp` into `out`, place the block by look-back
-// and write it (plus the header, the index entry and, for the last block, the
-// verbatim tail).
-template <uint32_t MAXB, int LEVEL>
-BSG_D void compress_finish(const CodecArgs &a, uint32_t tile, uint8_t *tmp, uint8_t *out,
-                           void *scratch, uint32_t lane)
+// Write block `tile` (its 4-byte length field and cs LZ4 bytes at `blk`, in
+// shared or global memory) at stream offset D, with the index entry, the
+// chunk header (block 0) and, after the last block, the verbatim tail.
+BSG_D void compress_place(const CodecArgs &a, uint32_t tile, const uint8_t *blk, uint32_t cs,
+                          uint64_t D, uint32_t lane)
 {
-    using L = CompPlan<MAXB, LEVEL>;
-    const uint32_t Bb = block_elems_of(a, tile);
-    const uint32_t S = Bb * a.es;
-    // bit-rows are Bb/8 bytes long: the previous row is one of the candidates
-    uint32_t cs = LEVEL >= 1
-        ? lz4_encode_warp<1, L::HBITS>(tmp, S, Bb / 8, out + 4, static_cast<uint16_t *>(scratch))
-        : lz4_encode_bitmap(tmp, S, Bb / 8, out + 4, static_cast<uint32_t *>(scratch));
-    if (cs == 0xffffffffu) {  // progress guard (not reachable for valid sizes)
-        if (lane == 0) set_status(a.status, BSGPU_ERR_CUDA);
-        cs = 0;
-    }
-    if (lane == 0) put_be32(out, cs);
-    __syncwarp();
-    const uint64_t excl = lookback(a.tile_state, tile, 4ull + cs, a.status, lane);
-    const uint64_t D = 12 + excl;
     if (D + 4 + cs > a.out_cap) {
         if (lane == 0) set_status(a.status, BSGPU_ERR_SPACE);
         return;
     }
-    copy_out(out, a.out + D, 4 + cs, lane);
+    copy_out(blk, a.out + D, 4 + cs, lane);
     if (a.block_offsets && lane == 0) a.block_offsets[tile] = D;
     if (tile == 0) write_chunk_header(a.out, a.n_elem * a.es, a.B * a.es, lane);
     if (tile + 1 == a.nb) {
@@ -504,6 +502,39 @@ BSG_D void compress_finish(const CodecArgs &a, uint32_t tile, uint8_t *tmp, uint
     }
 }
 
+// LZ4-encode the bit-rows in `tmp` into `dst` after a 4-byte length field;
+// returns the LZ4 size.
+template <int LEVEL, int HBITS>
+BSG_D uint32_t compress_encode(const CodecArgs &a, uint32_t Bb, const uint8_t *tmp, uint8_t *dst,
+                               void *scratch, uint32_t lane)
+{
+    const uint32_t S = Bb * a.es;
+    // bit-rows are Bb/8 bytes long: the previous row is one of the candidates
+    uint32_t cs = LEVEL >= 1
+        ? lz4_encode_warp<1, HBITS>(tmp, S, Bb / 8, dst + 4, static_cast<uint16_t *>(scratch))
+        : lz4_encode_bitmap(tmp, S, Bb / 8, dst + 4, static_cast<uint32_t *>(scratch));
+    if (cs == 0xffffffffu) {  // progress guard (not reachable for valid sizes)
+        if (lane == 0) set_status(a.status, BSGPU_ERR_CUDA);
+        cs = 0;
+    }
+    if (lane == 0) put_be32(dst, cs);
+    __syncwarp();
+    return cs;
+}
+
+// LZ4-encode the bit-rows in `tmp` into `out`, place the block by look-back
+// and write it.
+template <uint32_t MAXB, int LEVEL>
+BSG_D void compress_finish(const CodecArgs &a, uint32_t tile, uint8_t *tmp, uint8_t *out,
+                           void *scratch, uint32_t lane)
+{
+    using L = CompPlan<MAXB, LEVEL>;
+    const uint32_t Bb = block_elems_of(a, tile);
+    const uint32_t cs = compress_encode<LEVEL, L::HBITS>(a, Bb, tmp, out, scratch, lane);
+    const uint64_t excl = lookback(a.tile_state, tile, 4ull + cs, a.status, lane);
+    compress_place(a, tile, out, cs, 12 + excl, lane);
+}
+
 // One warp per CTA, persistent.  Per block: wait for its bulk copy into `in`,
 // round + transpose into `tmp`, start the next block's copy into `in`, then
 // LZ4 into `out`, look-back placement and the write-out, which overlap the
@@ -526,19 +557,19 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 9 : 1)
     }
     __syncwarp();
     uint32_t parity = 0;
-    uint32_t tile = grab_tile(a.tile_counter, lane);
-    bool pend = tile < a.nb && load_block(in, a.in + (uint64_t)tile * a.B * a.es,
-                                          block_elems_of(a, tile) * a.es, bar, lane);
-    while (tile < a.nb) {
+    uint32_t tile = a.tile_begin + grab_tile(a.tile_counter, lane);
+    bool pend = tile < a.tile_end && load_block(in, a.in + (uint64_t)tile * a.B * a.es,
+                                                block_elems_of(a, tile) * a.es, bar, lane);
+    while (tile < a.tile_end) {
         if (pend) {
             if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);
             parity ^= 1u;
         }
         compress_prepare(a, tile, in, tmp, lane);
         __syncwarp();
-        const uint32_t nxt = grab_tile(a.tile_counter, lane);
+        const uint32_t nxt = a.tile_begin + grab_tile(a.tile_counter, lane);
         pend = false;
-        if (nxt < a.nb) {
+        if (nxt < a.tile_end) {
             // the transpose's reads of `in` (generic proxy) precede the async write
             fence_proxy_async_smem();
             __syncwarp();
@@ -548,6 +579,148 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 9 : 1)
         compress_finish<MAXB, LEVEL>(a, tile, tmp, out, scratch, lane);
         __syncwarp();
         tile = nxt;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Compress, fast path: blocks of at most 8 KiB of 4- or 8-byte elements
+// ---------------------------------------------------------------------------
+template <int LEVEL>
+struct FastPlan {
+    static constexpr uint32_t MAXB = 8192;
+    static constexpr uint32_t TMP = r16(MAXB + 16);  // staged block, then its bit-rows
+    static constexpr int HBITS = 11;
+    static constexpr uint32_t SCR = LEVEL >= 1 ? (2u << HBITS) : 2u * 4u * (MAXB / 128u + 2u);
+    static constexpr uint32_t BYTES = TMP + r16(SCR) + 16;
+};
+
+uint32_t compress_fast_smem_bytes(int level)
+{
+    return level >= 1 ? FastPlan<1>::BYTES : FastPlan<0>::BYTES;
+}
+
+template <int LEVEL, int ES>
+__global__ void compress_fast_kernel(const __grid_constant__ CodecArgs a);
+
+uint32_t compress_fast_blocks_per_sm(int level, uint32_t es)
+{
+    int n = 0;
+    const uint32_t smem = compress_fast_smem_bytes(level);
+    cudaError_t e;
+    if (es == 8)
+        e = level >= 1
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, compress_fast_kernel<1, 8>, 32, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, compress_fast_kernel<0, 8>, 32, smem);
+    else
+        e = level >= 1
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, compress_fast_kernel<1, 4>, 32, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, compress_fast_kernel<0, 4>, 32, smem);
+    return e == cudaSuccess && n > 0 ? (uint32_t)n : 1u;
+}
+
+static_assert(FAST_SLOT_BYTES >= r16(4 + lz4b(8192) + 32), "staging slot too small");
+
+// Precision reduction of one group of 32 float32 values (16 consecutive time
+// samples of one product, the time axis being a multiple of 16) held in
+// registers in lane-rotated chunk order: a[m] is float (m + 4 (g & 7)) mod 32.
+struct VisGroupRound {
+    const VisParams *P;
+    uint32_t c_blk;  // complex index of the block's first sample
+    BSG_D void operator()(uint32_t g, uint32_t (&a)[32]) const
+    {
+        const uint32_t rot = g & 7u;
+        const uint32_t cg = c_blk + 16 * g;
+        const uint32_t fp = cg / P->T;
+        const uint32_t t0 = cg - fp * P->T;
+        const uint32_t f = fp / P->P;
+        const uint32_t p = fp - f * P->P;
+        const uint32_t ij = __ldg(P->pairs + p);
+        const uint32_t i = ij & 0xffffu, j = ij >> 16;
+        const bool is_auto = i == j;
+        const float cc = is_auto ? P->c2 : P->c;
+        const float *ai = P->autos + (size_t)(f * P->n_in + i) * P->T + t0;
+        const float *aj = P->autos + (size_t)(f * P->n_in + j) * P->T + t0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t c = (k + rot) & 7u;  // chunk c: samples t0 + 2c, t0 + 2c + 1
+            const float2 Ai = __ldg(reinterpret_cast<const float2 *>(ai + 2 * c));
+            const float2 Aj = __ldg(reinterpret_cast<const float2 *>(aj + 2 * c));
+            const float q0 = __fmul_rn(__fmul_rn(cc, Ai.x), Aj.x);
+            const float q1 = __fmul_rn(__fmul_rn(cc, Ai.y), Aj.y);
+            a[4 * k] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k]), q0));
+            a[4 * k + 2] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 2]), q1));
+            if (!is_auto) {
+                a[4 * k + 1] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 1]), q0));
+                a[4 * k + 3] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 3]), q1));
+            }
+        }
+    }
+};
+
+struct NoRound {
+    BSG_D void operator()(uint32_t, uint32_t (&)[32]) const {}
+};
+
+// One warp per CTA, persistent, one shared buffer: bulk-copy the block in,
+// round + bit-transpose it in place through registers, LZ4-encode it into
+// this warp's staging slot in global memory (it stays in L2), publish its
+// size, and place the PREVIOUS block: by then its predecessors have long
+// published theirs, so the look-back rarely waits.
+template <int LEVEL, int ES>
+__global__ void __launch_bounds__(32, 16) compress_fast_kernel(const __grid_constant__ CodecArgs a)
+{
+    using L = FastPlan<LEVEL>;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *tmp = sm;
+    void *scratch = sm + L::TMP;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::TMP + r16(L::SCR));
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint8_t *slot0 = a.slots + (size_t)(2 * blockIdx.x) * FAST_SLOT_BYTES;
+    uint8_t *slot1 = slot0 + FAST_SLOT_BYTES;
+    uint32_t parity = 0;
+    uint32_t ptile = ~0u, pcs = 0;  // the block waiting to be placed, in slot1
+    uint32_t tile = grab_tile(a.tile_counter, lane);
+    while (tile < a.tile_end) {
+        const uint32_t Bb = a.B;  // the fast path takes full blocks only
+        if (load_block(tmp, a.in + (uint64_t)tile * a.B * a.es, Bb * a.es, bar, lane)) {
+            if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);
+            parity ^= 1u;
+        }
+        if (ES == 8) {
+            shuffle8_inplace(tmp, Bb, lane);
+        } else if (a.vis.enabled) {
+            shuffle4_inplace(tmp, Bb, lane,
+                             VisGroupRound{&a.vis, (uint32_t)(((uint64_t)tile * a.B) >> 1)});
+        } else {
+            shuffle4_inplace(tmp, Bb, lane, NoRound{});
+        }
+        __syncwarp();
+        const uint32_t cs = compress_encode<LEVEL, L::HBITS>(a, Bb, tmp, slot0, scratch, lane);
+        lookback_publish(a.tile_state, tile, 4ull + cs, lane);
+        const uint32_t nxt = grab_tile(a.tile_counter, lane);
+        if (ptile != ~0u) {
+            const uint64_t excl = lookback_resolve(a.tile_state, ptile, 4ull + pcs, a.status, lane);
+            compress_place(a, ptile, slot1, pcs, 12 + excl, lane);
+        }
+        __syncwarp();
+        ptile = tile;
+        pcs = cs;
+        uint8_t *t = slot0;
+        slot0 = slot1;
+        slot1 = t;
+        tile = nxt;
+        // the next load overwrites `tmp`: the async proxy follows the generic reads
+        fence_proxy_async_smem();
+        __syncwarp();
+    }
+    if (ptile != ~0u) {
+        const uint64_t excl = lookback_resolve(a.tile_state, ptile, 4ull + pcs, a.status, lane);
+        compress_place(a, ptile, slot1, pcs, 12 + excl, lane);
     }
 }
 
@@ -905,6 +1078,16 @@ cudaError_t launch_compress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cu
     if (maxb <= 8192) return launch_warp_kernel(compress_kernel<8192, 0>, smem, grid, s, a);
     if (maxb <= 16384) return launch_warp_kernel(compress_kernel<16384, 0>, smem, grid, s, a);
     return launch_warp_kernel(compress_kernel<65536, 0>, smem, grid, s, a);
+}
+
+cudaError_t launch_compress_fast(const CodecArgs &a, uint32_t grid, cudaStream_t s)
+{
+    const uint32_t smem = compress_fast_smem_bytes(a.level);
+    if (a.es == 8)
+        return a.level >= 1 ? launch_warp_kernel(compress_fast_kernel<1, 8>, smem, grid, s, a)
+                            : launch_warp_kernel(compress_fast_kernel<0, 8>, smem, grid, s, a);
+    return a.level >= 1 ? launch_warp_kernel(compress_fast_kernel<1, 4>, smem, grid, s, a)
+                        : launch_warp_kernel(compress_fast_kernel<0, 4>, smem, grid, s, a);
 }
 
 cudaError_t launch_compress_small(const CodecArgs &a, cudaStream_t s)

@@ -31,6 +31,10 @@ struct CodecArgs {
     uint64_t n_elem;
     uint32_t es, B, nb, last_B, tail_elems;
     int level;               // compress: LZ4 search level (0 structural, 1 + hash)
+    uint32_t tile_begin;     // compress: tiles [tile_begin, tile_end) of this launch
+    uint32_t tile_end;
+    uint8_t *slots;          // compress fast path: two staging slots per warp
+    uint32_t nslot_warps;    // warps the slots cover
     VisParams vis;
 };
 
@@ -47,6 +51,15 @@ cudaError_t launch_reduce_precision(const float *in, float *out, uint64_t n_cplx
 cudaError_t launch_shuffle(const CodecArgs &a, bool inverse, uint32_t maxb, uint32_t grid,
                            cudaStream_t s);
 cudaError_t launch_compress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s);
+// Fast path for full blocks that the in-place register transposes take
+// (shuffle_inplace_ok; for a cube also n_time % 16 == 0): tiles
+// [0, a.tile_end), placement one block late through per-warp staging slots.
+cudaError_t launch_compress_fast(const CodecArgs &a, uint32_t grid, cudaStream_t s);
+uint32_t compress_fast_smem_bytes(int level);
+uint32_t compress_fast_blocks_per_sm(int level, uint32_t es);
+// staging slot size of the fast path and the warp count its slots cover
+constexpr uint32_t FAST_SLOT_BYTES = 8304;
+constexpr uint32_t FAST_MAX_WARPS = 2560;
 cudaError_t launch_compress_small(const CodecArgs &a, cudaStream_t s);
 cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s);
 cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, cudaStream_t s);

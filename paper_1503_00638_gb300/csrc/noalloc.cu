@@ -94,6 +94,8 @@ extern "C" int bsgpu_compress_noalloc(const void *in, size_t n_elem, size_t elem
     a.last_B = (uint32_t)(last ? last : B);
     a.tail_elems = (uint32_t)(rem % 8);
     a.level = level;
+    a.tile_begin = 0;
+    a.tile_end = (uint32_t)nb;
 
     // the array keeps the previous call's contents: clear what starts at zero
     cudaStream_t s = (cudaStream_t)stream;

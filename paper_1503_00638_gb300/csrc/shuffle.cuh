@@ -231,6 +231,95 @@ BSG_D void unshuffle8_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
     }
 }
 
+// Bit-transpose a block of 4-byte elements in place (buf holds Bb elements;
+// afterwards its 32 bit-rows of Bb/8 bytes), for Bb <= 1024 (one group of 32
+// elements per lane) or Bb == 2048 (two).  Each group's 32 values pass through
+// `fix(g, a)` before the transpose (the hook that rounds visibility data);
+// a[m] then holds element (m + 4 (g & 7)) mod 32 of group g.
+//
+// With 64 groups, row r of group g is word 64 r + g: rows 0..15 of the first
+// groups (g < 32) fall in the first half of the buffer, which holds only the
+// first groups' inputs, so they are written before the second groups are
+// read, and at most 48 values per lane are live.
+template <class Fix>
+BSG_D void shuffle4_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane, Fix fix)
+{
+    const uint32_t G = Bb / 32;
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(buf);
+    auto read_group = [&](uint32_t g, uint32_t (&a)[32]) {
+        const uint8_t *grp = buf + 128u * g;
+        const uint32_t rot = g & 7u;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            uint4 v = *reinterpret_cast<const uint4 *>(grp + 16u * ((k + rot) & 7u));
+            a[4 * k] = v.x;
+            a[4 * k + 1] = v.y;
+            a[4 * k + 2] = v.z;
+            a[4 * k + 3] = v.w;
+        }
+        fix(g, a);
+        transpose32(a);
+    };
+    const uint32_t g0 = lane, rot0 = 4u * (g0 & 7u);
+    uint32_t a[32];
+    if (g0 < G) read_group(g0, a);
+    __syncwarp();
+    if (G <= 32) {
+        if (g0 < G) {
+#pragma unroll
+            for (int r = 0; r < 32; r++) d32[r * G + g0] = rotl(a[r], rot0);
+        }
+        return;
+    }
+    // G == 64
+#pragma unroll
+    for (int r = 0; r < 16; r++) d32[r * 64 + g0] = rotl(a[r], rot0);
+    const uint32_t g1 = lane + 32u, rot1 = 4u * (g1 & 7u);
+    uint32_t b[32];
+    read_group(g1, b);
+    __syncwarp();
+#pragma unroll
+    for (int r = 16; r < 32; r++) d32[r * 64 + g0] = rotl(a[r], rot0);
+#pragma unroll
+    for (int r = 0; r < 32; r++) d32[r * 64 + g1] = rotl(b[r], rot1);
+}
+
+// 8-byte elements, at most 32 groups (one per lane).
+BSG_D void shuffle8_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t G = Bb / 32;
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(buf);
+    const uint32_t g = lane, rot = g & 15u;
+    uint32_t lo[32], hi[32];
+    if (g < G) {
+        const uint8_t *grp = buf + 256u * g;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            uint4 v = *reinterpret_cast<const uint4 *>(grp + 16u * ((k + rot) & 15u));
+            lo[2 * k] = v.x;
+            hi[2 * k] = v.y;
+            lo[2 * k + 1] = v.z;
+            hi[2 * k + 1] = v.w;
+        }
+    }
+    __syncwarp();
+    if (g < G) {
+        transpose32(lo);
+        transpose32(hi);
+#pragma unroll
+        for (int r = 0; r < 32; r++) {
+            d32[r * G + g] = rotl(lo[r], 2u * rot);
+            d32[(32 + r) * G + g] = rotl(hi[r], 2u * rot);
+        }
+    }
+}
+
+// Whether a block can be bit-transposed in place by the register paths above.
+BSG_HD bool shuffle_inplace_ok(uint32_t es, uint32_t Bb)
+{
+    return Bb % 32u == 0 && ((es == 4 && (Bb <= 1024 || Bb == 2048)) || (es == 8 && Bb <= 1024));
+}
+
 // Whether a block can be un-transposed in place by the register paths above.
 BSG_D bool unshuffle_inplace_ok(uint32_t es, uint32_t Bb)
 {

@@ -88,6 +88,16 @@ static int test_inplace_unshuffle(std::mt19937 &rng)
                     unshuffle8_inplace(C, B, threadIdx.x);
             });
             bad += memcmp(A, C, S) != 0;
+            if (shuffle_inplace_ok(es, B)) {
+                memcpy(C, A, S);
+                run_warp([&] {
+                    if (es == 4)
+                        shuffle4_inplace(C, B, threadIdx.x, [](uint32_t, uint32_t (&)[32]) {});
+                    else
+                        shuffle8_inplace(C, B, threadIdx.x);
+                });
+                bad += memcmp(rows.data(), C, S) != 0;
+            }
         }
     return bad;
 }
