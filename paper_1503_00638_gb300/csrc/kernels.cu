@@ -803,8 +803,10 @@ BSG_D DecLoad dec_issue(const CodecArgs &a, uint32_t tile, uint8_t *dst, uint64_
 // `comp`, LZ4-decode into `dec`, start the next block's copy into `comp`,
 // un-transpose `dec` in place and bulk-store it (blocks the register paths
 // cannot take are un-transposed into `comp` and stored before the next copy).
-template <uint32_t MAXB>
-__global__ void __launch_bounds__(32, MAXB <= 8192 ? 12 : 1)
+// ES: 4 or 8 compiles the in-place register un-transpose for that element
+// size; 0 compiles only the general path.
+template <uint32_t MAXB, int ES>
+__global__ void __launch_bounds__(32, MAXB <= 8192 ? 13 : 1)
     decompress_kernel(const __grid_constant__ CodecArgs a)
 {
     using L = DecPlan<MAXB>;
@@ -854,7 +856,7 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 12 : 1)
         }
         if (!good && lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);
         uint8_t *dst = a.out + (uint64_t)tile * a.B * a.es;
-        const bool inplace = MAXB <= 8192 && unshuffle_inplace_ok(a.es, Bb);
+        const bool inplace = ES != 0 && MAXB <= 8192 && unshuffle_inplace_ok(a.es, Bb);
         if (good && !inplace) {
             unshuffle_block(dec, comp, Bb, a.es, lane);
             __syncwarp();
@@ -870,9 +872,9 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 12 : 1)
             ld = dec_issue(a, nxt, comp, bar, lane);
         }
         if (good && inplace) {
-            if (a.es == 4)
-                unshuffle4_inplace<2>(dec, Bb, lane);
-            else
+            if (ES == 4)
+                unshuffle4_inplace(dec, Bb, lane);
+            else if (ES == 8)
                 unshuffle8_inplace(dec, Bb, lane);
             __syncwarp();
             if ((S & 15u) == 0 && ((uintptr_t)dst & 15u) == 0) {
@@ -1103,9 +1105,13 @@ cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, 
         return cudaGetLastError();
     }
     uint32_t smem = decompress_smem_bytes(maxb);
-    if (maxb <= 8192) return launch_warp_kernel(decompress_kernel<8192>, smem, grid, s, a);
-    if (maxb <= 16384) return launch_warp_kernel(decompress_kernel<16384>, smem, grid, s, a);
-    return launch_warp_kernel(decompress_kernel<65536>, smem, grid, s, a);
+    if (maxb <= 8192) {
+        if (a.es == 4) return launch_warp_kernel(decompress_kernel<8192, 4>, smem, grid, s, a);
+        if (a.es == 8) return launch_warp_kernel(decompress_kernel<8192, 8>, smem, grid, s, a);
+        return launch_warp_kernel(decompress_kernel<8192, 0>, smem, grid, s, a);
+    }
+    if (maxb <= 16384) return launch_warp_kernel(decompress_kernel<16384, 0>, smem, grid, s, a);
+    return launch_warp_kernel(decompress_kernel<65536, 0>, smem, grid, s, a);
 }
 
 cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, cudaStream_t s)

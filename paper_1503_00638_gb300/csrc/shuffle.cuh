@@ -173,36 +173,49 @@ BSG_HD void unshuffle_block(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint3
 
 #if defined(__CUDACC__) || defined(BSG_WARP_EMU)
 // Un-transpose a block of 4-byte elements in place (buf holds 32 bit-rows of
-// Bb/8 bytes; afterwards the Bb elements): every lane first reads all of its
-// groups (at most NG) into registers, then writes them back.
-template <int NG>
+// Bb/8 bytes; afterwards the Bb elements), for Bb <= 1024 (one group of 32
+// elements per lane) or Bb == 2048 (two).  With 64 groups, group g's output
+// is words [32 g, 32 g + 32) and row r of group g is word 64 r + g: the first
+// groups' outputs (g < 32, the first half) overwrite only rows 0..15, so a
+// lane reads rows 0..15 of both its groups and rows 16..31 of its first group
+// (48 values) before anything is written, then the rest.
 BSG_D void unshuffle4_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
 {
     const uint32_t G = Bb / 32;
     const uint32_t *s32 = reinterpret_cast<const uint32_t *>(buf);
-    uint32_t a[NG][32];
+    auto store_group = [&](uint32_t g, uint32_t (&a)[32]) {
+        transpose32(a);  // a[m] holds element (m + 4 rot) mod 32
+        const uint32_t rot = g & 7u;
+        uint8_t *grp = buf + 128u * g;
 #pragma unroll
-    for (int q = 0; q < NG; q++) {
-        const uint32_t g = lane + 32u * q;
-        if (g < G) {
+        for (int k = 0; k < 8; k++)
+            *reinterpret_cast<uint4 *>(grp + 16u * ((k + rot) & 7u)) =
+                make_uint4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+    };
+    const uint32_t g0 = lane, s0 = 4u * (g0 & 7u);
+    uint32_t a[32];
+    if (G <= 32) {
+        if (g0 < G) {
 #pragma unroll
-            for (int r = 0; r < 32; r++) a[q][r] = rotr(s32[r * G + g], 4u * (g & 7u));
+            for (int r = 0; r < 32; r++) a[r] = rotr(s32[r * G + g0], s0);
         }
+        __syncwarp();
+        if (g0 < G) store_group(g0, a);
+        return;
     }
+    // G == 64
+    const uint32_t g1 = lane + 32u, s1 = 4u * (g1 & 7u);
+    uint32_t b[32];
+#pragma unroll
+    for (int r = 0; r < 32; r++) a[r] = rotr(s32[r * 64 + g0], s0);
+#pragma unroll
+    for (int r = 0; r < 16; r++) b[r] = rotr(s32[r * 64 + g1], s1);
     __syncwarp();
+    store_group(g0, a);
 #pragma unroll
-    for (int q = 0; q < NG; q++) {
-        const uint32_t g = lane + 32u * q;
-        if (g < G) {
-            transpose32(a[q]);  // a[q][m] holds element (m + 4 rot) mod 32
-            const uint32_t rot = g & 7u;
-            uint8_t *grp = buf + 128u * g;
-#pragma unroll
-            for (int k = 0; k < 8; k++)
-                *reinterpret_cast<uint4 *>(grp + 16u * ((k + rot) & 7u)) =
-                    make_uint4(a[q][4 * k], a[q][4 * k + 1], a[q][4 * k + 2], a[q][4 * k + 3]);
-        }
-    }
+    for (int r = 16; r < 32; r++) b[r] = rotr(s32[r * 64 + g1], s1);
+    __syncwarp();
+    store_group(g1, b);
 }
 
 // Same for 8-byte elements and at most 32 groups (one per lane).
@@ -321,9 +334,9 @@ BSG_HD bool shuffle_inplace_ok(uint32_t es, uint32_t Bb)
 }
 
 // Whether a block can be un-transposed in place by the register paths above.
-BSG_D bool unshuffle_inplace_ok(uint32_t es, uint32_t Bb)
+BSG_HD bool unshuffle_inplace_ok(uint32_t es, uint32_t Bb)
 {
-    return Bb % 32u == 0 && ((es == 4 && Bb <= 2048) || (es == 8 && Bb <= 1024));
+    return shuffle_inplace_ok(es, Bb);
 }
 #endif  // __CUDACC__ || BSG_WARP_EMU
 

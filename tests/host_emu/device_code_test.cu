@@ -74,8 +74,8 @@ static int test_inplace_unshuffle(std::mt19937 &rng)
 {
     int bad = 0;
     for (int es : {4, 8})
-        for (int B : {32, 64, 96, 512, 1024, 2048}) {
-            if (!unshuffle_inplace_ok(es, B)) continue;
+        for (int B : {32, 64, 96, 512, 1024, 1536, 2048}) {
+            if (!unshuffle_inplace_ok(es, B)) continue;  // (B <= 1024 or 2048 for es 4)
             size_t S = (size_t)B * es;
             for (size_t i = 0; i < S; i++) A[i] = (uint8_t)rng();
             std::vector<uint8_t> rows(S);
@@ -83,7 +83,7 @@ static int test_inplace_unshuffle(std::mt19937 &rng)
             memcpy(C, rows.data(), S);
             run_warp([&] {
                 if (es == 4)
-                    unshuffle4_inplace<2>(C, B, threadIdx.x);
+                    unshuffle4_inplace(C, B, threadIdx.x);
                 else
                     unshuffle8_inplace(C, B, threadIdx.x);
             });
