@@ -700,7 +700,14 @@ __global__ void __launch_bounds__(32, 16) compress_fast_kernel(const __grid_cons
             shuffle4_inplace(tmp, Bb, lane, NoRound{});
         }
         __syncwarp();
-        const uint32_t cs = compress_encode<LEVEL, L::HBITS>(a, Bb, tmp, slot0, scratch, lane);
+        uint32_t cs;
+        if (LEVEL == 0 && (Bb * ES) % 128u == 0) {
+            cs = lz4_encode_bitmap_fast(tmp, Bb * ES, Bb / 8, slot0 + 4);
+            if (lane == 0) put_be32(slot0, cs);
+            __syncwarp();
+        } else {
+            cs = compress_encode<LEVEL, L::HBITS>(a, Bb, tmp, slot0, scratch, lane);
+        }
         lookback_publish(a.tile_state, tile, 4ull + cs, lane);
         const uint32_t nxt = grab_tile(a.tile_counter, lane);
         if (ptile != ~0u) {

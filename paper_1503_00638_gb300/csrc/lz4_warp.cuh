@@ -406,6 +406,168 @@ BSG_D uint32_t lz4_encode_bitmap(const uint8_t *src, uint32_t S, uint32_t rowlen
     return o;
 }
 
+// First set bit at or after position `from` (and at most `to`) of a bitmap of
+// up to 2048 bits held two words per lane (word q = lane + 32 j in w[j]);
+// ~0u if none.
+BSG_D uint32_t regmap_first_set(const uint32_t (&w)[2], uint32_t from, uint32_t to, uint32_t lane)
+{
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        const uint32_t q = lane + 32u * j;
+        uint32_t m = w[j];
+        const int lo = (int)from - (int)(32 * q), hi = (int)to - (int)(32 * q);
+        if (lo > 0) m = lo >= 32 ? 0u : (m & (~0u << lo));
+        if (hi < 31) m = hi < 0 ? 0u : (m & ((2u << hi) - 1u));
+        const uint32_t b = __ballot_sync(FULL, m != 0);
+        if (b) {
+            const uint32_t fl = __ffs(b) - 1;
+            const uint32_t mm = __shfl_sync(FULL, m, fl);
+            return 32u * (fl + 32u * j) + (__ffs(mm) - 1);
+        }
+    }
+    return ~0u;
+}
+
+// Level-0 encoder for the fast path (S a multiple of 128, at most 8192): the
+// same parse as lz4_encode_bitmap, with the equality bitmaps kept in
+// registers (two words per lane) and the sequences emitted 32 at a time in
+// parallel: the parse collects up to 32 (literal start, match start, match
+// length, offset) descriptors, one per lane; a warp scan of their encoded
+// lengths places them; each lane writes its own token, length and offset
+// bytes; the literal runs are copied one after another by the whole warp.
+BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t rowlen, uint8_t *dst)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
+    const uint32_t NW = S / 4, NB = NW / 32;
+    const uint32_t R = (rowlen & 3u) ? 0u : rowlen / 4;
+    // equality bitmaps: bit w of Erow (Erun) set when word w equals word w - R (w - 1)
+    uint32_t Erow[2] = {0u, 0u}, Erun[2] = {0u, 0u};
+    uint32_t prev_last = 0;  // lane 31's word of the previous bitmap word
+#pragma unroll
+    for (uint32_t k = 0; k < 64; k++) {
+        if (k < NB) {
+            const uint32_t w = 32 * k + lane;
+            const uint32_t x = s32[w];
+            uint32_t xp = __shfl_up_sync(FULL, x, 1);
+            if (lane == 0) xp = k ? prev_last : ~x;
+            prev_last = __shfl_sync(FULL, x, 31);
+            const uint32_t xr = (R && w >= R) ? s32[w - R] : ~x;
+            const uint32_t row = __ballot_sync(FULL, R && w >= R && x == xr);
+            const uint32_t run = __ballot_sync(FULL, w >= 1 && x == xp);
+            if (lane == (k & 31u)) {
+                Erow[k >> 5] = row;
+                Erun[k >> 5] = run;
+            }
+        }
+    }
+    // candidate bitmaps: bits w and w + 1 both set (8 equal bytes)
+    uint32_t Crow[2], Crun[2];
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        uint32_t nr = __shfl_down_sync(FULL, Erow[j], 1), nu = __shfl_down_sync(FULL, Erun[j], 1);
+        const uint32_t nr1 = __shfl_sync(FULL, j == 0 ? Erow[1] : 0u, 0);
+        const uint32_t nu1 = __shfl_sync(FULL, j == 0 ? Erun[1] : 0u, 0);
+        if (lane == 31) {
+            nr = nr1;
+            nu = nu1;
+        }
+        Crow[j] = Erow[j] & ((Erow[j] >> 1) | (nr << 31));
+        Crun[j] = Erun[j] & ((Erun[j] >> 1) | (nu << 31));
+    }
+    uint32_t Cany[2] = {Crow[0] | Crun[0], Crow[1] | Crun[1]};
+    uint32_t Zrow[2] = {~Erow[0], ~Erow[1]}, Zrun[2] = {~Erun[0], ~Erun[1]};
+
+    uint32_t anchor = 0, o = 0;
+    if (S >= LZ4_MFLIMIT + 1) {
+        const uint32_t wlim = (S - LZ4_LASTLITERALS - LZ4_GPU_MINMATCH) / 4;
+        const uint32_t matchlimit = S - LZ4_LASTLITERALS;
+        const uint32_t cap = matchlimit / 4;
+        uint32_t pos = 0;
+        bool more = true;
+        for (uint32_t guard = 0; more && guard <= NW; guard++) {
+            // parse up to 32 sequences; lane k keeps the k-th
+            uint32_t my_anchor = 0, my_mp = 0, my_len = 0, my_off = 0, n = 0;
+            for (; n < 32; n++) {
+                const uint32_t w0 = (pos + 3) / 4;
+                const uint32_t w = w0 <= wlim ? regmap_first_set(Cany, w0, wlim, lane) : ~0u;
+                if (w == ~0u) {
+                    more = false;
+                    break;
+                }
+                // the previous bit-row wins a tie
+                const uint32_t qi = w >> 5, bit = w & 31u;
+                const uint32_t crw = __shfl_sync(FULL, (qi >> 5) ? Crow[1] : Crow[0], qi & 31u);
+                const uint32_t isrow = (crw >> bit) & 1u;
+                const uint32_t off = isrow ? rowlen : 4u;
+                uint32_t wz = regmap_first_set(isrow ? Zrow : Zrun, w + 2, cap - 1, lane);
+                if (wz == ~0u) wz = cap;
+                uint32_t len = 4 * (wz - w);
+                if (4 * wz < matchlimit) {
+                    const uint32_t x = s32[wz] ^ s32[wz - off / 4];
+                    uint32_t eq = x ? ((uint32_t)(__ffs(x) - 1) >> 3) : 4u;
+                    if (eq > matchlimit - 4 * wz) eq = matchlimit - 4 * wz;
+                    len += eq;
+                }
+                uint32_t mp = 4 * w;
+                // back up over up to 3 equal bytes (never before the literal anchor)
+                if (mp > pos && mp > off) {
+                    const uint32_t x = ld32u(src, mp - 4) ^ ld32u(src, mp - 4 - off);
+                    uint32_t back = (x ? __clz(x) : 32u) >> 3;
+                    if (back > 3) back = 3;
+                    if (back > mp - pos) back = mp - pos;
+                    if (back > mp - off) back = mp - off;
+                    mp -= back;
+                    len += back;
+                }
+                if (lane == n) {
+                    my_anchor = pos;
+                    my_mp = mp;
+                    my_len = len;
+                    my_off = off;
+                }
+                pos = mp + len;
+            }
+            // emit the n sequences of this batch
+            const bool mine = lane < n;
+            const uint32_t LL = mine ? my_mp - my_anchor : 0u;
+            const uint32_t ML = mine ? my_len - LZ4_MINMATCH : 0u;
+            const uint32_t nll = lz4_ext_count(LL), nml = lz4_ext_count(ML);
+            const uint32_t total = mine ? 1 + nll + LL + 2 + nml : 0u;
+            uint32_t incl = total;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, incl, d);
+                if (lane >= (uint32_t)d) incl += t;
+            }
+            const uint32_t base = o + incl - total;
+            if (mine) {
+                dst[base] = (uint8_t)(((LL < 15 ? LL : 15) << 4) | (ML < 15 ? ML : 15));
+                for (uint32_t k = 0; k < nll; k++)
+                    dst[base + 1 + k] = k + 1 < nll ? 255u : (uint8_t)((LL - 15) % 255u);
+                const uint32_t tr = base + 1 + nll + LL;
+                dst[tr] = (uint8_t)(my_off & 255u);
+                dst[tr + 1] = (uint8_t)(my_off >> 8);
+                for (uint32_t k = 0; k < nml; k++)
+                    dst[tr + 2 + k] = k + 1 < nml ? 255u : (uint8_t)((ML - 15) % 255u);
+            }
+            for (uint32_t k = 0; k < n; k++) {
+                const uint32_t lk = __shfl_sync(FULL, LL, k);
+                if (lk == 0) continue;
+                const uint32_t ak = __shfl_sync(FULL, my_anchor, k);
+                const uint32_t dk = __shfl_sync(FULL, base + 1 + nll, k);
+                warp_copy(dst, dk, src, ak, lk, lane);
+            }
+            o += __shfl_sync(FULL, incl, 31);
+            anchor = pos;
+        }
+    }
+    __syncwarp();
+    o = lz4_emit_last(dst, o, src, anchor, S, lane);
+    __syncwarp();
+    return o;
+}
+
 // Warp-parallel read of 255-continued length bytes at src[ip..]; adds them to
 // *len.  Returns false if the bytes run past index `clen` (the stream end).
 BSG_D bool lz4_read_len(const uint8_t *src, uint32_t clen, uint32_t &ip, uint32_t &len,

@@ -125,6 +125,14 @@ static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc
         cases.push_back(m);
         rows.push_back((uint32_t)(4 * (rng() % 8)));
     }
+    for (int t = 0; t < 16; t++) {
+        int S = 128 * (1 + (int)(rng() % 64));
+        std::vector<uint8_t> m(S);
+        int alpha = 1 + (int)(rng() % 3);
+        for (int i = 0; i < S; i++) m[i] = (i / (1 + rng() % 97)) % 5 == 0 ? (uint8_t)rng() : (uint8_t)(rng() % alpha);
+        cases.push_back(m);
+        rows.push_back((uint32_t)(S / 32));
+    }
     for (int t = 0; t < 4; t++) {
         std::vector<int32_t> w(2048);
         int32_t x = 0;
@@ -162,6 +170,18 @@ static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc
             if (cs2 != cs || memcmp(E, Bf, cs)) {
                 fprintf(stderr, "bitmap encoder differs S=%u rows=%u %u vs %u\n", S, rows[ci], cs2, cs);
                 bad++;
+            }
+            if (S % 128 == 0 && S <= 8192 && S > 0) {
+                uint32_t cs3 = 0;
+                memset(E, 0xCD, S + 64);
+                run_warp([&] {
+                    uint32_t o = lz4_encode_bitmap_fast(A, S, rows[ci], E);
+                    if (threadIdx.x == 0) cs3 = o;
+                });
+                if (cs3 != cs || memcmp(E, Bf, cs)) {
+                    fprintf(stderr, "fast bitmap encoder differs S=%u rows=%u %u vs %u\n", S, rows[ci], cs3, cs);
+                    bad++;
+                }
             }
         }
         std::vector<uint8_t> out(S + 1);

@@ -21,6 +21,7 @@ inline void __syncwarp(unsigned = 0xffffffffu) { g_warp->bar.arrive_and_wait(); 
 inline uint32_t __ballot_sync(uint32_t, int p) { g_warp->v[threadIdx.x] = p ? 1 : 0; g_warp->bar.arrive_and_wait(); uint32_t r = 0; for (int i = 0; i < 32; i++) r |= g_warp->v[i] << i; g_warp->bar.arrive_and_wait(); return r; }
 template <class T> inline T __shfl_sync(uint32_t, T x, int src) { static_assert(sizeof(T)==4); uint32_t u; memcpy(&u,&x,4); g_warp->v[threadIdx.x] = u; g_warp->bar.arrive_and_wait(); uint32_t r = g_warp->v[src & 31]; g_warp->bar.arrive_and_wait(); T o; memcpy(&o,&r,4); return o; }
 template <class T> inline T __shfl_up_sync(uint32_t, T x, unsigned d) { static_assert(sizeof(T)==4); uint32_t u; memcpy(&u,&x,4); g_warp->v[threadIdx.x] = u; g_warp->bar.arrive_and_wait(); uint32_t r = threadIdx.x >= d ? g_warp->v[threadIdx.x - d] : u; g_warp->bar.arrive_and_wait(); T o; memcpy(&o,&r,4); return o; }
+template <class T> inline T __shfl_down_sync(uint32_t, T x, unsigned d) { static_assert(sizeof(T)==4); uint32_t u; memcpy(&u,&x,4); g_warp->v[threadIdx.x] = u; g_warp->bar.arrive_and_wait(); uint32_t r = threadIdx.x + d < 32 ? g_warp->v[threadIdx.x + d] : u; g_warp->bar.arrive_and_wait(); T o; memcpy(&o,&r,4); return o; }
 template <class T> inline T __shfl_xor_sync(uint32_t, T x, int m) { uint64_t u = 0; memcpy(&u,&x,sizeof(T)); static thread_local int dummy; (void)dummy; uint64_t *v64 = reinterpret_cast<uint64_t *>(g_warp->v64); v64[threadIdx.x] = u; g_warp->bar.arrive_and_wait(); uint64_t r = v64[threadIdx.x ^ m]; g_warp->bar.arrive_and_wait(); T o; memcpy(&o,&r,sizeof(T)); return o; }
 inline uint32_t __match_any_sync(uint32_t, uint32_t x) { g_warp->v[threadIdx.x] = x; g_warp->bar.arrive_and_wait(); uint32_t r = 0; for (int i = 0; i < 32; i++) if (g_warp->v[i] == x) r |= 1u << i; g_warp->bar.arrive_and_wait(); return r; }
 inline int __ffs(uint32_t x) { return x ? __builtin_ctz(x) + 1 : 0; }
