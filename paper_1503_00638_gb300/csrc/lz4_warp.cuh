@@ -443,21 +443,24 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
     const uint32_t R = (rowlen & 3u) ? 0u : rowlen / 4;
     // equality bitmaps: bit w of Erow (Erun) set when word w equals word w - R (w - 1)
     uint32_t Erow[2] = {0u, 0u}, Erun[2] = {0u, 0u};
-    uint32_t prev_last = 0;  // lane 31's word of the previous bitmap word
+    uint32_t prev_last = ~s32[0];  // last word of the previous 32 (none before word 0)
 #pragma unroll
-    for (uint32_t k = 0; k < 64; k++) {
-        if (k < NB) {
-            const uint32_t w = 32 * k + lane;
+    for (uint32_t j = 0; j < 2; j++) {
+        const uint32_t kend = NB < 32 * (j + 1) ? (NB > 32 * j ? NB - 32 * j : 0u) : 32u;
+#pragma unroll 4
+        for (uint32_t kk = 0; kk < kend; kk++) {
+            const uint32_t w = 32 * (32 * j + kk) + lane;
             const uint32_t x = s32[w];
             uint32_t xp = __shfl_up_sync(FULL, x, 1);
-            if (lane == 0) xp = k ? prev_last : ~x;
+            if (lane == 0) xp = prev_last;
             prev_last = __shfl_sync(FULL, x, 31);
-            const uint32_t xr = (R && w >= R) ? s32[w - R] : ~x;
-            const uint32_t row = __ballot_sync(FULL, R && w >= R && x == xr);
-            const uint32_t run = __ballot_sync(FULL, w >= 1 && x == xp);
-            if (lane == (k & 31u)) {
-                Erow[k >> 5] = row;
-                Erun[k >> 5] = run;
+            const bool rowok = w >= R && R != 0;
+            const uint32_t xr = s32[rowok ? w - R : w];
+            const uint32_t row = __ballot_sync(FULL, rowok && x == xr);
+            const uint32_t run = __ballot_sync(FULL, x == xp);
+            if (lane == kk) {
+                Erow[j] = row;
+                Erun[j] = run;
             }
         }
     }
