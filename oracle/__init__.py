@@ -76,6 +76,12 @@ def lib() -> ctypes.CDLL:
             L.orc_reduce_precision_c64.restype = None
             L.orc_granularity_map_c64.argtypes = [c_vp, c_vp, c_l, c_l, c_l, c_d, c_d]
             L.orc_granularity_map_c64.restype = None
+            L.orc_round_int.argtypes = [ctypes.c_int32, c_i]
+            L.orc_round_int.restype = ctypes.c_int32
+            L.orc_compensation_min.argtypes = [c_vp, c_i, c_l, c_l, c_l, c_l, c_l]
+            L.orc_compensation_min.restype = c_f
+            L.orc_reduce_precision.argtypes = [c_vp, c_vp, c_i, c_l, c_l, c_l, c_d, c_d, c_i]
+            L.orc_reduce_precision.restype = None
             L.orc_bitshuffle.argtypes = [c_vp, c_vp, c_sz, c_sz, c_sz, c_i]
             L.orc_bitshuffle.restype = c_i
             L.orc_lz4_bound.argtypes = [c_sz]
@@ -144,6 +150,39 @@ def reduce_precision_c64(vis: np.ndarray, N: float, f: float) -> np.ndarray:
     out = np.empty_like(vis)
     lib().orc_reduce_precision_c64(_ptr(vis), _ptr(out), F, n, T, N, f)
     return out
+
+
+def round_int(x: int, k: int) -> int:
+    """Integer data: nearest multiple of 2^k, ties to even (R17 on overflow)."""
+    return int(lib().orc_round_int(int(x), int(k)))
+
+
+def compensation_min(vis: np.ndarray, fr: int, t: int) -> np.float32:
+    """Sec. 3.2: min over crosses of 1 - |V_ij|^2 / (V_ii V_jj) at (fr, t) (R18)."""
+    F, P, T, is_int, a = _cube(vis)
+    return np.float32(lib().orc_compensation_min(_ptr(a), is_int, F, _n_inputs(P), T, fr, t))
+
+
+def reduce_precision(vis: np.ndarray, N: float, f: float, compensate: bool = False) -> np.ndarray:
+    """Round a [F][P][T] cube of complex64, or of int32 (re, im) pairs given as
+    an int32 array of shape [F][P][T][2], per Sec. 6 steps 1-3 (and the
+    compensated f of Sec. 3.2 when asked)."""
+    F, P, T, is_int, a = _cube(vis)
+    out = np.empty_like(a)
+    lib().orc_reduce_precision(_ptr(a), _ptr(out), is_int, F, _n_inputs(P), T, N, f,
+                               int(bool(compensate)))
+    return out
+
+
+def _cube(vis):
+    if vis.dtype == np.int32:
+        a = np.ascontiguousarray(vis)
+        assert a.ndim == 4 and a.shape[3] == 2
+        F, P, T = a.shape[:3]
+        return F, P, T, 1, a
+    a = np.ascontiguousarray(vis, dtype=np.complex64)
+    F, P, T = a.shape
+    return F, P, T, 0, a
 
 
 def granularity_map_c64(vis: np.ndarray, N: float, f: float) -> np.ndarray:

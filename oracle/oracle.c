@@ -30,6 +30,10 @@
  *   R11 compressed framing: 8-byte big-endian uncompressed byte count, 4-byte
  *       big-endian block size in bytes, then per block a 4-byte big-endian
  *       compressed length followed by the LZ4 block, then the verbatim tail.
+ *   R17 integer data: granularity 2^k with k <= 0 leaves the value alone; a
+ *       nearest multiple above INT32_MAX is replaced by the lower multiple.
+ *   R18 the compensated f of Sec. 3.2 is evaluated per (freq, time) sample,
+ *       in float32 as stated at orc_compensation_min.
  */
 #include <stddef.h>
 #include <stdint.h>
@@ -155,6 +159,108 @@ void orc_reduce_precision_c64(const float *in, float *out, long n_freq, long n_i
                         float q = orc_q32(0, Ai, Aj, f, N);
                         out[e] = orc_round_element(in[e], q);
                         out[e + 1] = orc_round_element(in[e + 1], q);
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* ---- Integer visibilities (Sec. 3, Sec. 5: CHIME records int32 re/im) ---- */
+
+/* Round an int32 to the nearest multiple of g = 2^k, ties to the even
+ * multiple.  k <= 0 means g <= 1: no rounding (Sec. 5.1: a granularity of
+ * unity implies no rounding for integers).  Reading R17: when the nearest
+ * multiple is above INT32_MAX, the lower multiple is taken.  Exact in int64. */
+int32_t orc_round_int(int32_t x, int k)
+{
+    if (k <= 0) return x;
+    if (k > 62) return 0;            /* |x| < 2^31 < g/2 */
+    int64_t g = (int64_t)1 << k;
+    int64_t m = (int64_t)x / g;      /* toward zero; make it the floor */
+    if ((int64_t)x - m * g < 0) m--;
+    int64_t r = (int64_t)x - m * g;  /* 0 <= r < g */
+    if (2 * r > g || (2 * r == g && (m & 1))) m++;
+    int64_t y = m * g;
+    if (y > INT32_MAX) y -= g;
+    return (int32_t)y;
+}
+
+/* ---- Sec. 3.2: compensating f for correlated noise ----
+ * f is multiplied by the minimum over cross products (i != j) of
+ * 1 - V_ij V_ij^* / (V_ii V_jj).  Reading R18: per (freq, time) sample, with
+ * rho = fl32(fl32(fl32(re re) + fl32(im im)) / fl32(A_i A_j)) and
+ * 1 - rho in float32; a negative or NaN value counts as 0 (no rounding for
+ * that sample), no cross product gives 1; the compensated constant is
+ * c = fl32(6 f m / N) evaluated in fp64.  Values are float32 components, or
+ * int32 components converted to float32 (round to nearest). */
+static float comp_value(const void *in, int is_int, long idx)
+{
+    return is_int ? (float)((const int32_t *)in)[idx] : ((const float *)in)[idx];
+}
+
+float orc_compensation_min(const void *in, int is_int, long n_freq, long n_in, long n_time,
+                           long fr, long t)
+{
+    long n_prod = n_in * (n_in + 1) / 2;
+    float m = 1.0f;
+    long p = 0;
+    for (long i = 0; i < n_in; i++) {
+        for (long j = i; j < n_in; j++, p++) {
+            if (i == j) continue;
+            long pii = i * n_in - i * (i - 1) / 2;
+            long pjj = j * n_in - j * (j - 1) / 2;
+            float Ai = comp_value(in, is_int, ((fr * n_prod + pii) * n_time + t) * 2);
+            float Aj = comp_value(in, is_int, ((fr * n_prod + pjj) * n_time + t) * 2);
+            float re = comp_value(in, is_int, ((fr * n_prod + p) * n_time + t) * 2);
+            float im = comp_value(in, is_int, ((fr * n_prod + p) * n_time + t) * 2 + 1);
+            float num = re * re + im * im;   /* each product rounded, then the sum */
+            float den = Ai * Aj;
+            float rho = num / den;
+            float om = 1.0f - rho;
+            if (!(om >= 0.0f)) om = 0.0f;
+            if (om < m) m = om;
+        }
+    }
+    (void)n_freq;
+    return m;
+}
+
+/* Precision reduction of a cube of float32 (is_int = 0) or int32 (is_int = 1)
+ * complex samples, optionally with the compensated f per (freq, time).
+ * Otherwise as orc_reduce_precision_c64. */
+void orc_reduce_precision(const void *in, void *out, int is_int, long n_freq, long n_in,
+                          long n_time, double N, double f, int compensate)
+{
+    long n_prod = n_in * (n_in + 1) / 2;
+    for (long fr = 0; fr < n_freq; fr++) {
+        for (long t = 0; t < n_time; t++) {
+            double fe = f;
+            if (compensate) {
+                float m = orc_compensation_min(in, is_int, n_freq, n_in, n_time, fr, t);
+                fe = f * (double)m;
+            }
+            float c = (float)(6.0 * fe / N);   /* as orc_q32 with f = fe (fe = f when m = 1) */
+            float c2 = 2.0f * c;
+            long p = 0;
+            for (long i = 0; i < n_in; i++) {
+                for (long j = i; j < n_in; j++, p++) {
+                    long e = ((fr * n_prod + p) * n_time + t) * 2;
+                    long pii = i * n_in - i * (i - 1) / 2;
+                    long pjj = j * n_in - j * (j - 1) / 2;
+                    float Ai = comp_value(in, is_int, ((fr * n_prod + pii) * n_time + t) * 2);
+                    float Aj = comp_value(in, is_int, ((fr * n_prod + pjj) * n_time + t) * 2);
+                    float q = (i == j) ? (c2 * Ai) * Ai : (c * Ai) * Aj;
+                    int k, ok = orc_granularity_exponent(q, &k);
+                    for (int part = 0; part < 2; part++) {
+                        int rounded = ok && !(i == j && part == 1);
+                        if (is_int) {
+                            int32_t x = ((const int32_t *)in)[e + part];
+                            ((int32_t *)out)[e + part] = rounded ? orc_round_int(x, k) : x;
+                        } else {
+                            float x = ((const float *)in)[e + part];
+                            ((float *)out)[e + part] = rounded ? orc_round_pow2(x, k) : x;
+                        }
                     }
                 }
             }
