@@ -46,6 +46,13 @@ extern "C" {
 #define BSGPU_OP_COMPRESS_VIS 3
 #define BSGPU_OP_REDUCE_PRECISION 4
 
+/* Data types of a visibility cube (the _ex entry points). */
+#define BSGPU_VIS_F32 0  /* interleaved float32 (re, im): complex64            */
+#define BSGPU_VIS_I32 1  /* interleaved int32 (re, im), as correlators emit   */
+
+/* Flags of the _ex entry points. */
+#define BSGPU_VIS_COMPENSATE 1  /* Sec. 3.2: per-sample compensated f, see below */
+
 /* Library version string. */
 const char *bsgpu_version(void);
 
@@ -76,6 +83,13 @@ size_t bsgpu_workspace_size(int op, size_t n_elem, size_t elem_size, size_t bloc
 size_t bsgpu_vis_workspace_size(int op, int64_t n_freq, int64_t n_inputs, int64_t n_time,
                                 size_t block_elems);
 
+/* As bsgpu_vis_workspace_size, for bsgpu_compress_vis_ex (elem_size 4 or 8)
+ * and bsgpu_reduce_precision_ex (elem_size ignored) with these flags (the
+ * compensated f needs one more float per (freq, time) sample).  The data type
+ * does not change the size.  0 for bad arguments. */
+size_t bsgpu_vis_workspace_size_ex(int op, int64_t n_freq, int64_t n_inputs, int64_t n_time,
+                                   size_t elem_size, size_t block_elems, int flags);
+
 /* Read the device status word of a workspace: waits for `stream`, then
  * copies the word to *status (BSGPU_OK or a negative BSGPU_ERR_*).  Returns
  * BSGPU_OK, or BSGPU_ERR_CUDA if the copy itself failed. */
@@ -100,6 +114,28 @@ int bsgpu_status(const void *ws, void *stream, int *status);
 int bsgpu_reduce_precision_c64(const void *in, void *out, int64_t n_freq, int64_t n_inputs,
                                int64_t n_time, double N, double f, void *ws, size_t ws_bytes,
                                void *stream);
+
+/* bsgpu_reduce_precision_c64 generalised (Sec. 3.2):
+ *   dtype : BSGPU_VIS_F32, or BSGPU_VIS_I32 for a cube of int32 (re, im)
+ *           pairs (same layout).  An int32 component is rounded to the
+ *           nearest multiple of g = 2^k, ties to the even multiple; k <= 0
+ *           (a granularity of one or less) leaves it alone, and a multiple
+ *           beyond INT32_MAX is replaced by the one below it.  q is formed
+ *           from the autos converted to float32 (round to nearest).
+ *   flags : 0, or BSGPU_VIS_COMPENSATE: the rounding noise adds to the
+ *           correlated noise of two inputs, which raises the noise of
+ *           products built from them; Sec. 3.2 bounds that increase by
+ *           using f m instead of f at each (freq, time) sample, where
+ *           m = min over cross products i != j of 1 - |V_ij|^2 / (V_ii V_jj)
+ *           (one minus the squared correlation coefficient), evaluated in
+ *           float32 with each operation rounded (|V_ij|^2 as re*re + im*im),
+ *           a negative or undefined value counting as 0, and m = 1 with one
+ *           input.  c is then fl32(6 (f m) / N) with f m, 6 (f m) and the
+ *           quotient in fp64.
+ * ws: bsgpu_vis_workspace_size_ex(BSGPU_OP_REDUCE_PRECISION, ..., flags). */
+int bsgpu_reduce_precision_ex(const void *in, void *out, int dtype, int64_t n_freq,
+                              int64_t n_inputs, int64_t n_time, double N, double f, int flags,
+                              void *ws, size_t ws_bytes, void *stream);
 
 /* Sec. 4.2 and Sec. 6 step 4: Bitshuffle.  Within each block of block_elems
  * elements (a multiple of 8; 0 = 4096 bytes), bit r of element e (r = 8 *
@@ -161,6 +197,19 @@ int bsgpu_compress_vis(const void *vis, int64_t n_freq, int64_t n_inputs, int64_
                        size_t out_cap,
                        uint64_t *d_out_bytes, uint64_t *d_block_offsets, void *ws,
                        size_t ws_bytes, void *stream);
+
+/* bsgpu_compress_vis generalised: dtype and flags as for
+ * bsgpu_reduce_precision_ex; elem_size 4 compresses the rounded cube as
+ * 2 n_freq n_prod n_time 4-byte components, elem_size 8 as n_freq n_prod
+ * n_time 8-byte (re, im) samples (the bit-rows then interleave the two
+ * components' bits, Sec. 4.2).  Decode with bsgpu_decompress(elem_size).
+ * ws: bsgpu_vis_workspace_size_ex(BSGPU_OP_COMPRESS_VIS, ..., elem_size,
+ * block_elems, flags) bytes. */
+int bsgpu_compress_vis_ex(const void *vis, int dtype, int64_t n_freq, int64_t n_inputs,
+                          int64_t n_time, double N, double f, int flags, size_t elem_size,
+                          size_t block_elems, int level, void *out, size_t out_cap,
+                          uint64_t *d_out_bytes, uint64_t *d_block_offsets, void *ws,
+                          size_t ws_bytes, void *stream);
 
 /* bsgpu_compress for callers that cannot allocate device memory (the paper
  * has no counterpart: this is a deployment variant).  Such callers are handed

@@ -22,6 +22,8 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 OK, ERR_ARG, ERR_SPACE, ERR_CORRUPT, ERR_CUDA, ERR_TIMEOUT, ERR_ALIGN = 0, -1, -2, -3, -4, -5, -6
 OP_COMPRESS, OP_DECOMPRESS, OP_COMPRESS_VIS, OP_REDUCE_PRECISION = 1, 2, 3, 4
+VIS_F32, VIS_I32 = 0, 1
+VIS_COMPENSATE = 1
 _NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_SPACE", -3: "ERR_CORRUPT", -4: "ERR_CUDA",
           -5: "ERR_TIMEOUT", -6: "ERR_ALIGN"}
 
@@ -32,14 +34,19 @@ _SIGS = {
     "bsgpu_num_blocks": ([_sz, _sz, _sz], _sz),
     "bsgpu_workspace_size": ([_i, _sz, _sz, _sz], _sz),
     "bsgpu_vis_workspace_size": ([_i, _i64, _i64, _i64, _sz], _sz),
+    "bsgpu_vis_workspace_size_ex": ([_i, _i64, _i64, _i64, _sz, _sz, _i], _sz),
     "bsgpu_status": ([_vp, _vp, ctypes.POINTER(_i)], _i),
     "bsgpu_reduce_precision_c64": ([_vp, _vp, _i64, _i64, _i64, _d, _d, _vp, _sz, _vp], _i),
+    "bsgpu_reduce_precision_ex": ([_vp, _vp, _i, _i64, _i64, _i64, _d, _d, _i, _vp, _sz, _vp],
+                                  _i),
     "bsgpu_bitshuffle": ([_vp, _vp, _sz, _sz, _sz, _vp], _i),
     "bsgpu_bitunshuffle": ([_vp, _vp, _sz, _sz, _sz, _vp], _i),
     "bsgpu_compress": ([_vp, _sz, _sz, _sz, _i, _vp, _sz, _vp, _vp, _vp, _sz, _vp], _i),
     "bsgpu_decompress": ([_vp, _sz, _vp, _sz, _sz, _sz, _vp, _vp, _sz, _vp], _i),
     "bsgpu_compress_vis": ([_vp, _i64, _i64, _i64, _d, _d, _sz, _i, _vp, _sz, _vp, _vp, _vp,
                             _sz, _vp], _i),
+    "bsgpu_compress_vis_ex": ([_vp, _i, _i64, _i64, _i64, _d, _d, _i, _sz, _sz, _i, _vp, _sz,
+                               _vp, _vp, _vp, _sz, _vp], _i),
     "bsgpu_compress_noalloc": ([_vp, _sz, _sz, _sz, _i, _vp, _sz, _vp, _vp, _vp], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -105,6 +112,12 @@ def vis_workspace_size(op: int, n_freq: int, n_inputs: int, n_time: int,
     return _lib.bsgpu_vis_workspace_size(op, n_freq, n_inputs, n_time, block_elems)
 
 
+def vis_workspace_size_ex(op: int, n_freq: int, n_inputs: int, n_time: int, elem_size: int = 4,
+                          block_elems: int = 0, flags: int = 0) -> int:
+    return _lib.bsgpu_vis_workspace_size_ex(op, n_freq, n_inputs, n_time, elem_size, block_elems,
+                                            flags)
+
+
 def status(ws: torch.Tensor, stream=None) -> int:
     """Device status word of a workspace (waits for the stream)."""
     st = ctypes.c_int(0)
@@ -130,6 +143,34 @@ def reduce_precision_c64(vis: torch.Tensor, N: float, f: float, out: torch.Tenso
     _check(_lib.bsgpu_reduce_precision_c64(_ptr(vis), _ptr(out), F, n, T, float(N), float(f),
                                            _ptr(ws), ws.numel(), _stream(stream)),
            "bsgpu_reduce_precision_c64")
+    return out
+
+
+def _cube(vis: torch.Tensor):
+    """(n_freq, n_inputs, n_time, dtype code) of a complex64 [F][P][T] cube or
+    an int32 [F][P][T][2] cube of (re, im) pairs."""
+    if vis.dtype == torch.complex64 and vis.dim() == 3:
+        F, P, T = vis.shape
+        return F, _n_inputs(P), T, VIS_F32
+    if vis.dtype == torch.int32 and vis.dim() == 4 and vis.shape[3] == 2:
+        F, P, T, _ = vis.shape
+        return F, _n_inputs(P), T, VIS_I32
+    raise ValueError("expected a complex64 [F][P][T] or int32 [F][P][T][2] cube")
+
+
+def reduce_precision(vis: torch.Tensor, N: float, f: float, compensate: bool = False,
+                     out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    """Round a complex64 or int32 cube, optionally with Sec. 3.2's
+    compensated f (returns out)."""
+    F, n, T, dt = _cube(vis)
+    flags = VIS_COMPENSATE if compensate else 0
+    out = torch.empty_like(vis) if out is None else out
+    need = vis_workspace_size_ex(OP_REDUCE_PRECISION, F, n, T, 4, 0, flags)
+    ws = new_workspace(need, vis.device) if ws is None else ws
+    _check(_lib.bsgpu_reduce_precision_ex(_ptr(vis), _ptr(out), dt, F, n, T, float(N), float(f),
+                                          flags, _ptr(ws), ws.numel(), _stream(stream)),
+           "bsgpu_reduce_precision_ex")
     return out
 
 
@@ -217,6 +258,31 @@ def compress_vis(vis: torch.Tensor, N: float, f: float, block_elems: int = 0,
                                    level, _ptr(out), out.numel(), _ptr(nb_dev), _ptr(offs), _ptr(ws),
                                    ws.numel(), _stream(stream)), "bsgpu_compress_vis")
     return Compressed(out, nb_dev, offs, n, 4, block_elems, ws)
+
+
+def compress_vis_ex(vis: torch.Tensor, N: float, f: float, compensate: bool = False,
+                    elem_size: int = 4, block_elems: int = 0, out: torch.Tensor | None = None,
+                    with_offsets: bool = True, ws: torch.Tensor | None = None, stream=None,
+                    level: int = 0) -> Compressed:
+    """Precision reduction (complex64 or int32 cube, optionally compensated)
+    + Bitshuffle + LZ4 with 4-byte components or 8-byte samples as elements."""
+    F, n_in, T, dt = _cube(vis)
+    flags = VIS_COMPENSATE if compensate else 0
+    n = F * (n_in * (n_in + 1) // 2) * T * 8 // elem_size
+    cap = compress_bound(n, elem_size, block_elems)
+    if cap == 0:
+        raise BsgpuError(ERR_ARG, "bsgpu_compress_bound")
+    out = torch.empty(cap, dtype=torch.uint8, device=vis.device) if out is None else out
+    nb_dev = torch.zeros(1, dtype=torch.int64, device=vis.device)
+    nblk = num_blocks(n, elem_size, block_elems)
+    offs = torch.empty(max(nblk, 1), dtype=torch.int64, device=vis.device) if with_offsets else None
+    need = vis_workspace_size_ex(OP_COMPRESS_VIS, F, n_in, T, elem_size, block_elems, flags)
+    ws = new_workspace(need, vis.device) if ws is None else ws
+    _check(_lib.bsgpu_compress_vis_ex(_ptr(vis), dt, F, n_in, T, float(N), float(f), flags,
+                                      elem_size, block_elems, level, _ptr(out), out.numel(),
+                                      _ptr(nb_dev), _ptr(offs), _ptr(ws), ws.numel(),
+                                      _stream(stream)), "bsgpu_compress_vis_ex")
+    return Compressed(out, nb_dev, offs, n, elem_size, block_elems, ws)
 
 
 def decompress(stream_buf: torch.Tensor, in_bytes: int, n_elem: int, elem_size: int,

@@ -76,17 +76,19 @@ uint32_t persistent_grid(uint32_t smem_per_cta, uint64_t work)
 }
 
 struct WsLayout {
-    size_t state, autos, pairs, offsets, slots, total;
+    size_t state, autos, pairs, cft, offsets, slots, total;
 };
 
 // Whether compress takes the fast kernel (full blocks of at most 8 KiB of 4-
-// or 8-byte elements; a cube also needs n_time % 16 == 0).
+// or 8-byte elements; a cube of 4-byte components also needs n_time % 16 == 0).
 bool fast_shape(const Geometry &g, uint64_t n_time)
 {
-    return shuffle_inplace_ok(g.es, g.B) && (n_time == 0 || n_time % 16 == 0);
+    return shuffle_inplace_ok(g.es, g.B) && (n_time == 0 || g.es == 8 || n_time % 16 == 0);
 }
 
-WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint64_t n_time = 0)
+// n_ft: entries of the per-(freq, time) compensated-c table (0 = none)
+WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint64_t n_time = 0,
+                   size_t n_ft = 0)
 {
     WsLayout L{};
     size_t o = WS_HEADER;
@@ -103,6 +105,10 @@ WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint
         o += r256(n_auto * 4);
         L.pairs = o;
         o += r256(n_prod * 4);
+        if (n_ft) {
+            L.cft = o;
+            o += r256(n_ft * 4);
+        }
     }
     if (op == BSGPU_OP_DECOMPRESS) {
         L.offsets = o;
@@ -128,9 +134,11 @@ int vis_check(int64_t n_freq, int64_t n_in, int64_t n_time, double N, double f, 
 }
 
 VisParams vis_params(const WsLayout &L, void *ws, uint64_t n_in, uint64_t n_time, uint64_t n_prod,
-                     double N, double f)
+                     double N, double f, int is_int = 0)
 {
     VisParams v{};
+    v.is_int = is_int;
+    v.cft = L.cft ? reinterpret_cast<const float *>((uint8_t *)ws + L.cft) : nullptr;
     v.autos = reinterpret_cast<const float *>((uint8_t *)ws + L.autos);
     v.pairs = reinterpret_cast<const uint32_t *>((uint8_t *)ws + L.pairs);
     v.n_in = (uint32_t)n_in;
@@ -142,6 +150,26 @@ VisParams vis_params(const WsLayout &L, void *ws, uint64_t n_in, uint64_t n_time
     v.c2 = 2.0f * v.c;            // autos: s^2 = A_i^2 / N
     v.enabled = 1;
     return v;
+}
+
+int vis_dtype_ok(int dtype, int flags)
+{
+    if (dtype != BSGPU_VIS_F32 && dtype != BSGPU_VIS_I32) return 0;
+    return (flags & ~BSGPU_VIS_COMPENSATE) == 0;
+}
+
+// The tables (autos, product indices) and, when asked, the compensated c
+// per (freq, time): everything the rounding kernels read besides the cube.
+int vis_prepare(const void *vis, const VisParams &v, int64_t n_freq, int64_t n_inputs,
+                int64_t n_time, double N, double f, cudaStream_t s)
+{
+    cudaError_t e = launch_vis_tables(reinterpret_cast<const float *>(vis),
+                                      const_cast<float *>(v.autos),
+                                      const_cast<uint32_t *>(v.pairs), (uint32_t)n_freq,
+                                      (uint32_t)n_inputs, (uint32_t)n_time, v.is_int, s);
+    if (e != cudaSuccess) return BSGPU_ERR_CUDA;
+    if (v.cft) e = launch_vis_compensation(vis, v, (uint32_t)n_freq, f, N, s);
+    return e == cudaSuccess ? BSGPU_OK : BSGPU_ERR_CUDA;
 }
 
 }  // namespace
@@ -172,16 +200,27 @@ size_t bsgpu_workspace_size(int op, size_t n_elem, size_t elem_size, size_t bloc
     return ws_layout(op, g, 0, 0).total;
 }
 
-size_t bsgpu_vis_workspace_size(int op, int64_t n_freq, int64_t n_inputs, int64_t n_time,
-                                size_t block_elems)
+size_t bsgpu_vis_workspace_size_ex(int op, int64_t n_freq, int64_t n_inputs, int64_t n_time,
+                                   size_t elem_size, size_t block_elems, int flags)
 {
     uint64_t n_prod, n_cplx;
     if (op != BSGPU_OP_COMPRESS_VIS && op != BSGPU_OP_REDUCE_PRECISION) return 0;
+    if (!vis_dtype_ok(BSGPU_VIS_F32, flags)) return 0;
     if (vis_check(n_freq, n_inputs, n_time, 1.0, 0.0, n_prod, n_cplx) != BSGPU_OK) return 0;
     Geometry g{};
-    if (op == BSGPU_OP_COMPRESS_VIS && geometry(2 * n_cplx, 4, block_elems, g) != BSGPU_OK)
-        return 0;
-    return ws_layout(op, g, (uint64_t)n_freq * n_inputs * n_time, n_prod, (uint64_t)n_time).total;
+    if (op == BSGPU_OP_COMPRESS_VIS) {
+        if (elem_size != 4 && elem_size != 8) return 0;
+        if (geometry(n_cplx * 8 / elem_size, elem_size, block_elems, g) != BSGPU_OK) return 0;
+    }
+    const size_t n_ft = (flags & BSGPU_VIS_COMPENSATE) ? (size_t)n_freq * n_time : 0;
+    return ws_layout(op, g, (uint64_t)n_freq * n_inputs * n_time, n_prod, (uint64_t)n_time, n_ft)
+        .total;
+}
+
+size_t bsgpu_vis_workspace_size(int op, int64_t n_freq, int64_t n_inputs, int64_t n_time,
+                                size_t block_elems)
+{
+    return bsgpu_vis_workspace_size_ex(op, n_freq, n_inputs, n_time, 4, block_elems, 0);
 }
 
 int bsgpu_status(const void *ws, void *stream, int *status)
@@ -196,27 +235,26 @@ int bsgpu_status(const void *ws, void *stream, int *status)
     return BSGPU_OK;
 }
 
-int bsgpu_reduce_precision_c64(const void *in, void *out, int64_t n_freq, int64_t n_inputs,
-                               int64_t n_time, double N, double f, void *ws, size_t ws_bytes,
-                               void *stream)
+int bsgpu_reduce_precision_ex(const void *in, void *out, int dtype, int64_t n_freq,
+                              int64_t n_inputs, int64_t n_time, double N, double f, int flags,
+                              void *ws, size_t ws_bytes, void *stream)
 {
     uint64_t n_prod, n_cplx;
+    if (!vis_dtype_ok(dtype, flags)) return BSGPU_ERR_ARG;
     int rc = vis_check(n_freq, n_inputs, n_time, N, f, n_prod, n_cplx);
     if (rc) return rc;
     if (!in || !out || !ws) return BSGPU_ERR_ARG;
     if (!aligned16(in) || !aligned16(out) || !aligned16(ws)) return BSGPU_ERR_ALIGN;
     Geometry g{};
     uint64_t n_auto = (uint64_t)n_freq * n_inputs * n_time;
-    WsLayout L = ws_layout(BSGPU_OP_REDUCE_PRECISION, g, n_auto, n_prod);
+    const size_t n_ft = (flags & BSGPU_VIS_COMPENSATE) ? (size_t)n_freq * n_time : 0;
+    WsLayout L = ws_layout(BSGPU_OP_REDUCE_PRECISION, g, n_auto, n_prod, 0, n_ft);
     if (ws_bytes < L.total) return BSGPU_ERR_SPACE;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(ws, 0, WS_HEADER, s) != cudaSuccess) return BSGPU_ERR_CUDA;
-    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f);
-    cudaError_t e = launch_vis_tables(reinterpret_cast<const float *>(in),
-                                      const_cast<float *>(v.autos),
-                                      const_cast<uint32_t *>(v.pairs), (uint32_t)n_freq,
-                                      (uint32_t)n_inputs, (uint32_t)n_time, s);
-    if (e != cudaSuccess) return BSGPU_ERR_CUDA;
+    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32);
+    rc = vis_prepare(in, v, n_freq, n_inputs, n_time, N, f, s);
+    if (rc) return rc;
     // 256-thread blocks, each warp rounding runs of 1024 samples
     uint64_t runs = (n_cplx + 1023) / 1024;
     int dev = 0, sms = 148;
@@ -227,6 +265,14 @@ int bsgpu_reduce_precision_c64(const void *in, void *out, int64_t n_freq, int64_
     if (grid == 0) grid = 1;
     return cuda_err(launch_reduce_precision(reinterpret_cast<const float *>(in),
                                             reinterpret_cast<float *>(out), n_cplx, v, grid, s));
+}
+
+int bsgpu_reduce_precision_c64(const void *in, void *out, int64_t n_freq, int64_t n_inputs,
+                               int64_t n_time, double N, double f, void *ws, size_t ws_bytes,
+                               void *stream)
+{
+    return bsgpu_reduce_precision_ex(in, out, BSGPU_VIS_F32, n_freq, n_inputs, n_time, N, f, 0,
+                                     ws, ws_bytes, stream);
 }
 
 static int shuffle_common(const void *in, void *out, size_t n_elem, size_t elem_size,
@@ -340,34 +386,46 @@ int bsgpu_compress(const void *in, size_t n_elem, size_t elem_size, size_t block
                            ws_bytes, stream, nullptr, L);
 }
 
-int bsgpu_compress_vis(const void *vis, int64_t n_freq, int64_t n_inputs, int64_t n_time,
-                       double N, double f, size_t block_elems, int level, void *out,
-                       size_t out_cap,
-                       uint64_t *d_out_bytes, uint64_t *d_block_offsets, void *ws,
-                       size_t ws_bytes, void *stream)
+int bsgpu_compress_vis_ex(const void *vis, int dtype, int64_t n_freq, int64_t n_inputs,
+                          int64_t n_time, double N, double f, int flags, size_t elem_size,
+                          size_t block_elems, int level, void *out, size_t out_cap,
+                          uint64_t *d_out_bytes, uint64_t *d_block_offsets, void *ws,
+                          size_t ws_bytes, void *stream)
 {
     uint64_t n_prod, n_cplx;
+    if (!vis_dtype_ok(dtype, flags) || (elem_size != 4 && elem_size != 8)) return BSGPU_ERR_ARG;
     int rc = vis_check(n_freq, n_inputs, n_time, N, f, n_prod, n_cplx);
     if (rc) return rc;
     Geometry g;
-    rc = geometry(2 * n_cplx, 4, block_elems, g);
+    rc = geometry(n_cplx * 8 / elem_size, elem_size, block_elems, g);
     if (rc) return rc;
     if (!vis || !out || !d_out_bytes || !ws) return BSGPU_ERR_ARG;
     if (!aligned16(vis) || !aligned16(ws) || ((uintptr_t)d_out_bytes & 7u) ||
         ((uintptr_t)d_block_offsets & 7u))
         return BSGPU_ERR_ALIGN;
     uint64_t n_auto = (uint64_t)n_freq * n_inputs * n_time;
-    WsLayout L = ws_layout(BSGPU_OP_COMPRESS_VIS, g, n_auto, n_prod, (uint64_t)n_time);
+    const size_t n_ft = (flags & BSGPU_VIS_COMPENSATE) ? (size_t)n_freq * n_time : 0;
+    WsLayout L = ws_layout(BSGPU_OP_COMPRESS_VIS, g, n_auto, n_prod, (uint64_t)n_time, n_ft);
     if (ws_bytes < L.total) return BSGPU_ERR_SPACE;
-    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f);
+    if (level < 0 || level > 1) return BSGPU_ERR_ARG;
+    if (out_cap < stream_bound(g)) return BSGPU_ERR_SPACE;
+    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = launch_vis_tables(reinterpret_cast<const float *>(vis),
-                                      const_cast<float *>(v.autos),
-                                      const_cast<uint32_t *>(v.pairs), (uint32_t)n_freq,
-                                      (uint32_t)n_inputs, (uint32_t)n_time, s);
-    if (e != cudaSuccess) return BSGPU_ERR_CUDA;
+    rc = vis_prepare(vis, v, n_freq, n_inputs, n_time, N, f, s);
+    if (rc) return rc;
     return compress_common(vis, g, level, out, out_cap, d_out_bytes, d_block_offsets, ws,
                            ws_bytes, stream, &v, L);
+}
+
+int bsgpu_compress_vis(const void *vis, int64_t n_freq, int64_t n_inputs, int64_t n_time,
+                       double N, double f, size_t block_elems, int level, void *out,
+                       size_t out_cap,
+                       uint64_t *d_out_bytes, uint64_t *d_block_offsets, void *ws,
+                       size_t ws_bytes, void *stream)
+{
+    return bsgpu_compress_vis_ex(vis, BSGPU_VIS_F32, n_freq, n_inputs, n_time, N, f, 0, 4,
+                                 block_elems, level, out, out_cap, d_out_bytes, d_block_offsets,
+                                 ws, ws_bytes, stream);
 }
 
 int bsgpu_decompress(const void *in, size_t in_bytes, void *out, size_t n_elem, size_t elem_size,

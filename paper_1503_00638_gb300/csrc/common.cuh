@@ -144,6 +144,36 @@ BSG_D float reduce_one(float x, float q)
 }
 #endif
 
+// Integer data: nearest multiple of 2^k, ties to the even multiple; k <= 0
+// leaves x alone (a granularity of one or less); a nearest multiple above
+// INT32_MAX is replaced by the lower one.  k is at most 63 here.
+BSG_HD int32_t round_int_pow2(int32_t x, int k)
+{
+    if (k <= 0) return x;
+    if (k >= 32) return 0;  // |x| <= 2^31 <= g / 2: the nearest (even) multiple is 0
+    const int64_t g = (int64_t)1 << k;
+    int64_t m = (int64_t)x >> k;  // floor
+    const int64_t r = (int64_t)x - m * g, h = g >> 1;
+    if (r > h || (r == h && (m & 1))) m++;
+    int64_t y = m * g;
+    if (y > INT32_MAX) y -= g;
+    return (int32_t)y;
+}
+
+// granularity exponent k = max{k : 4^k < q} from q's bits (see magic_bits)
+BSG_HD int granularity_k(uint32_t Q) { return (int)((Q + 0x007fffffu) >> 24) - 64; }
+
+#ifdef __CUDACC__
+// Round one component given as its 32 bits: float32, or int32 when is_int.
+BSG_D uint32_t reduce_bits(uint32_t xb, float q, bool is_int)
+{
+    const uint32_t Q = __float_as_uint(q);
+    if (!q_usable(Q)) return xb;
+    if (is_int) return (uint32_t)round_int_pow2((int32_t)xb, granularity_k(Q));
+    return __float_as_uint(round_to_granularity(__uint_as_float(xb), magic_bits(Q)));
+}
+#endif
+
 // ---------------------------------------------------------------------------
 // PTX wrappers: mbarrier, bulk (TMA) copies, relaxed/acquire global accesses
 // ---------------------------------------------------------------------------

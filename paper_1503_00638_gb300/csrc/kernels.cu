@@ -161,30 +161,26 @@ BSG_D void write_chunk_header(uint8_t *out, uint64_t total, uint32_t block_bytes
 // ---------------------------------------------------------------------------
 // Precision reduction of complex samples (Sec. 3.2, Sec. 6 steps 1-3)
 // ---------------------------------------------------------------------------
-// Round one complex sample (re, im) of product p = (i, j) at (f, t).
-BSG_D float2 reduce_sample(float2 v, uint32_t ij, uint32_t f, uint32_t t, const VisParams &P)
+// Round one complex sample (re, im bits) of product p = (i, j) at (f, t).
+BSG_D uint2 reduce_sample(uint2 v, uint32_t ij, uint32_t f, uint32_t t, const VisParams &P)
 {
     const uint32_t i = ij & 0xffffu, j = ij >> 16;
     const uint32_t row = f * P.n_in;
     const float Ai = __ldg(P.autos + (size_t)(row + i) * P.T + t);
-    if (i == j) {
-        // s^2 = V_ii^2 / N: q = (2 c A_i) A_i; Im V_ii has no noise and stays
-        const float q = __fmul_rn(__fmul_rn(P.c2, Ai), Ai);
-        v.x = reduce_one(v.x, q);
-    } else {
-        // s^2 = V_ii V_jj / (2N): q = (c A_i) A_j for both components
-        const float Aj = __ldg(P.autos + (size_t)(row + j) * P.T + t);
-        const float q = __fmul_rn(__fmul_rn(P.c, Ai), Aj);
-        v.x = reduce_one(v.x, q);
-        v.y = reduce_one(v.y, q);
-    }
+    const bool is_auto = i == j;
+    // autos: s^2 = V_ii^2 / N, q = (2 c A_i) A_i, Im V_ii has no noise and stays;
+    // crosses: s^2 = V_ii V_jj / (2N), q = (c A_i) A_j for both components
+    const float Aj = is_auto ? Ai : __ldg(P.autos + (size_t)(row + j) * P.T + t);
+    const float q = __fmul_rn(__fmul_rn(vis_c(P, f, t, is_auto), Ai), Aj);
+    v.x = reduce_bits(v.x, q, P.is_int);
+    if (!is_auto) v.y = reduce_bits(v.y, q, P.is_int);
     return v;
 }
 
 // Round `ncplx` consecutive complex samples starting at global complex index
 // c0, lane k taking samples c0 + k, c0 + k + 32, ...  src and dst may be the
 // same (in-place) and may be shared or global memory.
-BSG_D void reduce_run(const float2 *src, float2 *dst, uint32_t c0, uint32_t ncplx,
+BSG_D void reduce_run(const uint2 *src, uint2 *dst, uint32_t c0, uint32_t ncplx,
                       const VisParams &P, uint32_t lane)
 {
     uint32_t c = c0 + lane;
@@ -213,7 +209,7 @@ BSG_D void reduce_run(const float2 *src, float2 *dst, uint32_t c0, uint32_t ncpl
 // product per 16-byte access, so the product lookup and the two autos loads
 // serve both, and the auto / cross choice is a select (for an auto A_j = A_i,
 // the constant is 2c and the imaginary part is kept).
-BSG_D void reduce_run2(const float4 *src, float4 *dst, uint32_t c0, uint32_t ncplx,
+BSG_D void reduce_run2(const uint4 *src, uint4 *dst, uint32_t c0, uint32_t ncplx,
                        const VisParams &P, uint32_t lane)
 {
     uint32_t c = c0 + 2 * lane;
@@ -229,15 +225,15 @@ BSG_D void reduce_run2(const float4 *src, float4 *dst, uint32_t c0, uint32_t ncp
         const float2 Ai = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + i) * P.T + t));
         const float2 Aj = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + j) * P.T + t));
         const bool is_auto = i == j;
-        const float cc = is_auto ? P.c2 : P.c;
-        const float qa = __fmul_rn(__fmul_rn(cc, Ai.x), Aj.x);
-        const float qb = __fmul_rn(__fmul_rn(cc, Ai.y), Aj.y);
-        float4 v = src[k];
-        const float xi0 = reduce_one(v.y, qa), xi1 = reduce_one(v.w, qb);
-        v.x = reduce_one(v.x, qa);
-        v.z = reduce_one(v.z, qb);
-        v.y = is_auto ? v.y : xi0;
-        v.w = is_auto ? v.w : xi1;
+        const float qa = __fmul_rn(__fmul_rn(vis_c(P, f, t, is_auto), Ai.x), Aj.x);
+        const float qb = __fmul_rn(__fmul_rn(vis_c(P, f, t + 1, is_auto), Ai.y), Aj.y);
+        uint4 v = src[k];
+        v.x = reduce_bits(v.x, qa, P.is_int);
+        v.z = reduce_bits(v.z, qb, P.is_int);
+        if (!is_auto) {
+            v.y = reduce_bits(v.y, qa, P.is_int);
+            v.w = reduce_bits(v.w, qb, P.is_int);
+        }
         dst[k] = v;
         t += r64;
         p += q64;
@@ -275,7 +271,6 @@ BSG_D void round_shuffle4_vis(const uint8_t *src, uint8_t *dst, uint32_t Bb, uin
         const uint32_t ij = __ldg(P.pairs + p);
         const uint32_t i = ij & 0xffffu, j = ij >> 16;
         const bool is_auto = i == j;
-        const float cc = is_auto ? P.c2 : P.c;
         const float *ai = P.autos + (size_t)(f * P.n_in + i) * P.T + t0;
         const float *aj = P.autos + (size_t)(f * P.n_in + j) * P.T + t0;
         uint32_t a[32];
@@ -293,17 +288,14 @@ BSG_D void round_shuffle4_vis(const uint8_t *src, uint8_t *dst, uint32_t Bb, uin
         }
 #pragma unroll
         for (int k = 0; k < 8; k++) {
-            const float q0 = __fmul_rn(__fmul_rn(cc, Ai[k].x), Aj[k].x);
-            const float q1 = __fmul_rn(__fmul_rn(cc, Ai[k].y), Aj[k].y);
-            const float re0 = reduce_one(__uint_as_float(a[4 * k]), q0);
-            const float im0 = reduce_one(__uint_as_float(a[4 * k + 1]), q0);
-            const float re1 = reduce_one(__uint_as_float(a[4 * k + 2]), q1);
-            const float im1 = reduce_one(__uint_as_float(a[4 * k + 3]), q1);
-            a[4 * k] = __float_as_uint(re0);
-            a[4 * k + 2] = __float_as_uint(re1);
+            const uint32_t t = t0 + 2 * ((k + rot) & 7u);
+            const float q0 = __fmul_rn(__fmul_rn(vis_c(P, f, t, is_auto), Ai[k].x), Aj[k].x);
+            const float q1 = __fmul_rn(__fmul_rn(vis_c(P, f, t + 1, is_auto), Ai[k].y), Aj[k].y);
+            a[4 * k] = reduce_bits(a[4 * k], q0, P.is_int);
+            a[4 * k + 2] = reduce_bits(a[4 * k + 2], q1, P.is_int);
             if (!is_auto) {
-                a[4 * k + 1] = __float_as_uint(im0);
-                a[4 * k + 3] = __float_as_uint(im1);
+                a[4 * k + 1] = reduce_bits(a[4 * k + 1], q0, P.is_int);
+                a[4 * k + 3] = reduce_bits(a[4 * k + 3], q1, P.is_int);
             }
         }
         // a[m] holds float (m + 4 rot) mod 32 of the group
@@ -313,18 +305,17 @@ BSG_D void round_shuffle4_vis(const uint8_t *src, uint8_t *dst, uint32_t Bb, uin
     }
 }
 
-// Round the float at global float index fi (used for the verbatim tail).
-BSG_D float reduce_float_at(float x, uint64_t fi, const VisParams &P)
+// Round the component (32 bits) at global component index fi (used for the
+// verbatim tail).
+BSG_D uint32_t reduce_component_at(uint32_t xb, uint64_t fi, const VisParams &P)
 {
     uint32_t c = (uint32_t)(fi >> 1);
     uint32_t fp = c / P.T, t = c - fp * P.T;
     uint32_t f = fp / P.P, p = fp - f * P.P;
-    float2 v = (fi & 1) ? make_float2(0.f, x) : make_float2(x, 0.f);
-    uint32_t ij = __ldg(P.pairs + p);
-    uint32_t i = ij & 0xffffu, j = ij >> 16;
+    uint2 v = (fi & 1) ? make_uint2(0u, xb) : make_uint2(xb, 0u);
+    const uint32_t ij = __ldg(P.pairs + p);
     // the imaginary part of an auto is never rounded; everything else as usual
-    float2 r = reduce_sample(v, ij, f, t, P);
-    if ((fi & 1) && i == j) return x;
+    const uint2 r = reduce_sample(v, ij, f, t, P);
     return (fi & 1) ? r.y : r.x;
 }
 
@@ -332,7 +323,7 @@ BSG_D float reduce_float_at(float x, uint64_t fi, const VisParams &P)
 // pairs[p] = i | j << 16 for the upper-triangle product order.
 __global__ void vis_tables_kernel(const float *__restrict__ vis, float *__restrict__ autos,
                                   uint32_t *__restrict__ pairs, uint32_t n_freq, uint32_t n_in,
-                                  uint32_t T)
+                                  uint32_t T, int is_int)
 {
     const uint32_t P = n_in * (n_in + 1) / 2;
     const uint64_t n_auto = (uint64_t)n_freq * n_in * T;
@@ -343,7 +334,9 @@ __global__ void vis_tables_kernel(const float *__restrict__ vis, float *__restri
         uint32_t i = (uint32_t)(fi % n_in);
         uint64_t f = fi / n_in;
         uint64_t pii = (uint64_t)i * n_in - (uint64_t)i * (i - 1) / 2;
-        autos[x] = vis[((f * P + pii) * T + t) * 2];
+        const size_t at = ((f * P + pii) * T + t) * 2;
+        // int32 autos are converted to float32 (round to nearest)
+        autos[x] = is_int ? __int2float_rn(reinterpret_cast<const int32_t *>(vis)[at]) : vis[at];
     }
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
         // row i holds products [i n - i (i-1)/2, (i+1) n - (i+1) i / 2)
@@ -359,9 +352,58 @@ __global__ void vis_tables_kernel(const float *__restrict__ vis, float *__restri
     }
 }
 
+// Sec. 3.2's compensation: per (freq, time) sample, c is recomputed from
+// f m with m = min over cross products of 1 - |V_ij|^2 / (V_ii V_jj) in
+// float32 (each operation rounded to nearest; a negative or NaN value counts
+// as 0; no cross product gives 1), c = fl32(6 (f m) / N) in fp64.  One CTA per
+// (frequency, chunk of up to 1024 time samples); the minimum of non-negative
+// floats is taken on their bit patterns.
+__global__ void __launch_bounds__(256) vis_compensation_kernel(const void *__restrict__ vis,
+                                                               VisParams P, float *cft,
+                                                               uint32_t n_freq, double f,
+                                                               double N)
+{
+    __shared__ uint32_t mins[1024];
+    const uint32_t nchunk = (P.T + 1023) / 1024;
+    for (uint32_t cb = blockIdx.x; cb < n_freq * nchunk; cb += gridDim.x) {
+        const uint32_t fr = cb / nchunk, t0 = (cb % nchunk) * 1024;
+        const uint32_t tn = P.T - t0 < 1024 ? P.T - t0 : 1024;
+        for (uint32_t t = threadIdx.x; t < tn; t += blockDim.x) mins[t] = __float_as_uint(1.0f);
+        __syncthreads();
+        for (uint64_t e = threadIdx.x; e < (uint64_t)P.P * tn; e += blockDim.x) {
+            const uint32_t p = (uint32_t)(e / tn), t = t0 + (uint32_t)(e % tn);
+            const uint32_t ij = __ldg(P.pairs + p);
+            const uint32_t i = ij & 0xffffu, j = ij >> 16;
+            if (i == j) continue;
+            const float Ai = __ldg(P.autos + ((size_t)fr * P.n_in + i) * P.T + t);
+            const float Aj = __ldg(P.autos + ((size_t)fr * P.n_in + j) * P.T + t);
+            const size_t at = (((size_t)fr * P.P + p) * P.T + t) * 2;
+            float re, im;
+            if (P.is_int) {
+                re = __int2float_rn(reinterpret_cast<const int32_t *>(vis)[at]);
+                im = __int2float_rn(reinterpret_cast<const int32_t *>(vis)[at + 1]);
+            } else {
+                re = reinterpret_cast<const float *>(vis)[at];
+                im = reinterpret_cast<const float *>(vis)[at + 1];
+            }
+            const float num = __fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im));
+            const float den = __fmul_rn(Ai, Aj);
+            float om = __fsub_rn(1.0f, __fdiv_rn(num, den));
+            if (!(om >= 0.0f)) om = 0.0f;
+            atomicMin(&mins[t - t0], __float_as_uint(om));
+        }
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < tn; t += blockDim.x) {
+            const double fe = __dmul_rn(f, (double)__uint_as_float(mins[t]));
+            cft[(size_t)fr * P.T + t0 + t] = __double2float_rn(__ddiv_rn(__dmul_rn(6.0, fe), N));
+        }
+        __syncthreads();
+    }
+}
+
 // Standalone precision reduction: each warp rounds runs of 1024 samples.
-__global__ void __launch_bounds__(256) reduce_precision_kernel(const float2 *__restrict__ in,
-                                                               float2 *__restrict__ out,
+__global__ void __launch_bounds__(256) reduce_precision_kernel(const uint2 *__restrict__ in,
+                                                               uint2 *__restrict__ out,
                                                                uint64_t n_cplx, VisParams P)
 {
     const uint32_t lane = threadIdx.x & 31u;
@@ -371,7 +413,7 @@ __global__ void __launch_bounds__(256) reduce_precision_kernel(const float2 *__r
     for (uint64_t r = warp * RUN; r < n_cplx; r += nwarps * RUN) {
         uint32_t cnt = (uint32_t)(n_cplx - r < RUN ? n_cplx - r : RUN);
         if ((P.T & 1u) == 0)  // r is even and so is cnt (n_cplx = F P T is even)
-            reduce_run2(reinterpret_cast<const float4 *>(in + r), reinterpret_cast<float4 *>(out + r),
+            reduce_run2(reinterpret_cast<const uint4 *>(in + r), reinterpret_cast<uint4 *>(out + r),
                         (uint32_t)r, cnt, P, lane);
         else
             reduce_run(in + r, out + r, (uint32_t)r, cnt, P, lane);
@@ -447,19 +489,20 @@ BSG_D void compress_prepare(const CodecArgs &a, uint32_t tile, uint8_t *in, uint
                             uint32_t lane)
 {
     const uint32_t Bb = block_elems_of(a, tile);
-    // float index tile * B is even: whole complex samples
-    const uint32_t c0 = (uint32_t)(((uint64_t)tile * a.B) >> 1);
-    if (a.vis.enabled && Bb % 32u == 0 && a.vis.T % 16u == 0) {
+    // the block starts at a whole complex sample (B is a multiple of 8)
+    const uint32_t c0 = (uint32_t)(((uint64_t)tile * a.B * a.es) >> 3);
+    const uint32_t ncplx = Bb * a.es / 8;
+    if (a.vis.enabled && a.es == 4 && Bb % 32u == 0 && a.vis.T % 16u == 0) {
         round_shuffle4_vis(in, tmp, Bb, c0, a.vis, lane);
         return;
     }
     if (a.vis.enabled) {
-        if ((a.vis.T & 1u) == 0) {  // c0 and Bb / 2 are even (Bb is a multiple of 8)
-            float4 *b4 = reinterpret_cast<float4 *>(in);
-            reduce_run2(b4, b4, c0, Bb / 2, a.vis, lane);
+        if ((a.vis.T & 1u) == 0) {  // c0 and ncplx are even
+            uint4 *b4 = reinterpret_cast<uint4 *>(in);
+            reduce_run2(b4, b4, c0, ncplx, a.vis, lane);
         } else {
-            float2 *b2 = reinterpret_cast<float2 *>(in);
-            reduce_run(b2, b2, c0, Bb / 2, a.vis, lane);
+            uint2 *b2 = reinterpret_cast<uint2 *>(in);
+            reduce_run(b2, b2, c0, ncplx, a.vis, lane);
         }
         __syncwarp();
     }
@@ -489,10 +532,12 @@ BSG_D void compress_place(const CodecArgs &a, uint32_t tile, const uint8_t *blk,
             return;
         }
         if (a.vis.enabled) {
-            if (lane < a.tail_elems) {
-                const float *src = reinterpret_cast<const float *>(a.in);
-                float x = reduce_float_at(src[first + lane], first + lane, a.vis);
-                uint32_t u = __float_as_uint(x);
+            // the tail as 32-bit components, each rounded like any other
+            const uint32_t tc = tb / 4;
+            const uint64_t c0 = first * a.es / 4;
+            if (lane < tc) {
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(a.in);
+                const uint32_t u = reduce_component_at(src[c0 + lane], c0 + lane, a.vis);
                 for (int k = 0; k < 4; k++) a.out[end + 4 * lane + k] = (uint8_t)(u >> (8 * k));
             }
         } else {
@@ -599,7 +644,7 @@ uint32_t compress_fast_smem_bytes(int level)
     return level >= 1 ? FastPlan<1>::BYTES : FastPlan<0>::BYTES;
 }
 
-template <int LEVEL, int ES>
+template <int LEVEL, int ES, bool GEN = false>
 __global__ void compress_fast_kernel(const __grid_constant__ CodecArgs a);
 
 uint32_t compress_fast_blocks_per_sm(int level, uint32_t es)
@@ -620,9 +665,47 @@ uint32_t compress_fast_blocks_per_sm(int level, uint32_t es)
 
 static_assert(FAST_SLOT_BYTES >= r16(4 + lz4b(8192) + 32), "staging slot too small");
 
-// Precision reduction of one group of 32 float32 values (16 consecutive time
+// Round the 32 components of one group (16 samples t0 .. t0 + 15 of one
+// product) held as a[m] = component (m + 4 rot) mod 32.  GEN: int32 data or a
+// per-sample compensated c; otherwise float32 with the constant c, which is
+// kept as its own instantiation so that the common case carries no per-value
+// selects.
+template <bool GEN>
+BSG_D void round_group(const VisParams &P, uint32_t (&a)[32], uint32_t rot, uint32_t f,
+                       uint32_t t0, const float *ai, const float *aj, bool is_auto)
+{
+    const float cc = is_auto ? P.c2 : P.c;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const uint32_t c = (k + rot) & 7u;  // chunk c: samples t0 + 2c, t0 + 2c + 1
+        const float2 Ai = __ldg(reinterpret_cast<const float2 *>(ai + 2 * c));
+        const float2 Aj = __ldg(reinterpret_cast<const float2 *>(aj + 2 * c));
+        if (GEN) {
+            const float q0 = __fmul_rn(__fmul_rn(vis_c(P, f, t0 + 2 * c, is_auto), Ai.x), Aj.x);
+            const float q1 = __fmul_rn(__fmul_rn(vis_c(P, f, t0 + 2 * c + 1, is_auto), Ai.y), Aj.y);
+            a[4 * k] = reduce_bits(a[4 * k], q0, P.is_int);
+            a[4 * k + 2] = reduce_bits(a[4 * k + 2], q1, P.is_int);
+            if (!is_auto) {
+                a[4 * k + 1] = reduce_bits(a[4 * k + 1], q0, P.is_int);
+                a[4 * k + 3] = reduce_bits(a[4 * k + 3], q1, P.is_int);
+            }
+        } else {
+            const float q0 = __fmul_rn(__fmul_rn(cc, Ai.x), Aj.x);
+            const float q1 = __fmul_rn(__fmul_rn(cc, Ai.y), Aj.y);
+            a[4 * k] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k]), q0));
+            a[4 * k + 2] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 2]), q1));
+            if (!is_auto) {
+                a[4 * k + 1] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 1]), q0));
+                a[4 * k + 3] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 3]), q1));
+            }
+        }
+    }
+}
+
+// Precision reduction of one group of 32 components (16 consecutive time
 // samples of one product, the time axis being a multiple of 16) held in
-// registers in lane-rotated chunk order: a[m] is float (m + 4 (g & 7)) mod 32.
+// registers in lane-rotated chunk order: a[m] is component (m + 4 (g & 7)) mod 32.
+template <bool GEN>
 struct VisGroupRound {
     const VisParams *P;
     uint32_t c_blk;  // complex index of the block's first sample
@@ -637,23 +720,9 @@ struct VisGroupRound {
         const uint32_t ij = __ldg(P->pairs + p);
         const uint32_t i = ij & 0xffffu, j = ij >> 16;
         const bool is_auto = i == j;
-        const float cc = is_auto ? P->c2 : P->c;
         const float *ai = P->autos + (size_t)(f * P->n_in + i) * P->T + t0;
         const float *aj = P->autos + (size_t)(f * P->n_in + j) * P->T + t0;
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            const uint32_t c = (k + rot) & 7u;  // chunk c: samples t0 + 2c, t0 + 2c + 1
-            const float2 Ai = __ldg(reinterpret_cast<const float2 *>(ai + 2 * c));
-            const float2 Aj = __ldg(reinterpret_cast<const float2 *>(aj + 2 * c));
-            const float q0 = __fmul_rn(__fmul_rn(cc, Ai.x), Aj.x);
-            const float q1 = __fmul_rn(__fmul_rn(cc, Ai.y), Aj.y);
-            a[4 * k] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k]), q0));
-            a[4 * k + 2] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 2]), q1));
-            if (!is_auto) {
-                a[4 * k + 1] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 1]), q0));
-                a[4 * k + 3] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 3]), q1));
-            }
-        }
+        round_group<GEN>(*P, a, rot, f, t0, ai, aj, is_auto);
     }
 };
 
@@ -665,8 +734,9 @@ struct NoRound {
 // round + bit-transpose it in place through registers, LZ4-encode it into
 // this warp's staging slot in global memory (it stays in L2), publish its
 // size, and place the PREVIOUS block: by then its predecessors have long
-// published theirs, so the look-back rarely waits.
-template <int LEVEL, int ES>
+// published theirs, so the look-back rarely waits.  GEN (4-byte elements of a
+// cube only): int32 components or a compensated c (see round_group).
+template <int LEVEL, int ES, bool GEN>
 __global__ void __launch_bounds__(32, 16) compress_fast_kernel(const __grid_constant__ CodecArgs a)
 {
     using L = FastPlan<LEVEL>;
@@ -692,10 +762,22 @@ __global__ void __launch_bounds__(32, 16) compress_fast_kernel(const __grid_cons
             parity ^= 1u;
         }
         if (ES == 8) {
+            if (a.vis.enabled) {
+                // one complex sample per element: round them in place first
+                const uint32_t c0 = (uint32_t)((uint64_t)tile * a.B);
+                if ((a.vis.T & 1u) == 0) {
+                    uint4 *b4 = reinterpret_cast<uint4 *>(tmp);
+                    reduce_run2(b4, b4, c0, Bb, a.vis, lane);
+                } else {
+                    uint2 *b2 = reinterpret_cast<uint2 *>(tmp);
+                    reduce_run(b2, b2, c0, Bb, a.vis, lane);
+                }
+                __syncwarp();
+            }
             shuffle8_inplace(tmp, Bb, lane);
         } else if (a.vis.enabled) {
             shuffle4_inplace(tmp, Bb, lane,
-                             VisGroupRound{&a.vis, (uint32_t)(((uint64_t)tile * a.B) >> 1)});
+                             VisGroupRound<GEN>{&a.vis, (uint32_t)(((uint64_t)tile * a.B) >> 1)});
         } else {
             shuffle4_inplace(tmp, Bb, lane, NoRound{});
         }
@@ -738,9 +820,9 @@ __global__ void compress_small_kernel(const __grid_constant__ CodecArgs a)
     write_chunk_header(a.out, a.n_elem * a.es, a.B * a.es, lane);
     const uint32_t tb = a.tail_elems * a.es;
     if (a.vis.enabled) {
-        if (lane < a.tail_elems) {
-            const float *src = reinterpret_cast<const float *>(a.in);
-            uint32_t u = __float_as_uint(reduce_float_at(src[lane], lane, a.vis));
+        if (lane < tb / 4) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(a.in);
+            const uint32_t u = reduce_component_at(src[lane], lane, a.vis);
             for (int k = 0; k < 4; k++) a.out[12 + 4 * lane + k] = (uint8_t)(u >> (8 * k));
         }
     } else {
@@ -1041,8 +1123,18 @@ static cudaError_t launch_warp_kernel(K kernel, uint32_t smem, uint32_t grid, cu
     return cudaGetLastError();
 }
 
+cudaError_t launch_vis_compensation(const void *vis, const VisParams &P, uint32_t n_freq,
+                                    double f, double N, cudaStream_t s)
+{
+    const uint64_t work = (uint64_t)n_freq * ((P.T + 1023) / 1024);
+    const uint32_t grid = (uint32_t)(work < 8192 ? work : 8192);
+    vis_compensation_kernel<<<grid ? grid : 1, 256, 0, s>>>(vis, P, const_cast<float *>(P.cft),
+                                                            n_freq, f, N);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_vis_tables(const float *vis, float *autos, uint32_t *pairs, uint32_t n_freq,
-                              uint32_t n_in, uint32_t T, cudaStream_t s)
+                              uint32_t n_in, uint32_t T, int is_int, cudaStream_t s)
 {
     uint64_t n = (uint64_t)n_freq * n_in * T;
     uint64_t P = (uint64_t)n_in * (n_in + 1) / 2;
@@ -1050,15 +1142,15 @@ cudaError_t launch_vis_tables(const float *vis, float *autos, uint32_t *pairs, u
     uint32_t blocks = (uint32_t)((work + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (blocks == 0) blocks = 1;
-    vis_tables_kernel<<<blocks, 256, 0, s>>>(vis, autos, pairs, n_freq, n_in, T);
+    vis_tables_kernel<<<blocks, 256, 0, s>>>(vis, autos, pairs, n_freq, n_in, T, is_int);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_precision(const float *in, float *out, uint64_t n_cplx,
                                     const VisParams &v, uint32_t grid, cudaStream_t s)
 {
-    reduce_precision_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float2 *>(in),
-                                                 reinterpret_cast<float2 *>(out), n_cplx, v);
+    reduce_precision_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const uint2 *>(in),
+                                                 reinterpret_cast<uint2 *>(out), n_cplx, v);
     return cudaGetLastError();
 }
 
@@ -1095,6 +1187,9 @@ cudaError_t launch_compress_fast(const CodecArgs &a, uint32_t grid, cudaStream_t
     if (a.es == 8)
         return a.level >= 1 ? launch_warp_kernel(compress_fast_kernel<1, 8>, smem, grid, s, a)
                             : launch_warp_kernel(compress_fast_kernel<0, 8>, smem, grid, s, a);
+    if (a.vis.enabled && (a.vis.is_int || a.vis.cft))
+        return a.level >= 1 ? launch_warp_kernel(compress_fast_kernel<1, 4, true>, smem, grid, s, a)
+                            : launch_warp_kernel(compress_fast_kernel<0, 4, true>, smem, grid, s, a);
     return a.level >= 1 ? launch_warp_kernel(compress_fast_kernel<1, 4>, smem, grid, s, a)
                         : launch_warp_kernel(compress_fast_kernel<0, 4>, smem, grid, s, a);
 }

@@ -14,8 +14,17 @@ struct VisParams {
     uint32_t n_in, T, P;    // inputs, time samples, products
     uint32_t qT, rT;        // 32 / T and 32 % T (advance of a lane by 32 samples)
     float c, c2;            // fl32(6 f / N) and 2 c
+    const float *cft;       // per (freq, time) compensated c (Sec. 3.2), or null
+    int is_int;             // components are int32 (else float32)
     int enabled;
 };
+
+// c (2c for the real part of an auto) of the sample at (f, t)
+__device__ __forceinline__ float vis_c(const VisParams &P, uint32_t f, uint32_t t, bool is_auto)
+{
+    const float c = P.cft ? P.cft[(size_t)f * P.T + t] : P.c;
+    return is_auto ? 2.0f * c : c;
+}
 
 // One framed stream (compress / decompress / bitshuffle).
 struct CodecArgs {
@@ -45,7 +54,10 @@ uint32_t shuffle_smem_bytes(uint32_t maxb);
 
 // Launchers (return cudaGetLastError()).  `grid` warps of 32 threads.
 cudaError_t launch_vis_tables(const float *vis, float *autos, uint32_t *pairs, uint32_t n_freq,
-                              uint32_t n_in, uint32_t T, cudaStream_t s);
+                              uint32_t n_in, uint32_t T, int is_int, cudaStream_t s);
+// per (freq, time) compensated c of Sec. 3.2 into P.cft (needs the tables)
+cudaError_t launch_vis_compensation(const void *vis, const VisParams &P, uint32_t n_freq,
+                                    double f, double N, cudaStream_t s);
 cudaError_t launch_reduce_precision(const float *in, float *out, uint64_t n_cplx,
                                     const VisParams &v, uint32_t grid, cudaStream_t s);
 cudaError_t launch_shuffle(const CodecArgs &a, bool inverse, uint32_t maxb, uint32_t grid,

@@ -112,6 +112,17 @@ def visibilities(cfg: VisConfig, freq_lo: int = 0, freq_hi: int | None = None) -
     return out
 
 
+def visibilities_int(cfg: VisConfig, scale: float, freq_lo: int = 0,
+                     freq_hi: int | None = None) -> np.ndarray:
+    """The cube of ``cfg`` as a correlator's integers: an int32 array of shape
+    [freq][prod][time][2] holding (re, im) of ``visibilities(cfg) * scale``
+    rounded to the nearest integer and clipped to the int32 range."""
+    v = visibilities(cfg, freq_lo, freq_hi)
+    a = np.stack([v.real, v.imag], axis=-1).astype(np.float64) * scale
+    lim = np.iinfo(np.int32)
+    return np.clip(np.rint(a), lim.min, lim.max).astype(np.int32)
+
+
 def random_walk(n: int, dtype, seed: int = 0) -> np.ndarray:
     """x_{t+1} = x_t +- 2^k with k ~ U{0..6} and a fair sign; integers wrap."""
     dtype = np.dtype(dtype)

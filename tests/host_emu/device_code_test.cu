@@ -13,6 +13,7 @@ extern "C" {
 size_t orc_lz4_compress_block(const uint8_t *src, size_t n, uint8_t *dst, size_t cap);
 int orc_lz4_decompress_block(const uint8_t *src, size_t src_len, uint8_t *dst, size_t dst_len);
 int orc_bitshuffle(const void *vin, void *vout, size_t n, size_t es, size_t block_elems, int inverse);
+int32_t orc_round_int(int32_t x, int k);
 }
 using namespace bsg;
 alignas(16) static uint8_t A[70000], Bf[70000], C[70000], T[65536];
@@ -48,6 +49,31 @@ static int test_granularity_bits(std::mt19937 &rng)
         float Tm;
         memcpy(&Tm, &Tb, 4);
         if ((double)Tm != ldexp(1.0, k + 23)) bad++;
+        if (granularity_k(Q) != k) bad++;
+    }
+    return bad;
+}
+
+// integer rounding against the oracle's, over random and extreme values
+static int test_round_int(std::mt19937 &rng)
+{
+    int bad = 0;
+    const int32_t edge[] = {0, 1, -1, 2, -2, 3, -3, INT32_MAX, INT32_MIN, INT32_MAX - 1,
+                            INT32_MIN + 1, 1 << 30, -(1 << 30), 12345, -12345};
+    for (int k = -3; k <= 66; k++) {
+        for (int32_t x : edge) bad += round_int_pow2(x, k) != orc_round_int(x, k);
+        for (int it = 0; it < 4000; it++) {
+            int32_t x = (int32_t)rng();
+            if (it & 1) x >>= (rng() % 31);  // small magnitudes too
+            bad += round_int_pow2(x, k) != orc_round_int(x, k);
+            // ties: x = (2m + 1) 2^(k-1)
+            if (k >= 1 && k <= 30) {
+                int64_t m = (int32_t)rng() >> (k + 1);
+                int64_t y = (2 * m + 1) * ((int64_t)1 << (k - 1));
+                if (y >= INT32_MIN && y <= INT32_MAX)
+                    bad += round_int_pow2((int32_t)y, k) != orc_round_int((int32_t)y, k);
+            }
+        }
     }
     return bad;
 }
@@ -219,6 +245,7 @@ int main()
 {
     std::mt19937 rng(7);
     int t = test_transpose(rng), g = test_granularity_bits(rng), s = test_shuffles(rng);
+    g += test_round_int(rng);
     s += test_inplace_unshuffle(rng);
     double gr0 = 0, gr1 = 0, orr = 0;
     int l0 = test_lz4(rng, 0, gr0, orr);

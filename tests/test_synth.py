@@ -44,3 +44,14 @@ def test_random_walk_steps():
             d = (d + 2 ** (8 * w.itemsize - 1)) % 2 ** (8 * w.itemsize) - 2 ** (8 * w.itemsize - 1)
         a = np.abs(d)
         assert set(np.unique(a).astype(int).tolist()) <= {1, 2, 4, 8, 16, 32, 64}
+
+
+def test_visibilities_int_is_the_scaled_cube():
+    cfg = synth.VisConfig(2, 3, 4, 2 ** 10, 0.1, seed=5)
+    v = synth.visibilities(cfg)
+    a = synth.visibilities_int(cfg, 1000.0)
+    assert a.dtype == np.int32 and a.shape == v.shape + (2,)
+    assert np.array_equal(a[..., 0], np.rint(v.real.astype(np.float64) * 1000.0))
+    assert np.array_equal(a[..., 1], np.rint(v.imag.astype(np.float64) * 1000.0))
+    big = synth.visibilities_int(cfg, 1e9)  # autos ~100 * 1e9: clipped to int32
+    assert big.max() == np.iinfo(np.int32).max
