@@ -236,6 +236,80 @@ int bsgpu_compress_noalloc(const void *in, size_t n_elem, size_t elem_size, size
                            int level, void *out, size_t out_cap, uint64_t *d_out_bytes,
                            uint64_t *d_block_offsets, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched codec (Sec. 4.2.1: blocks are independent units of work).  Many
+ * independent chunks -- each its own framed stream, with its own element
+ * size (1, 2, 4 or 8) and block size (at most 8192 bytes) -- compressed or
+ * decompressed by ONE persistent launch whose work queue runs over every
+ * (chunk, block) item, so uneven chunk sizes do not leave SMs idle.  Each
+ * chunk's stream is byte-identical to what bsgpu_compress() writes for that
+ * chunk alone with the same level.
+ * ------------------------------------------------------------------------ */
+
+/* One chunk of a batch (host memory; pointers are device pointers, 16-byte
+ * aligned).
+ *   compress  : in = n_elem * elem_size bytes; out = stream buffer of
+ *               out_cap >= bsgpu_compress_bound() bytes; in_bytes ignored.
+ *   decompress: in = the chunk's stream of in_bytes bytes (or see
+ *               d_in_bytes); out = n_elem * elem_size bytes; out_cap ignored.
+ *   block_elems: a multiple of 8 with block_elems * elem_size <= 8192, or 0
+ *               for the 4096-byte default. */
+typedef struct bsgpu_chunk {
+    const void *in;
+    void *out;
+    uint64_t n_elem;
+    uint64_t in_bytes;
+    uint64_t out_cap;
+    uint32_t elem_size;
+    uint32_t block_elems;
+} bsgpu_chunk;
+
+/* Bytes of the table image for n_chunks chunks (0 for none). */
+size_t bsgpu_batch_table_bytes(uint32_t n_chunks);
+
+/* Host-only: validate the chunks for op (BSGPU_OP_COMPRESS or
+ * BSGPU_OP_DECOMPRESS) and write the table image (bsgpu_batch_table_bytes
+ * bytes) to host memory `table`; the caller copies it, unchanged, to 16-byte
+ * aligned device memory before the batch call (it holds the chunks' device
+ * pointers, sizes and first item indices).  *n_items receives the number of
+ * items: each chunk's block count, or 1 for a chunk of fewer than 8 elements.
+ * *ws_bytes receives the device workspace the batch call needs.  Chunk c's
+ * block index entries start at item (sum over earlier chunks of their item
+ * counts).  Errors: BSGPU_ERR_ARG (element size, block size, null pointer),
+ * BSGPU_ERR_ALIGN, BSGPU_ERR_SPACE (table or a chunk's out_cap too small). */
+int bsgpu_batch_plan(int op, const bsgpu_chunk *chunks, uint32_t n_chunks, void *table,
+                     size_t table_bytes, uint64_t *n_items, size_t *ws_bytes);
+
+/* Compress every chunk of a planned batch.
+ *   d_table         : the device copy of the table image
+ *   level           : as for bsgpu_compress
+ *   d_out_bytes     : n_chunks device uint64s, each chunk's stream length
+ *   d_block_offsets : NULL or n_items device uint64s (per-chunk block index,
+ *                     offsets relative to the chunk's stream)
+ *   d_chunk_status  : n_chunks device ints, zeroed by the call, then
+ *                     BSGPU_ERR_SPACE / BSGPU_ERR_TIMEOUT for a chunk that
+ *                     failed on the device
+ *   ctas_per_sm     : resident one-warp CTAs per SM (0 = as many as fit;
+ *                     the tuning knob of the batch engine)
+ * Asynchronous on `stream`; nothing allocated. */
+int bsgpu_compress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_items, int level,
+                         uint64_t *d_out_bytes, uint64_t *d_block_offsets, int *d_chunk_status,
+                         void *ws, size_t ws_bytes, uint32_t ctas_per_sm, void *stream);
+
+/* Decompress every chunk of a planned batch (planned with
+ * BSGPU_OP_DECOMPRESS).  d_in_bytes: NULL (use each chunk's in_bytes) or
+ * n_chunks device uint64s of stream lengths (e.g. a compress batch's
+ * d_out_bytes, so both can run back to back without the host).
+ * d_block_offsets: the index from bsgpu_compress_batch, or NULL (each
+ * chunk's block chain is then walked on the device by one thread per chunk
+ * first: slow for long chunks).  A corrupt chunk sets BSGPU_ERR_CORRUPT in
+ * its d_chunk_status entry; its output is then unspecified, the other
+ * chunks are unaffected and nothing outside the given buffers is touched. */
+int bsgpu_decompress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_items,
+                           const uint64_t *d_in_bytes, const uint64_t *d_block_offsets,
+                           int *d_chunk_status, void *ws, size_t ws_bytes, uint32_t ctas_per_sm,
+                           void *stream);
+
 #ifdef __cplusplus
 }
 #endif

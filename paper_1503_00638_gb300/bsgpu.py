@@ -48,7 +48,22 @@ _SIGS = {
     "bsgpu_compress_vis_ex": ([_vp, _i, _i64, _i64, _i64, _d, _d, _i, _sz, _sz, _i, _vp, _sz,
                                _vp, _vp, _vp, _sz, _vp], _i),
     "bsgpu_compress_noalloc": ([_vp, _sz, _sz, _sz, _i, _vp, _sz, _vp, _vp, _vp], _i),
+    "bsgpu_batch_table_bytes": ([ctypes.c_uint32], _sz),
+    "bsgpu_batch_plan": ([_i, _vp, ctypes.c_uint32, _vp, _sz, ctypes.POINTER(ctypes.c_uint64),
+                          ctypes.POINTER(_sz)], _i),
+    "bsgpu_compress_batch": ([_vp, ctypes.c_uint32, ctypes.c_uint64, _i, _vp, _vp, _vp, _vp, _sz,
+                              ctypes.c_uint32, _vp], _i),
+    "bsgpu_decompress_batch": ([_vp, ctypes.c_uint32, ctypes.c_uint64, _vp, _vp, _vp, _vp, _sz,
+                                ctypes.c_uint32, _vp], _i),
 }
+
+
+class Chunk(ctypes.Structure):
+    """bsgpu_chunk: one chunk of a batch (device pointers, sizes)."""
+    _fields_ = [("in_ptr", ctypes.c_void_p), ("out_ptr", ctypes.c_void_p),
+                ("n_elem", ctypes.c_uint64), ("in_bytes", ctypes.c_uint64),
+                ("out_cap", ctypes.c_uint64), ("elem_size", ctypes.c_uint32),
+                ("block_elems", ctypes.c_uint32)]
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
@@ -320,3 +335,39 @@ def compress_noalloc(x: torch.Tensor, block_elems: int = 0, elem_size: int | Non
                                        _ptr(nbytes_dev), _ptr(offsets), _stream(stream)),
            "bsgpu_compress_noalloc")
     return out, nbytes_dev, offsets
+
+
+# -- batched codec (one persistent launch over many chunks) -------------------
+
+def batch_table_bytes(n_chunks: int) -> int:
+    return _lib.bsgpu_batch_table_bytes(n_chunks)
+
+
+def batch_plan(op: int, chunks) -> tuple:
+    """Validate a list of :class:`Chunk` for op and return (table image as a
+    uint8 CPU tensor, n_items, workspace bytes).  Host only."""
+    n = len(chunks)
+    arr = (Chunk * n)(*chunks)
+    table = torch.zeros(max(batch_table_bytes(n), 16), dtype=torch.uint8)
+    n_items, ws = ctypes.c_uint64(0), ctypes.c_size_t(0)
+    _check(_lib.bsgpu_batch_plan(op, ctypes.cast(arr, ctypes.c_void_p), n, table.data_ptr(),
+                                 table.numel(), ctypes.byref(n_items), ctypes.byref(ws)),
+           "bsgpu_batch_plan")
+    return table, n_items.value, ws.value
+
+
+def compress_batch(d_table: torch.Tensor, n_chunks: int, n_items: int, out_bytes: torch.Tensor,
+                   offsets: torch.Tensor | None, status: torch.Tensor, ws: torch.Tensor,
+                   level: int = 0, ctas_per_sm: int = 0, stream=None) -> None:
+    _check(_lib.bsgpu_compress_batch(_ptr(d_table), n_chunks, n_items, level, _ptr(out_bytes),
+                                     _ptr(offsets), _ptr(status), _ptr(ws), ws.numel(),
+                                     ctas_per_sm, _stream(stream)), "bsgpu_compress_batch")
+
+
+def decompress_batch(d_table: torch.Tensor, n_chunks: int, n_items: int,
+                     in_bytes: torch.Tensor | None, offsets: torch.Tensor | None,
+                     status: torch.Tensor, ws: torch.Tensor, ctas_per_sm: int = 0,
+                     stream=None) -> None:
+    _check(_lib.bsgpu_decompress_batch(_ptr(d_table), n_chunks, n_items, _ptr(in_bytes),
+                                       _ptr(offsets), _ptr(status), _ptr(ws), ws.numel(),
+                                       ctas_per_sm, _stream(stream)), "bsgpu_decompress_batch")

@@ -1,0 +1,591 @@
+// Batched codec: many independent chunks (uneven sizes, element sizes 1, 2,
+// 4 or 8, their own block sizes) compressed or decompressed by ONE persistent
+// launch.  Sec. 4.2.1 makes blocks independent units of work; here the work
+// queue runs over every (chunk, block) item of the batch, so the GPU stays
+// full however the sizes are spread.
+//
+// Host side: bsgpu_batch_plan() validates the chunks and writes a table image
+// (one record per chunk, then the first item index of every chunk); the
+// caller copies it to device memory, where the kernels read it.  Each chunk's
+// blocks are numbered locally: its look-back state, block index and status
+// start at its own first item, so a chunk's stream is exactly the one
+// bsgpu_compress() writes for it alone.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "../../include/bsgpu.h"
+#include "codec.cuh"
+
+namespace bsg {
+
+// One chunk as the kernels see it (80 bytes, written by the planner).
+struct BatchChunk {
+    const uint8_t *in;
+    uint8_t *out;
+    uint64_t n_elem;
+    uint64_t in_bytes;   // decompress: stream length
+    uint64_t out_cap;    // compress: capacity of out
+    uint64_t item0;      // first item of the chunk
+    uint32_t es, B, nb, last_B;
+    uint32_t tail, pad0, pad1, pad2;
+};
+static_assert(sizeof(BatchChunk) == 80, "table record layout");
+
+struct BatchArgs {
+    const BatchChunk *chunks;
+    const uint64_t *starts;       // n_chunks + 1 first-item indices
+    uint32_t n_chunks;
+    uint32_t n_items;
+    uint64_t *state;              // compress: look-back state, one per item
+    uint32_t *counter;            // work-queue counter
+    uint8_t *slots;               // compress: two staging slots per CTA
+    uint64_t *out_bytes;          // compress: per chunk stream length
+    const uint64_t *in_bytes;     // decompress: per chunk stream length, or null
+    uint64_t *offsets;            // per item block offsets, or null
+    int *status;                  // per chunk status
+    int level;
+};
+
+// Chunk holding item t: the last c with starts[c] <= t (every chunk has at
+// least one item, so the starts are strictly increasing).
+BSG_D uint32_t find_chunk(const uint64_t *starts, uint32_t n, uint32_t t)
+{
+    uint32_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (__ldg(starts + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The single-stream argument block of chunk c (local block numbering).
+BSG_D CodecArgs chunk_args(const BatchArgs &b, uint32_t c)
+{
+    const BatchChunk &ch = b.chunks[c];
+    CodecArgs a{};
+    a.in = ch.in;
+    a.out = ch.out;
+    a.in_bytes = b.in_bytes ? b.in_bytes[c] : ch.in_bytes;
+    a.out_cap = ch.out_cap;
+    a.out_bytes = b.out_bytes ? b.out_bytes + c : nullptr;
+    a.block_offsets = b.offsets ? b.offsets + ch.item0 : nullptr;
+    a.tile_state = b.state ? b.state + ch.item0 : nullptr;
+    a.status = b.status + c;
+    a.n_elem = ch.n_elem;
+    a.es = ch.es;
+    a.B = ch.B;
+    a.nb = ch.nb;
+    a.last_B = ch.last_B;
+    a.tail_elems = ch.tail;
+    a.level = b.level;
+    return a;
+}
+
+// A chunk of fewer than 8 elements: header plus the elements verbatim.
+BSG_D void compress_tiny(const CodecArgs &a, uint32_t lane)
+{
+    const uint32_t tb = a.tail_elems * a.es;
+    if (12 + tb > a.out_cap) {
+        if (lane == 0) set_status(a.status, BSGPU_ERR_SPACE);
+        return;
+    }
+    write_chunk_header(a.out, a.n_elem * a.es, a.B * a.es, lane);
+    for (uint32_t k = lane; k < tb; k += 32) a.out[12 + k] = a.in[k];
+    if (lane == 0) *a.out_bytes = 12 + tb;
+}
+
+// Bit-transpose block `tile` of chunk `ch` into `tmp`: in place through
+// registers after a bulk copy when the shape allows, else straight from
+// global memory by the byte-wise path (a chunk's shortened last block).
+BSG_D void batch_prepare(const BatchChunk &ch, uint32_t tile, uint32_t Bb, uint8_t *tmp,
+                         uint64_t *bar, uint32_t &parity, int *status, uint32_t lane)
+{
+    const uint32_t es = ch.es;
+    const uint8_t *src = ch.in + (uint64_t)tile * ch.B * es;
+    if (!shuffle_inplace_ok(es, Bb)) {
+        // rare (a chunk's shortened last block): the byte-wise path keeps
+        // register pressure down
+        shuffle_generic(src, tmp, Bb, es, lane);
+        __syncwarp();
+        return;
+    }
+    if (load_block(tmp, src, Bb * es, bar, lane)) {
+        if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(status, BSGPU_ERR_TIMEOUT);
+        parity ^= 1u;
+    }
+    if (es == 2)
+        shuffle2_inplace(tmp, Bb, lane);
+    else if (es == 4)
+        shuffle4_inplace(tmp, Bb, lane, NoRound{});
+    else
+        shuffle8_inplace(tmp, Bb, lane);
+    __syncwarp();
+}
+
+// Exclusive prefix of block `tile` of chunk c by look-back, then its
+// placement (index entry, chunk header, verbatim tail, stream length).
+BSG_D void batch_place(const BatchArgs &b, uint32_t c, uint32_t tile, const uint8_t *blk,
+                       uint32_t cs, uint32_t lane)
+{
+    const CodecArgs a = chunk_args(b, c);
+    const uint64_t excl = lookback_resolve(a.tile_state, tile, 4ull + cs, a.status, lane);
+    compress_place(a, tile, blk, cs, 12 + excl, lane);
+}
+
+// One warp per CTA, persistent, one shared buffer (as compress_fast_kernel):
+// per item, transpose the block, LZ4-encode it into this warp's staging slot,
+// publish its size in its chunk's look-back state, then place the PREVIOUS
+// item's block, whose predecessors have long published theirs.  Only the
+// chunk index and local block number live across an item; the chunk's
+// fields are re-read from its (cached) table record where they are used.
+template <int LEVEL>
+__global__ void __launch_bounds__(32, 16) compress_batch_kernel(const __grid_constant__ BatchArgs b)
+{
+    using L = FastPlan<LEVEL>;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *tmp = sm;
+    void *scratch = sm + L::TMP;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::TMP + r16(L::SCR));
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint8_t *slot0 = b.slots + (size_t)(2 * blockIdx.x) * FAST_SLOT_BYTES;
+    uint8_t *slot1 = slot0 + FAST_SLOT_BYTES;
+    uint32_t parity = 0;
+    uint32_t ptile = ~0u, pchunk = 0, pcs = 0;  // the block waiting to be placed, in slot1
+    uint32_t t = grab_tile(b.counter, lane);
+    while (t < b.n_items) {
+        const uint32_t c = find_chunk(b.starts, b.n_chunks, t);
+        const BatchChunk &ch = b.chunks[c];
+        const uint32_t tile = t - (uint32_t)ch.item0;
+        const uint32_t nb = ch.nb;
+        uint32_t cs = 0;
+        if (nb == 0) {
+            compress_tiny(chunk_args(b, c), lane);
+        } else {
+            const uint32_t Bb = tile + 1 == nb ? ch.last_B : ch.B;
+            const uint32_t S = Bb * ch.es;
+            batch_prepare(ch, tile, Bb, tmp, bar, parity, b.status + c, lane);
+            // bit-rows are Bb/8 bytes long: the previous row is one of the candidates
+            if (LEVEL >= 1)
+                cs = lz4_encode_warp<1, L::HBITS>(tmp, S, Bb / 8, slot0 + 4,
+                                                  static_cast<uint16_t *>(scratch));
+            else if (S % 128u == 0)
+                cs = lz4_encode_bitmap_fast(tmp, S, Bb / 8, slot0 + 4);
+            else
+                cs = lz4_encode_bitmap(tmp, S, Bb / 8, slot0 + 4, static_cast<uint32_t *>(scratch));
+            if (cs == 0xffffffffu) {  // progress guard (not reachable for valid sizes)
+                if (lane == 0) set_status(b.status + c, BSGPU_ERR_CUDA);
+                cs = 0;
+            }
+            if (lane == 0) put_be32(slot0, cs);
+            __syncwarp();
+            lookback_publish(b.state + ch.item0, tile, 4ull + cs, lane);
+        }
+        const uint32_t nxt = grab_tile(b.counter, lane);
+        if (ptile != ~0u) batch_place(b, pchunk, ptile, slot1, pcs, lane);
+        __syncwarp();
+        if (nb != 0) {
+            ptile = tile;
+            pchunk = c;
+            pcs = cs;
+            uint8_t *x = slot0;
+            slot0 = slot1;
+            slot1 = x;
+        } else {
+            ptile = ~0u;
+        }
+        t = nxt;
+        // the next load overwrites `tmp`: the async proxy follows the generic reads
+        fence_proxy_async_smem();
+        __syncwarp();
+    }
+    if (ptile != ~0u) batch_place(b, pchunk, ptile, slot1, pcs, lane);
+}
+
+// Header of a chunk's stream (checked with its first item).
+BSG_D void check_header(const CodecArgs &a, uint32_t lane)
+{
+    uint32_t ok = 1;
+    if (lane < 12) {
+        const uint8_t want = lane < 8 ? (uint8_t)((a.n_elem * a.es) >> (8 * (7 - lane)))
+                                      : (uint8_t)(((uint64_t)a.B * a.es) >> (8 * (11 - lane)));
+        ok = a.in_bytes >= 12 && a.in[lane] == want;
+    }
+    if (__ballot_sync(FULL, !ok) && lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);
+}
+
+// The verbatim tail after a chunk's last block, or after the header alone for
+// a chunk without blocks (whose stream is then exactly 12 + tail bytes).
+BSG_D void copy_tail(const CodecArgs &a, uint32_t lane)
+{
+    const uint32_t tb = a.tail_elems * a.es;
+    const uint64_t first = (a.n_elem - a.tail_elems) * a.es;
+    const bool ok = a.nb ? a.in_bytes >= 12 + tb : a.in_bytes == 12 + tb;
+    if (ok)
+        for (uint32_t k = lane; k < tb; k += 32) a.out[first + k] = a.in[a.in_bytes - tb + k];
+    else if (lane == 0)
+        set_status(a.status, BSGPU_ERR_CORRUPT);
+}
+
+// Start fetching item t's stream bytes into `comp` (nothing for a chunk
+// without blocks).
+BSG_D DecLoad batch_issue(const BatchArgs &b, uint32_t c, uint32_t t, uint8_t *comp,
+                          uint64_t *bar, uint32_t lane)
+{
+    const CodecArgs a = chunk_args(b, c);
+    if (a.nb == 0) return DecLoad{};
+    return dec_issue(a, t - (uint32_t)b.chunks[c].item0, comp, bar, lane);
+}
+
+// LZ4-decode block `tile` of chunk c (stream bytes in `comp`) into `dec`;
+// true when it decoded to exactly its size.
+BSG_D bool batch_decode(const BatchArgs &b, uint32_t c, uint32_t tile, const DecLoad &cur,
+                        uint8_t *comp, uint8_t *dec, uint32_t lane)
+{
+    const BatchChunk &ch = b.chunks[c];
+    const uint32_t Bb = tile + 1 == ch.nb ? ch.last_B : ch.B;
+    bool good = cur.ok;
+    if (good) {
+        if (cur.eidx != ~0u) comp[cur.eidx] = cur.ebyte;
+        __syncwarp();
+        good = get_be32(comp + cur.delta) == cur.clen &&
+               lz4_decode_warp(comp, cur.delta + 4, cur.clen, dec, Bb * ch.es) == 0;
+    }
+    if (!good && lane == 0) set_status(b.status + c, BSGPU_ERR_CORRUPT);
+    return good;
+}
+
+// One warp per CTA, persistent (as decompress_kernel<8192, ES>): per item,
+// wait for its stream bytes, LZ4-decode, start the next item's copy (of
+// whichever chunk it belongs to), un-transpose and store.  As in the
+// compressor only chunk indices and block numbers live across an item.
+__global__ void __launch_bounds__(32, 13) decompress_batch_kernel(const __grid_constant__ BatchArgs b)
+{
+    using L = DecPlan<8192>;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *comp = sm;
+    uint8_t *dec = sm + L::COMP;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(dec + L::DEC);
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t parity = 0;
+    uint32_t t = grab_tile(b.counter, lane);
+    uint32_t c = 0;
+    DecLoad ld{};
+    if (t < b.n_items) {
+        c = find_chunk(b.starts, b.n_chunks, t);
+        ld = batch_issue(b, c, t, comp, bar, lane);
+    }
+    while (t < b.n_items) {
+        const uint32_t tile = t - (uint32_t)b.chunks[c].item0;
+        const uint32_t nb = b.chunks[c].nb;
+        const DecLoad cur = ld;
+        if (cur.bulk) {
+            if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(b.status + c, BSGPU_ERR_TIMEOUT);
+            parity ^= 1u;
+        }
+        if (tile == 0) check_header(chunk_args(b, c), lane);
+        const uint32_t nxt = grab_tile(b.counter, lane);
+        const uint32_t nc = nxt < b.n_items ? find_chunk(b.starts, b.n_chunks, nxt) : c;
+        // the previous block's bulk store must have finished reading `dec`
+        if (lane == 0) bulk_wait_read0();
+        __syncwarp();
+        bool good = false, inplace = false;
+        if (nb) {
+            good = batch_decode(b, c, tile, cur, comp, dec, lane);
+            const BatchChunk &ch = b.chunks[c];
+            const uint32_t Bb = tile + 1 == nb ? ch.last_B : ch.B;
+            inplace = unshuffle_inplace_ok(ch.es, Bb);
+            if (good && !inplace) {
+                const uint32_t S = Bb * ch.es;
+                uint8_t *dst = ch.out + (uint64_t)tile * ch.B * ch.es;
+                unshuffle_block(dec, comp, Bb, ch.es, lane);
+                __syncwarp();
+                for (uint32_t k = lane; k < S; k += 32) dst[k] = comp[k];
+            }
+        }
+        __syncwarp();
+        ld = DecLoad{};
+        if (nxt < b.n_items) {
+            // `comp` was last read by the generic proxy
+            fence_proxy_async_smem();
+            __syncwarp();
+            ld = batch_issue(b, nc, nxt, comp, bar, lane);
+        }
+        if (good && inplace) {
+            const BatchChunk &ch = b.chunks[c];
+            const uint32_t es = ch.es;
+            const uint32_t Bb = tile + 1 == nb ? ch.last_B : ch.B;
+            const uint32_t S = Bb * es;
+            uint8_t *dst = ch.out + (uint64_t)tile * ch.B * es;
+            if (es == 2)
+                unshuffle2_inplace(dec, Bb, lane);
+            else if (es == 4)
+                unshuffle4_inplace(dec, Bb, lane);
+            else
+                unshuffle8_inplace(dec, Bb, lane);
+            __syncwarp();
+            if ((S & 15u) == 0 && ((uintptr_t)dst & 15u) == 0) {
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    bulk_s2g(dst, dec, S);
+                    bulk_commit();
+                }
+            } else {
+                for (uint32_t k = lane; k < S; k += 32) dst[k] = dec[k];
+            }
+        }
+        if (nb == 0 || tile + 1 == nb) copy_tail(chunk_args(b, c), lane);
+        __syncwarp();
+        t = nxt;
+        c = nc;
+    }
+    if (lane == 0) bulk_wait0();
+    __syncwarp();
+}
+
+// Block offsets of every chunk by walking its chain of length fields (one
+// thread per chunk; slow for long chunks, used only without an index).
+__global__ void chain_walk_batch_kernel(const __grid_constant__ BatchArgs b)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= b.n_chunks) return;
+    const CodecArgs a = chunk_args(b, c);
+    const uint64_t tail_b = (uint64_t)a.tail_elems * a.es;
+    uint64_t D = 12;
+    for (uint32_t k = 0; k < a.nb; k++) {
+        if (D + 4 > a.in_bytes) {
+            set_status(a.status, BSGPU_ERR_CORRUPT);
+            for (; k < a.nb; k++) a.block_offsets[k] = 0;  // dec_issue rejects D < 12
+            return;
+        }
+        a.block_offsets[k] = D;
+        const uint8_t *p = a.in + D;
+        const uint32_t len = ((uint32_t)p[0] << 24) | ((uint32_t)p[1] << 16) |
+                             ((uint32_t)p[2] << 8) | (uint32_t)p[3];
+        D += 4ull + len;
+    }
+    if (D + tail_b != a.in_bytes) set_status(a.status, BSGPU_ERR_CORRUPT);
+}
+
+}  // namespace bsg
+
+using namespace bsg;
+
+namespace {
+
+constexpr size_t BATCH_HEADER = 256;  // [0] unused status word, [4] work-queue counter
+
+size_t r256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t table_bytes(uint32_t n) { return ((size_t)n * sizeof(BatchChunk) + 8ull * (n + 1) + 15) & ~(size_t)15; }
+
+struct BatchWs {
+    size_t state, slots, offsets, total;
+};
+
+BatchWs batch_ws(int op, uint64_t n_items, uint32_t grid_max)
+{
+    BatchWs w{};
+    size_t o = BATCH_HEADER;
+    if (op == BSGPU_OP_COMPRESS) {
+        w.state = o;
+        o += r256(8 * n_items);
+        w.slots = o;
+        o += (size_t)grid_max * 2 * FAST_SLOT_BYTES;
+    } else {
+        w.offsets = o;  // block offsets when the caller has no index
+        o += r256(8 * n_items);
+    }
+    w.total = o;
+    return w;
+}
+
+int sm_count()
+{
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+template <typename K>
+uint32_t occupancy(K kernel, uint32_t smem)
+{
+    int n = 0;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 32, smem) != cudaSuccess || n < 1)
+        n = 1;
+    return (uint32_t)n;
+}
+
+template <typename K>
+cudaError_t launch_batch(K kernel, uint32_t smem, uint32_t grid, cudaStream_t s, const BatchArgs &b)
+{
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kernel<<<grid, 32, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+// Persistent grid: ctas_per_sm (0 = as many as fit) warps on every SM, never
+// more than the items or the staging slots.
+uint32_t batch_grid(uint32_t fit, uint32_t ctas_per_sm, uint64_t n_items)
+{
+    uint32_t per = ctas_per_sm && ctas_per_sm < fit ? ctas_per_sm : fit;
+    uint64_t g = (uint64_t)sm_count() * per;
+    if (g > FAST_MAX_WARPS) g = FAST_MAX_WARPS;
+    if (g > n_items) g = n_items;
+    return g ? (uint32_t)g : 1u;
+}
+
+bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+size_t bsgpu_batch_table_bytes(uint32_t n_chunks)
+{
+    return n_chunks ? table_bytes(n_chunks) : 0;
+}
+
+int bsgpu_batch_plan(int op, const bsgpu_chunk *chunks, uint32_t n_chunks, void *table,
+                     size_t table_bytes_given, uint64_t *n_items, size_t *ws_bytes)
+{
+    if (op != BSGPU_OP_COMPRESS && op != BSGPU_OP_DECOMPRESS) return BSGPU_ERR_ARG;
+    if (!chunks || !n_chunks || !table || !n_items || !ws_bytes) return BSGPU_ERR_ARG;
+    if (table_bytes_given < table_bytes(n_chunks)) return BSGPU_ERR_SPACE;
+    BatchChunk *rec = static_cast<BatchChunk *>(table);
+    uint64_t *starts = reinterpret_cast<uint64_t *>(rec + n_chunks);
+    uint64_t items = 0;
+    for (uint32_t c = 0; c < n_chunks; c++) {
+        const bsgpu_chunk &k = chunks[c];
+        const uint64_t es = k.elem_size;
+        if (es != 1 && es != 2 && es != 4 && es != 8) return BSGPU_ERR_ARG;
+        const uint64_t B = k.block_elems ? k.block_elems : 4096 / es;
+        if (B == 0 || B % 8 || B * es > 8192) return BSGPU_ERR_ARG;
+        if ((!k.in && k.n_elem) || (!k.out && (op == BSGPU_OP_COMPRESS || k.n_elem)))
+            return BSGPU_ERR_ARG;
+        if ((k.in && !aligned(k.in, 16)) || (k.out && !aligned(k.out, 16))) return BSGPU_ERR_ALIGN;
+        const uint64_t full = k.n_elem / B, rem = k.n_elem % B, last = rem - rem % 8;
+        const uint64_t nb = full + (last ? 1 : 0);
+        if (op == BSGPU_OP_COMPRESS &&
+            k.out_cap < bsgpu_compress_bound(k.n_elem, k.elem_size, (size_t)B))
+            return BSGPU_ERR_SPACE;
+        if (op == BSGPU_OP_DECOMPRESS && !k.in) return BSGPU_ERR_ARG;
+        BatchChunk r{};
+        r.in = static_cast<const uint8_t *>(k.in);
+        r.out = static_cast<uint8_t *>(k.out);
+        r.n_elem = k.n_elem;
+        r.in_bytes = k.in_bytes;
+        r.out_cap = k.out_cap;
+        r.item0 = items;
+        r.es = (uint32_t)es;
+        r.B = (uint32_t)B;
+        r.nb = (uint32_t)nb;
+        r.last_B = (uint32_t)(last ? last : B);
+        r.tail = (uint32_t)(rem % 8);
+        std::memcpy(rec + c, &r, sizeof r);
+        starts[c] = items;
+        items += nb ? nb : 1;  // a chunk without blocks still takes one item
+        if (items >= (1ull << 31)) return BSGPU_ERR_ARG;
+    }
+    starts[n_chunks] = items;
+    *n_items = items;
+    *ws_bytes = batch_ws(op, items, FAST_MAX_WARPS).total;
+    return BSGPU_OK;
+}
+
+int bsgpu_compress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_items, int level,
+                         uint64_t *d_out_bytes, uint64_t *d_block_offsets, int *d_chunk_status,
+                         void *ws, size_t ws_bytes, uint32_t ctas_per_sm, void *stream)
+{
+    if (!d_table || !n_chunks || !n_items || n_items >= (1ull << 31) || level < 0 || level > 1)
+        return BSGPU_ERR_ARG;
+    if (!d_out_bytes || !d_chunk_status || !ws) return BSGPU_ERR_ARG;
+    if (!aligned(d_table, 16) || !aligned(ws, 16) || !aligned(d_out_bytes, 8) ||
+        !aligned(d_block_offsets, 8) || !aligned(d_chunk_status, 4))
+        return BSGPU_ERR_ALIGN;
+    const BatchWs w = batch_ws(BSGPU_OP_COMPRESS, n_items, FAST_MAX_WARPS);
+    if (ws_bytes < w.total) return BSGPU_ERR_SPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(ws, 0, w.state + 8 * n_items, s) != cudaSuccess ||
+        cudaMemsetAsync(d_chunk_status, 0, sizeof(int) * n_chunks, s) != cudaSuccess)
+        return BSGPU_ERR_CUDA;
+    BatchArgs b{};
+    b.chunks = static_cast<const BatchChunk *>(d_table);
+    b.starts = reinterpret_cast<const uint64_t *>(b.chunks + n_chunks);
+    b.n_chunks = n_chunks;
+    b.n_items = (uint32_t)n_items;
+    b.state = reinterpret_cast<uint64_t *>((uint8_t *)ws + w.state);
+    b.counter = reinterpret_cast<uint32_t *>((uint8_t *)ws + 4);
+    b.slots = (uint8_t *)ws + w.slots;
+    b.out_bytes = d_out_bytes;
+    b.offsets = d_block_offsets;
+    b.status = d_chunk_status;
+    b.level = level;
+    const uint32_t smem = compress_fast_smem_bytes(level);
+    cudaError_t e;
+    if (level >= 1) {
+        const uint32_t g = batch_grid(occupancy(compress_batch_kernel<1>, smem), ctas_per_sm, n_items);
+        e = launch_batch(compress_batch_kernel<1>, smem, g, s, b);
+    } else {
+        const uint32_t g = batch_grid(occupancy(compress_batch_kernel<0>, smem), ctas_per_sm, n_items);
+        e = launch_batch(compress_batch_kernel<0>, smem, g, s, b);
+    }
+    return e == cudaSuccess ? BSGPU_OK : BSGPU_ERR_CUDA;
+}
+
+int bsgpu_decompress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_items,
+                           const uint64_t *d_in_bytes, const uint64_t *d_block_offsets,
+                           int *d_chunk_status, void *ws, size_t ws_bytes, uint32_t ctas_per_sm,
+                           void *stream)
+{
+    if (!d_table || !n_chunks || !n_items || n_items >= (1ull << 31)) return BSGPU_ERR_ARG;
+    if (!d_chunk_status || !ws) return BSGPU_ERR_ARG;
+    if (!aligned(d_table, 16) || !aligned(ws, 16) || !aligned(d_in_bytes, 8) ||
+        !aligned(d_block_offsets, 8) || !aligned(d_chunk_status, 4))
+        return BSGPU_ERR_ALIGN;
+    const BatchWs w = batch_ws(BSGPU_OP_DECOMPRESS, n_items, FAST_MAX_WARPS);
+    if (ws_bytes < w.total) return BSGPU_ERR_SPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(ws, 0, BATCH_HEADER, s) != cudaSuccess ||
+        cudaMemsetAsync(d_chunk_status, 0, sizeof(int) * n_chunks, s) != cudaSuccess)
+        return BSGPU_ERR_CUDA;
+    BatchArgs b{};
+    b.chunks = static_cast<const BatchChunk *>(d_table);
+    b.starts = reinterpret_cast<const uint64_t *>(b.chunks + n_chunks);
+    b.n_chunks = n_chunks;
+    b.n_items = (uint32_t)n_items;
+    b.counter = reinterpret_cast<uint32_t *>((uint8_t *)ws + 4);
+    b.in_bytes = d_in_bytes;
+    b.status = d_chunk_status;
+    if (d_block_offsets) {
+        b.offsets = const_cast<uint64_t *>(d_block_offsets);
+    } else {
+        b.offsets = reinterpret_cast<uint64_t *>((uint8_t *)ws + w.offsets);
+        chain_walk_batch_kernel<<<(n_chunks + 127) / 128, 128, 0, s>>>(b);
+        if (cudaGetLastError() != cudaSuccess) return BSGPU_ERR_CUDA;
+    }
+    const uint32_t smem = decompress_smem_bytes(8192);
+    const uint32_t g = batch_grid(occupancy(decompress_batch_kernel, smem), ctas_per_sm, n_items);
+    return launch_batch(decompress_batch_kernel, smem, g, s, b) == cudaSuccess ? BSGPU_OK
+                                                                               : BSGPU_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,617 @@
+// Device-side building blocks shared by the codec kernels (kernels.cu) and
+// the batched engine (batch.cu): shared-memory plans, bulk-copy staging and
+// write-out, the precision-reduction helpers (Sec. 3.2), the decoupled
+// look-back that places variable-size compressed blocks in one pass, block
+// placement and encoding, and the decoder's block fetch.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "lz4_warp.cuh"
+#include "shuffle.cuh"
+
+namespace bsg {
+
+// ---------------------------------------------------------------------------
+// Shared-memory plans
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr uint32_t r16(uint32_t x) { return (x + 15u) & ~15u; }
+__host__ __device__ constexpr uint32_t r128(uint32_t x) { return (x + 127u) & ~127u; }
+__host__ __device__ constexpr uint32_t cmax(uint32_t a, uint32_t b) { return a > b ? a : b; }
+__host__ __device__ constexpr uint32_t lz4b(uint32_t n) { return n + n / 255u + 16u; }
+
+template <uint32_t MAXB, int LEVEL>
+struct CompPlan {
+    static constexpr uint32_t IN = r16(MAXB);          // staged block (bulk copy target)
+    static constexpr uint32_t TMP = r16(MAXB + 16);    // bit-rows (LZ4 input, read 8 past)
+    // LZ4 output with its 4-byte length field in front (write-out reads 16 past)
+    static constexpr uint32_t OUT = r16(4 + lz4b(MAXB) + 16);
+    // level 1: one 16-bit hash entry per probed word position of the largest
+    // block; level 0: two word-equality bitmaps
+    static constexpr int HBITS = MAXB <= 8192 ? 11 : (MAXB <= 16384 ? 12 : 13);
+    static constexpr uint32_t SCR = LEVEL >= 1 ? (2u << HBITS) : 2u * 4u * (MAXB / 128u + 2u);
+    static constexpr uint32_t BYTES = IN + TMP + OUT + r16(SCR) + 16;
+};
+
+template <uint32_t MAXB>
+struct DecPlan {
+    // stream bytes of one block at their 16-byte phase, read 8 past the end
+    static constexpr uint32_t COMP = r16(16 + 4 + lz4b(MAXB) + 16);
+    static constexpr uint32_t DEC = r16(MAXB + 16);
+    static constexpr uint32_t BYTES = COMP + DEC + 16;
+};
+
+template <uint32_t MAXB>
+struct ShufPlan {
+    static constexpr uint32_t BUF = r128(MAXB + 32);
+    static constexpr uint32_t BYTES = 3 * BUF + 16;
+};
+
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+BSG_D uint32_t grab_tile(uint32_t *counter, uint32_t lane)
+{
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1u);
+    return __shfl_sync(FULL, t, 0);
+}
+
+BSG_D uint32_t block_elems_of(const CodecArgs &a, uint32_t tile)
+{
+    return tile + 1 == a.nb ? a.last_B : a.B;
+}
+
+// Start moving `bytes` from global `src` to shared `dst`: one bulk copy when
+// both ends are 16-byte aligned (returns true: wait on `bar`), otherwise a
+// plain warp copy (returns false: done).
+BSG_D bool load_block(uint8_t *dst, const uint8_t *src, uint32_t bytes, uint64_t *bar,
+                      uint32_t lane)
+{
+    if ((bytes & 15u) == 0 && ((uintptr_t)src & 15u) == 0 && bytes > 0) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_g2s(dst, src, bytes, bar);
+        }
+        return true;
+    }
+    for (uint32_t k = lane; k < bytes; k += 32) dst[k] = src[k];
+    __syncwarp();
+    return false;
+}
+
+// Copy len bytes from 16-byte aligned shared `s` to global `g` (any alignment):
+// byte stores up to g's next 16-byte boundary, then 16-byte stores assembled
+// from two aligned shared vectors and a funnel shift, then the ragged end.
+// Reads up to 32 bytes past s + len.
+BSG_D void copy_out(const uint8_t *s, uint8_t *g, uint32_t len, uint32_t lane)
+{
+    uint32_t head = (uint32_t)((16u - ((uintptr_t)g & 15u)) & 15u);
+    if (head > len) head = len;
+    if (lane < head) g[lane] = s[lane];
+    const uint32_t nchunk = (len - head) / 16u;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(s);
+    const uint32_t q = (head >> 2) & 3u, sh = (head & 3u) * 8u;
+    for (uint32_t c = lane; c < nchunk; c += 32) {
+        uint32_t so = head + 16u * c;
+        uint4 A = s4[so >> 4], B = s4[(so >> 4) + 1];
+        uint4 v;
+        switch (q) {  // uniform across the warp
+        case 0:
+            v = make_uint4(funnel_r(A.x, A.y, sh), funnel_r(A.y, A.z, sh), funnel_r(A.z, A.w, sh),
+                           funnel_r(A.w, B.x, sh));
+            break;
+        case 1:
+            v = make_uint4(funnel_r(A.y, A.z, sh), funnel_r(A.z, A.w, sh), funnel_r(A.w, B.x, sh),
+                           funnel_r(B.x, B.y, sh));
+            break;
+        case 2:
+            v = make_uint4(funnel_r(A.z, A.w, sh), funnel_r(A.w, B.x, sh), funnel_r(B.x, B.y, sh),
+                           funnel_r(B.y, B.z, sh));
+            break;
+        default:
+            v = make_uint4(funnel_r(A.w, B.x, sh), funnel_r(B.x, B.y, sh), funnel_r(B.y, B.z, sh),
+                           funnel_r(B.z, B.w, sh));
+            break;
+        }
+        *reinterpret_cast<uint4 *>(g + so) = v;
+    }
+    for (uint32_t k = head + 16u * nchunk + lane; k < len; k += 32) g[k] = s[k];
+}
+
+BSG_D void put_be32(uint8_t *p, uint32_t v)
+{
+    p[0] = (uint8_t)(v >> 24);
+    p[1] = (uint8_t)(v >> 16);
+    p[2] = (uint8_t)(v >> 8);
+    p[3] = (uint8_t)v;
+}
+
+BSG_D uint32_t get_be32(const uint8_t *p)
+{
+    return ((uint32_t)p[0] << 24) | ((uint32_t)p[1] << 16) | ((uint32_t)p[2] << 8) | p[3];
+}
+
+// 12-byte chunk header: big-endian total bytes, big-endian block bytes
+BSG_D void write_chunk_header(uint8_t *out, uint64_t total, uint32_t block_bytes, uint32_t lane)
+{
+    if (lane < 8) out[lane] = (uint8_t)(total >> (8 * (7 - lane)));
+    else if (lane < 12) out[lane] = (uint8_t)(block_bytes >> (8 * (11 - lane)));
+}
+
+// ---------------------------------------------------------------------------
+// Precision reduction of complex samples (Sec. 3.2, Sec. 6 steps 1-3)
+// ---------------------------------------------------------------------------
+// Round one complex sample (re, im bits) of product p = (i, j) at (f, t).
+BSG_D uint2 reduce_sample(uint2 v, uint32_t ij, uint32_t f, uint32_t t, const VisParams &P)
+{
+    const uint32_t i = ij & 0xffffu, j = ij >> 16;
+    const uint32_t row = f * P.n_in;
+    const float Ai = __ldg(P.autos + (size_t)(row + i) * P.T + t);
+    const bool is_auto = i == j;
+    // autos: s^2 = V_ii^2 / N, q = (2 c A_i) A_i, Im V_ii has no noise and stays;
+    // crosses: s^2 = V_ii V_jj / (2N), q = (c A_i) A_j for both components
+    const float Aj = is_auto ? Ai : __ldg(P.autos + (size_t)(row + j) * P.T + t);
+    const float q = __fmul_rn(__fmul_rn(vis_c(P, f, t, is_auto), Ai), Aj);
+    v.x = reduce_bits(v.x, q, P.is_int);
+    if (!is_auto) v.y = reduce_bits(v.y, q, P.is_int);
+    return v;
+}
+
+// Round `ncplx` consecutive complex samples starting at global complex index
+// c0, lane k taking samples c0 + k, c0 + k + 32, ...  src and dst may be the
+// same (in-place) and may be shared or global memory.
+BSG_D void reduce_run(const uint2 *src, uint2 *dst, uint32_t c0, uint32_t ncplx,
+                      const VisParams &P, uint32_t lane)
+{
+    uint32_t c = c0 + lane;
+    uint32_t fp = c / P.T;
+    uint32_t t = c - fp * P.T;
+    uint32_t f = fp / P.P;
+    uint32_t p = fp - f * P.P;
+    for (uint32_t k = lane; k < ncplx; k += 32) {
+        const uint32_t ij = __ldg(P.pairs + p);
+        dst[k] = reduce_sample(src[k], ij, f, t, P);
+        t += P.rT;
+        p += P.qT;
+        if (t >= P.T) {
+            t -= P.T;
+            p++;
+        }
+        while (p >= P.P) {
+            p -= P.P;
+            f++;
+        }
+    }
+}
+
+// Same for an even number of samples starting at an even index c0 when the
+// time axis is even: each lane takes two consecutive samples (t, t+1) of one
+// product per 16-byte access, so the product lookup and the two autos loads
+// serve both, and the auto / cross choice is a select (for an auto A_j = A_i,
+// the constant is 2c and the imaginary part is kept).
+BSG_D void reduce_run2(const uint4 *src, uint4 *dst, uint32_t c0, uint32_t ncplx,
+                       const VisParams &P, uint32_t lane)
+{
+    uint32_t c = c0 + 2 * lane;
+    uint32_t fp = c / P.T;
+    uint32_t t = c - fp * P.T;
+    uint32_t f = fp / P.P;
+    uint32_t p = fp - f * P.P;
+    const uint32_t q64 = 64 / P.T, r64 = 64 % P.T;
+    for (uint32_t k = lane; k < ncplx / 2; k += 32) {
+        const uint32_t ij = __ldg(P.pairs + p);
+        const uint32_t i = ij & 0xffffu, j = ij >> 16;
+        const uint32_t row = f * P.n_in;
+        const float2 Ai = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + i) * P.T + t));
+        const float2 Aj = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + j) * P.T + t));
+        const bool is_auto = i == j;
+        const float qa = __fmul_rn(__fmul_rn(vis_c(P, f, t, is_auto), Ai.x), Aj.x);
+        const float qb = __fmul_rn(__fmul_rn(vis_c(P, f, t + 1, is_auto), Ai.y), Aj.y);
+        uint4 v = src[k];
+        v.x = reduce_bits(v.x, qa, P.is_int);
+        v.z = reduce_bits(v.z, qb, P.is_int);
+        if (!is_auto) {
+            v.y = reduce_bits(v.y, qa, P.is_int);
+            v.w = reduce_bits(v.w, qb, P.is_int);
+        }
+        dst[k] = v;
+        t += r64;
+        p += q64;
+        if (t >= P.T) {
+            t -= P.T;
+            p++;
+        }
+        while (p >= P.P) {
+            p -= P.P;
+            f++;
+        }
+    }
+}
+
+// Precision reduction fused into the 32 x 32 register transpose of a block of
+// float32 components (elem size 4), for cubes whose time axis is a multiple
+// of 16: a group of 32 floats is 16 consecutive time samples of one product,
+// so one product lookup and 16 autos pairs serve the whole group.  Lane k of
+// the warp takes groups k, k + 32, ...; its 16-byte chunks are read in a
+// lane-rotated order (conflict-free banks) and the autos are loaded in the
+// same order; the rotation is undone on the transposed rows.
+BSG_D void round_shuffle4_vis(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t c_blk,
+                              const VisParams &P, uint32_t lane)
+{
+    const uint32_t G = Bb / 32;
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t g = lane; g < G; g += 32) {
+        const uint8_t *grp = src + 128u * g;
+        const uint32_t rot = g & 7u;
+        const uint32_t cg = c_blk + 16 * g;       // first sample of the group
+        const uint32_t fp = cg / P.T;
+        const uint32_t t0 = cg - fp * P.T;
+        const uint32_t f = fp / P.P;
+        const uint32_t p = fp - f * P.P;
+        const uint32_t ij = __ldg(P.pairs + p);
+        const uint32_t i = ij & 0xffffu, j = ij >> 16;
+        const bool is_auto = i == j;
+        const float *ai = P.autos + (size_t)(f * P.n_in + i) * P.T + t0;
+        const float *aj = P.autos + (size_t)(f * P.n_in + j) * P.T + t0;
+        uint32_t a[32];
+        float2 Ai[8], Aj[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t c = (k + rot) & 7u;  // chunk c holds samples t0 + 2c, t0 + 2c + 1
+            uint4 v = *reinterpret_cast<const uint4 *>(grp + 16u * c);
+            a[4 * k] = v.x;
+            a[4 * k + 1] = v.y;
+            a[4 * k + 2] = v.z;
+            a[4 * k + 3] = v.w;
+            Ai[k] = __ldg(reinterpret_cast<const float2 *>(ai + 2 * c));
+            Aj[k] = __ldg(reinterpret_cast<const float2 *>(aj + 2 * c));
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t t = t0 + 2 * ((k + rot) & 7u);
+            const float q0 = __fmul_rn(__fmul_rn(vis_c(P, f, t, is_auto), Ai[k].x), Aj[k].x);
+            const float q1 = __fmul_rn(__fmul_rn(vis_c(P, f, t + 1, is_auto), Ai[k].y), Aj[k].y);
+            a[4 * k] = reduce_bits(a[4 * k], q0, P.is_int);
+            a[4 * k + 2] = reduce_bits(a[4 * k + 2], q1, P.is_int);
+            if (!is_auto) {
+                a[4 * k + 1] = reduce_bits(a[4 * k + 1], q0, P.is_int);
+                a[4 * k + 3] = reduce_bits(a[4 * k + 3], q1, P.is_int);
+            }
+        }
+        // a[m] holds float (m + 4 rot) mod 32 of the group
+        transpose32(a);
+#pragma unroll
+        for (int r = 0; r < 32; r++) d32[r * G + g] = rotl(a[r], 4u * rot);
+    }
+}
+
+// Round the component (32 bits) at global component index fi (used for the
+// verbatim tail).
+BSG_D uint32_t reduce_component_at(uint32_t xb, uint64_t fi, const VisParams &P)
+{
+    uint32_t c = (uint32_t)(fi >> 1);
+    uint32_t fp = c / P.T, t = c - fp * P.T;
+    uint32_t f = fp / P.P, p = fp - f * P.P;
+    uint2 v = (fi & 1) ? make_uint2(0u, xb) : make_uint2(xb, 0u);
+    const uint32_t ij = __ldg(P.pairs + p);
+    // the imaginary part of an auto is never rounded; everything else as usual
+    const uint2 r = reduce_sample(v, ij, f, t, P);
+    return (fi & 1) ? r.y : r.x;
+}
+
+// ---------------------------------------------------------------------------
+// Decoupled look-back over per-block compressed sizes (single-pass output
+// placement).  state[t]: 0 = not ready, (1 << 62) | aggregate, (2 << 62) |
+// inclusive prefix.  Tiles are taken in order from a counter, so every
+// predecessor is held by a running warp; waits are bounded all the same.
+// ---------------------------------------------------------------------------
+constexpr uint64_t LB_FA = 1ull << 62, LB_FP = 2ull << 62, LB_VM = (1ull << 62) - 1;
+
+// Make a block's compressed size visible to its successors (tile 0 publishes
+// its inclusive prefix directly).
+BSG_D void lookback_publish(uint64_t *state, uint32_t tile, uint64_t agg, uint32_t lane)
+{
+    if (lane == 0) st_relaxed_u64(state + tile, (tile == 0 ? LB_FP : LB_FA) | agg);
+}
+
+// Exclusive prefix of a block whose size is already published; publishes its
+// inclusive prefix.
+BSG_D uint64_t lookback_resolve(uint64_t *state, uint32_t tile, uint64_t agg, int *status,
+                                uint32_t lane)
+{
+    constexpr uint64_t FP = LB_FP, VM = LB_VM;
+    if (tile == 0) return 0;
+    uint64_t excl = 0;
+    int64_t base = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    for (;;) {
+        int64_t idx = base - (int64_t)lane;
+        uint64_t v = idx >= 0 ? ld_relaxed_u64(state + idx) : FP;
+        uint32_t flag = (uint32_t)(v >> 62);
+        uint32_t pm = __ballot_sync(FULL, flag == 2);
+        uint32_t im = __ballot_sync(FULL, flag == 0);
+        uint32_t first = pm ? (uint32_t)(__ffs(pm) - 1) : 31u;
+        uint32_t need = first >= 31 ? FULL : ((2u << first) - 1u);
+        if (im & need) {
+            // predecessors usually publish within a few polls (each poll is a
+            // round trip to L2); sleep only once the wait is clearly long
+            if (++spins > (1u << 21)) {
+                if (lane == 0) set_status(status, BSGPU_ERR_TIMEOUT);
+                break;
+            }
+            if (spins > 4096) __nanosleep(100);
+            continue;
+        }
+        uint64_t x = lane <= first ? (v & VM) : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+        excl += x;
+        if (pm) break;
+        base -= 32;
+    }
+    if (lane == 0) st_relaxed_u64(state + tile, FP | (excl + agg));
+    return excl;
+}
+
+BSG_D uint64_t lookback(uint64_t *state, uint32_t tile, uint64_t agg, int *status,
+                        uint32_t lane)
+{
+    lookback_publish(state, tile, agg, lane);
+    return lookback_resolve(state, tile, agg, status, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Compress: [round ->] bitshuffle -> LZ4 -> placed by look-back
+// ---------------------------------------------------------------------------
+// Round (for a cube) and bit-transpose block `tile` from `in` into `tmp`.
+BSG_D void compress_prepare(const CodecArgs &a, uint32_t tile, uint8_t *in, uint8_t *tmp,
+                            uint32_t lane)
+{
+    const uint32_t Bb = block_elems_of(a, tile);
+    // the block starts at a whole complex sample (B is a multiple of 8)
+    const uint32_t c0 = (uint32_t)(((uint64_t)tile * a.B * a.es) >> 3);
+    const uint32_t ncplx = Bb * a.es / 8;
+    if (a.vis.enabled && a.es == 4 && Bb % 32u == 0 && a.vis.T % 16u == 0) {
+        round_shuffle4_vis(in, tmp, Bb, c0, a.vis, lane);
+        return;
+    }
+    if (a.vis.enabled) {
+        if ((a.vis.T & 1u) == 0) {  // c0 and ncplx are even
+            uint4 *b4 = reinterpret_cast<uint4 *>(in);
+            reduce_run2(b4, b4, c0, ncplx, a.vis, lane);
+        } else {
+            uint2 *b2 = reinterpret_cast<uint2 *>(in);
+            reduce_run(b2, b2, c0, ncplx, a.vis, lane);
+        }
+        __syncwarp();
+    }
+    shuffle_block(in, tmp, Bb, a.es, lane);
+}
+
+// Write block `tile` (its 4-byte length field and cs LZ4 bytes at `blk`, in
+// shared or global memory) at stream offset D, with the index entry, the
+// chunk header (block 0) and, after the last block, the verbatim tail.
+BSG_D void compress_place(const CodecArgs &a, uint32_t tile, const uint8_t *blk, uint32_t cs,
+                          uint64_t D, uint32_t lane)
+{
+    if (D + 4 + cs > a.out_cap) {
+        if (lane == 0) set_status(a.status, BSGPU_ERR_SPACE);
+        return;
+    }
+    copy_out(blk, a.out + D, 4 + cs, lane);
+    if (a.block_offsets && lane == 0) a.block_offsets[tile] = D;
+    if (tile == 0) write_chunk_header(a.out, a.n_elem * a.es, a.B * a.es, lane);
+    if (tile + 1 == a.nb) {
+        // the (n mod 8) trailing elements follow the last block verbatim
+        const uint64_t end = D + 4 + cs;
+        const uint64_t first = a.n_elem - a.tail_elems;
+        const uint32_t tb = a.tail_elems * a.es;
+        if (end + tb > a.out_cap) {
+            if (lane == 0) set_status(a.status, BSGPU_ERR_SPACE);
+            return;
+        }
+        if (a.vis.enabled) {
+            // the tail as 32-bit components, each rounded like any other
+            const uint32_t tc = tb / 4;
+            const uint64_t c0 = first * a.es / 4;
+            if (lane < tc) {
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(a.in);
+                const uint32_t u = reduce_component_at(src[c0 + lane], c0 + lane, a.vis);
+                for (int k = 0; k < 4; k++) a.out[end + 4 * lane + k] = (uint8_t)(u >> (8 * k));
+            }
+        } else {
+            for (uint32_t k = lane; k < tb; k += 32) a.out[end + k] = a.in[first * a.es + k];
+        }
+        if (lane == 0) *a.out_bytes = end + tb;
+    }
+}
+
+// LZ4-encode the bit-rows in `tmp` into `dst` after a 4-byte length field;
+// returns the LZ4 size.
+template <int LEVEL, int HBITS>
+BSG_D uint32_t compress_encode(const CodecArgs &a, uint32_t Bb, const uint8_t *tmp, uint8_t *dst,
+                               void *scratch, uint32_t lane)
+{
+    const uint32_t S = Bb * a.es;
+    // bit-rows are Bb/8 bytes long: the previous row is one of the candidates
+    uint32_t cs = LEVEL >= 1
+        ? lz4_encode_warp<1, HBITS>(tmp, S, Bb / 8, dst + 4, static_cast<uint16_t *>(scratch))
+        : lz4_encode_bitmap(tmp, S, Bb / 8, dst + 4, static_cast<uint32_t *>(scratch));
+    if (cs == 0xffffffffu) {  // progress guard (not reachable for valid sizes)
+        if (lane == 0) set_status(a.status, BSGPU_ERR_CUDA);
+        cs = 0;
+    }
+    if (lane == 0) put_be32(dst, cs);
+    __syncwarp();
+    return cs;
+}
+
+// LZ4-encode the bit-rows in `tmp` into `out`, place the block by look-back
+// and write it.
+template <uint32_t MAXB, int LEVEL>
+BSG_D void compress_finish(const CodecArgs &a, uint32_t tile, uint8_t *tmp, uint8_t *out,
+                           void *scratch, uint32_t lane)
+{
+    using L = CompPlan<MAXB, LEVEL>;
+    const uint32_t Bb = block_elems_of(a, tile);
+    const uint32_t cs = compress_encode<LEVEL, L::HBITS>(a, Bb, tmp, out, scratch, lane);
+    const uint64_t excl = lookback(a.tile_state, tile, 4ull + cs, a.status, lane);
+    compress_place(a, tile, out, cs, 12 + excl, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Compress, fast path: blocks of at most 8 KiB of 4- or 8-byte elements
+// ---------------------------------------------------------------------------
+template <int LEVEL>
+struct FastPlan {
+    static constexpr uint32_t MAXB = 8192;
+    static constexpr uint32_t TMP = r16(MAXB + 16);  // staged block, then its bit-rows
+    static constexpr int HBITS = 11;
+    static constexpr uint32_t SCR = LEVEL >= 1 ? (2u << HBITS) : 2u * 4u * (MAXB / 128u + 2u);
+    static constexpr uint32_t BYTES = TMP + r16(SCR) + 16;
+};
+
+static_assert(FAST_SLOT_BYTES >= r16(4 + lz4b(8192) + 32), "staging slot too small");
+
+// Round the 32 components of one group (16 samples t0 .. t0 + 15 of one
+// product) held as a[m] = component (m + 4 rot) mod 32.  GEN: int32 data or a
+// per-sample compensated c; otherwise float32 with the constant c, which is
+// kept as its own instantiation so that the common case carries no per-value
+// selects.
+template <bool GEN>
+BSG_D void round_group(const VisParams &P, uint32_t (&a)[32], uint32_t rot, uint32_t f,
+                       uint32_t t0, const float *ai, const float *aj, bool is_auto)
+{
+    const float cc = is_auto ? P.c2 : P.c;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const uint32_t c = (k + rot) & 7u;  // chunk c: samples t0 + 2c, t0 + 2c + 1
+        const float2 Ai = __ldg(reinterpret_cast<const float2 *>(ai + 2 * c));
+        const float2 Aj = __ldg(reinterpret_cast<const float2 *>(aj + 2 * c));
+        if (GEN) {
+            const float q0 = __fmul_rn(__fmul_rn(vis_c(P, f, t0 + 2 * c, is_auto), Ai.x), Aj.x);
+            const float q1 = __fmul_rn(__fmul_rn(vis_c(P, f, t0 + 2 * c + 1, is_auto), Ai.y), Aj.y);
+            a[4 * k] = reduce_bits(a[4 * k], q0, P.is_int);
+            a[4 * k + 2] = reduce_bits(a[4 * k + 2], q1, P.is_int);
+            if (!is_auto) {
+                a[4 * k + 1] = reduce_bits(a[4 * k + 1], q0, P.is_int);
+                a[4 * k + 3] = reduce_bits(a[4 * k + 3], q1, P.is_int);
+            }
+        } else {
+            const float q0 = __fmul_rn(__fmul_rn(cc, Ai.x), Aj.x);
+            const float q1 = __fmul_rn(__fmul_rn(cc, Ai.y), Aj.y);
+            a[4 * k] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k]), q0));
+            a[4 * k + 2] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 2]), q1));
+            if (!is_auto) {
+                a[4 * k + 1] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 1]), q0));
+                a[4 * k + 3] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 3]), q1));
+            }
+        }
+    }
+}
+
+// Precision reduction of one group of 32 components (16 consecutive time
+// samples of one product, the time axis being a multiple of 16) held in
+// registers in lane-rotated chunk order: a[m] is component (m + 4 (g & 7)) mod 32.
+template <bool GEN>
+struct VisGroupRound {
+    const VisParams *P;
+    uint32_t c_blk;  // complex index of the block's first sample
+    BSG_D void operator()(uint32_t g, uint32_t (&a)[32]) const
+    {
+        const uint32_t rot = g & 7u;
+        const uint32_t cg = c_blk + 16 * g;
+        const uint32_t fp = cg / P->T;
+        const uint32_t t0 = cg - fp * P->T;
+        const uint32_t f = fp / P->P;
+        const uint32_t p = fp - f * P->P;
+        const uint32_t ij = __ldg(P->pairs + p);
+        const uint32_t i = ij & 0xffffu, j = ij >> 16;
+        const bool is_auto = i == j;
+        const float *ai = P->autos + (size_t)(f * P->n_in + i) * P->T + t0;
+        const float *aj = P->autos + (size_t)(f * P->n_in + j) * P->T + t0;
+        round_group<GEN>(*P, a, rot, f, t0, ai, aj, is_auto);
+    }
+};
+
+struct NoRound {
+    BSG_D void operator()(uint32_t, uint32_t (&)[32]) const {}
+};
+
+// ---------------------------------------------------------------------------
+// Decompress: LZ4 decode -> bit un-transpose, every block at once
+// ---------------------------------------------------------------------------
+
+struct DecLoad {
+    bool bulk;       // a bulk copy is in flight on the barrier
+    bool ok;         // offsets passed the range checks
+    uint32_t delta;  // shared index of the first stream byte (D & 15)
+    uint32_t clen;   // LZ4 bytes of the block
+    uint32_t eidx;   // shared index this lane's edge byte goes to (or ~0)
+    uint8_t ebyte;
+};
+
+// Bytes [D, Dn) of the stream go to shared index x - (D & ~15): the 16-byte
+// aligned middle by one bulk copy, the ragged head and tail (< 16 bytes each)
+// by plain loads held in registers until the block is processed.
+BSG_D DecLoad dec_issue(const CodecArgs &a, uint32_t tile, uint8_t *dst, uint64_t *bar,
+                        uint32_t lane)
+{
+    DecLoad r;
+    r.bulk = false;
+    r.ok = false;
+    r.eidx = ~0u;
+    r.ebyte = 0;
+    r.delta = 0;
+    r.clen = 0;
+    const uint32_t Bb = block_elems_of(a, tile);
+    const uint64_t tail_b = (uint64_t)a.tail_elems * a.es;
+    if (a.in_bytes < 12 + tail_b) return r;
+    const uint64_t D = a.block_offsets[tile];
+    const uint64_t Dn = tile + 1 < a.nb ? a.block_offsets[tile + 1] : a.in_bytes - tail_b;
+    if (D < 12 || Dn < D + 4 || Dn > a.in_bytes || Dn - D - 4 > lz4b(Bb * a.es)) return r;
+    r.ok = true;
+    r.clen = (uint32_t)(Dn - D - 4);
+    // alignment is a property of the absolute address, not of the offset
+    const uint64_t g0 = (uint64_t)(uintptr_t)(a.in + D), gn = g0 + (Dn - D);
+    const uint64_t base = g0 & ~15ull;
+    r.delta = (uint32_t)(g0 - base);
+    const uint64_t A0 = (g0 + 15) & ~15ull, A1 = gn & ~15ull;
+    const uint64_t head_end = A0 < gn ? A0 : gn;
+    const uint64_t tail_beg = A1 > A0 ? A1 : A0;
+    if (A1 > A0) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar, (uint32_t)(A1 - A0));
+            bulk_g2s(dst + (A0 - base), reinterpret_cast<const void *>(A0), (uint32_t)(A1 - A0),
+                     bar);
+        }
+        r.bulk = true;
+    }
+    uint64_t x = lane < 16 ? g0 + lane : tail_beg + (lane - 16);
+    if ((lane < 16 && x < head_end) || (lane >= 16 && x < gn)) {
+        r.ebyte = *reinterpret_cast<const uint8_t *>(x);
+        r.eidx = (uint32_t)(x - base);
+    }
+    return r;
+}
+
+
+template <typename K>
+inline cudaError_t launch_warp_kernel(K kernel, uint32_t smem, uint32_t grid, cudaStream_t s,
+                                      const CodecArgs &a)
+{
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kernel<<<grid, 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+
+}  // namespace bsg

@@ -327,9 +327,134 @@ BSG_D void shuffle8_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
     }
 }
 
+// 2-byte elements: a lane takes a group of 64 elements (128 bytes, 32 words
+// w_0..w_31, word w_j holding elements 2j and 2j + 1).  Pairing w_j with
+// w_(j+16) by byte permutes gives 32 words P_n = e_n | e_(n+32) << 16, so one
+// 32 x 32 transpose yields bit r of elements 0..31 in word r and of elements
+// 32..63 in word 16 + r: the group's two words of bit-row r (16 rows of Bb/8
+// bytes).  The 16-byte chunks are read in a lane-rotated order over all 8
+// chunks (conflict-free banks): step k reads chunk c = (k + g) & 7 and its
+// partner c ^ 4, so a pair arrives as (w_j, w_(j+16)) when c < 4 and swapped
+// otherwise, and the byte-permute selectors follow (a per-lane choice).  The
+// columns come out rotated by 8 (g & 3) bits, undone on the rows.
+struct Shuf2Sel {
+    uint32_t lo, hi;  // selectors giving the pair's low and high halves
+};
+
+BSG_HD Shuf2Sel shuf2_sel(uint32_t c)
+{
+    return c < 4 ? Shuf2Sel{0x5410u, 0x7632u} : Shuf2Sel{0x1054u, 0x3276u};
+}
+
+// Bb <= 2048 (G <= 32 groups of 64, one per lane) or Bb == 4096 (G == 64:
+// rows 0..7 of the first 32 groups fall in the first half of the buffer and
+// are written before the second groups are read; at most 48 live values).
+BSG_D void shuffle2_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t G = Bb / 64;
+    auto read_group = [&](uint32_t g, uint32_t (&a)[32]) {
+        const uint8_t *grp = buf + 128u * g;
+        const uint32_t rot = g & 7u;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t c = (k + rot) & 7u;
+            const uint4 v = *reinterpret_cast<const uint4 *>(grp + 16u * c);
+            const uint4 w = *reinterpret_cast<const uint4 *>(grp + 16u * (c ^ 4u));
+            const Shuf2Sel sel = shuf2_sel(c);
+            const uint32_t x[4] = {v.x, v.y, v.z, v.w}, y[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                a[8 * k + 2 * i] = bperm(x[i], y[i], sel.lo);
+                a[8 * k + 2 * i + 1] = bperm(x[i], y[i], sel.hi);
+            }
+        }
+        // a[n] = P_((n + 8 rot) mod 32)
+        transpose32(a);
+    };
+    auto put_rows = [&](uint32_t g, const uint32_t (&a)[32], int r0, int r1) {
+        const uint32_t s = 8u * (g & 3u);
+#pragma unroll
+        for (int r = r0; r < r1; r++)
+            *reinterpret_cast<uint2 *>(buf + 4u * (2u * G * r + 2u * g)) =
+                make_uint2(rotl(a[r], s), rotl(a[16 + r], s));
+    };
+    const uint32_t g0 = lane;
+    uint32_t a[32];
+    if (g0 < G) read_group(g0, a);
+    __syncwarp();
+    if (G <= 32) {
+        if (g0 < G) put_rows(g0, a, 0, 16);
+        return;
+    }
+    // G == 64
+    put_rows(g0, a, 0, 8);
+    const uint32_t g1 = lane + 32u;
+    uint32_t b[32];
+    read_group(g1, b);
+    __syncwarp();
+    put_rows(g0, a, 8, 16);
+    put_rows(g1, b, 0, 16);
+}
+
+// Inverse of shuffle2_inplace (same shapes).  With G == 64 a lane reads all
+// of its first group and rows 0..7 of its second (48 values) before anything
+// is written.
+BSG_D void unshuffle2_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t G = Bb / 64;
+    auto get_rows = [&](uint32_t g, uint32_t (&a)[32], int r0, int r1) {
+        const uint32_t s = 8u * (g & 3u);
+#pragma unroll
+        for (int r = r0; r < r1; r++) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(buf + 4u * (2u * G * r + 2u * g));
+            a[r] = rotr(v.x, s);
+            a[16 + r] = rotr(v.y, s);
+        }
+    };
+    auto store_group = [&](uint32_t g, uint32_t (&a)[32]) {
+        transpose32(a);  // a[n] = P_((n + 8 rot) mod 32)
+        uint8_t *grp = buf + 128u * g;
+        const uint32_t rot = g & 7u;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t c = (k + rot) & 7u;
+            // P_2j = lo(w_j) | lo(w_(j+16)) << 16, P_2j+1 = hi(w_j) | hi(w_(j+16)) << 16
+            uint32_t x[4], y[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const uint32_t wj = bperm(a[8 * k + 2 * i], a[8 * k + 2 * i + 1], 0x5410u);
+                const uint32_t wj16 = bperm(a[8 * k + 2 * i], a[8 * k + 2 * i + 1], 0x7632u);
+                x[i] = c < 4 ? wj : wj16;
+                y[i] = c < 4 ? wj16 : wj;
+            }
+            *reinterpret_cast<uint4 *>(grp + 16u * c) = make_uint4(x[0], x[1], x[2], x[3]);
+            *reinterpret_cast<uint4 *>(grp + 16u * (c ^ 4u)) = make_uint4(y[0], y[1], y[2], y[3]);
+        }
+    };
+    const uint32_t g0 = lane;
+    uint32_t a[32];
+    if (G <= 32) {
+        if (g0 < G) get_rows(g0, a, 0, 16);
+        __syncwarp();
+        if (g0 < G) store_group(g0, a);
+        return;
+    }
+    // G == 64
+    const uint32_t g1 = lane + 32u;
+    uint32_t b[32];
+    get_rows(g0, a, 0, 16);
+    get_rows(g1, b, 0, 8);
+    __syncwarp();
+    store_group(g0, a);
+    get_rows(g1, b, 8, 16);
+    __syncwarp();
+    store_group(g1, b);
+}
+
 // Whether a block can be bit-transposed in place by the register paths above.
 BSG_HD bool shuffle_inplace_ok(uint32_t es, uint32_t Bb)
 {
+    if (es == 2) return Bb % 64u == 0 && (Bb <= 2048 || Bb == 4096);
     return Bb % 32u == 0 && ((es == 4 && (Bb <= 1024 || Bb == 2048)) || (es == 8 && Bb <= 1024));
 }
 

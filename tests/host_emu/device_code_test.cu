@@ -96,19 +96,24 @@ static int test_shuffles(std::mt19937 &rng)
     return bad;
 }
 
+static int g_inplace_cases = 0;
+
 static int test_inplace_unshuffle(std::mt19937 &rng)
 {
     int bad = 0;
-    for (int es : {4, 8})
-        for (int B : {32, 64, 96, 512, 1024, 1536, 2048}) {
+    for (int es : {2, 4, 8})
+        for (int B : {32, 64, 96, 128, 512, 1024, 1536, 2048, 3072, 4096}) {
             if (!unshuffle_inplace_ok(es, B)) continue;  // (B <= 1024 or 2048 for es 4)
+            g_inplace_cases++;
             size_t S = (size_t)B * es;
             for (size_t i = 0; i < S; i++) A[i] = (uint8_t)rng();
             std::vector<uint8_t> rows(S);
             orc_bitshuffle(A, rows.data(), B, es, B, 0);
             memcpy(C, rows.data(), S);
             run_warp([&] {
-                if (es == 4)
+                if (es == 2)
+                    unshuffle2_inplace(C, B, threadIdx.x);
+                else if (es == 4)
                     unshuffle4_inplace(C, B, threadIdx.x);
                 else
                     unshuffle8_inplace(C, B, threadIdx.x);
@@ -117,7 +122,9 @@ static int test_inplace_unshuffle(std::mt19937 &rng)
             if (shuffle_inplace_ok(es, B)) {
                 memcpy(C, A, S);
                 run_warp([&] {
-                    if (es == 4)
+                    if (es == 2)
+                        shuffle2_inplace(C, B, threadIdx.x);
+                    else if (es == 4)
                         shuffle4_inplace(C, B, threadIdx.x, [](uint32_t, uint32_t (&)[32]) {});
                     else
                         shuffle8_inplace(C, B, threadIdx.x);
@@ -247,6 +254,8 @@ int main()
     int t = test_transpose(rng), g = test_granularity_bits(rng), s = test_shuffles(rng);
     g += test_round_int(rng);
     s += test_inplace_unshuffle(rng);
+    printf("in-place shapes %d\n", g_inplace_cases);
+    if (g_inplace_cases != 20) s++;  // es 2: 7 shapes, es 4: 7, es 8: 6
     double gr0 = 0, gr1 = 0, orr = 0;
     int l0 = test_lz4(rng, 0, gr0, orr);
     int l1 = test_lz4(rng, 1, gr1, orr);
