@@ -14,6 +14,12 @@ region) in GB/s.  Ranks are independent replicas on their own cubes (weak
 scaling; no collective on the data path).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl bsgpu|reference]
+
+``--workload batch`` measures the batched engine instead: 4096 chunks of
+log-uniform sizes in [64 KiB, 64 MiB] (about 40 GB), element sizes 2, 4 or 8
+bytes at random, half rounded visibility cubes (16 inputs x 64 time
+samples, N = 2^16, f = 0.01) and half random walks, compressed and
+decompressed by one persistent launch each, replayed from a CUDA graph.
 """
 from __future__ import annotations
 
@@ -52,6 +58,9 @@ def parse():
     p.add_argument("--freqs", type=int, default=1024,
                    help="frequencies of the cube (1024 = the full workload; fewer only for "
                         "profiling runs)")
+    p.add_argument("--workload", default="chime", choices=["chime", "batch"])
+    p.add_argument("--chunks", type=int, default=4096,
+                   help="batch workload: number of chunks (4096 = the full workload)")
     return p.parse_args()
 
 
@@ -196,6 +205,209 @@ def recorded_traffic(scale_units):
     return per_unit * scale_units
 
 
+# -- the batched-engine workload ------------------------------------------------
+
+BATCH_WORKLOAD = ("batch of 4096 chunks, log-uniform 64 KiB..64 MiB (~40 GB), elem 2/4/8 B, "
+                  "half rounded visibilities (16 inputs x 64 time), half random walks")
+BATCH_BLOCK_BYTES = 8192
+
+
+def batch_specs(n_chunks, seed):
+    """(bytes, elem size, kind) per chunk; sizes log-uniform on [64 KiB, 64 MiB]."""
+    rng = np.random.default_rng([seed, 4])
+    sizes = np.exp(rng.uniform(np.log(64 << 10), np.log(64 << 20), n_chunks)).astype(np.int64)
+    es = rng.choice([2, 4, 8], n_chunks)
+    kind = rng.random(n_chunks) < 0.5
+    return [(int(b) // int(e) * int(e), int(e), "vis" if k else "walk")
+            for b, e, k in zip(sizes, es, kind)]
+
+
+def batch_inputs(specs, seed, device="cuda"):
+    """Device buffers of the chunks: rounded visibility cubes (16 inputs x 64
+    time, as many frequencies as the size needs, cut to size) or random walks."""
+    import torch
+    from paper_1503_00638_gb300 import bsgpu, synth
+    xs = []
+    per_freq = synth.n_products(16) * 64 * 8
+    for k, (nb, es, kind) in enumerate(specs):
+        if kind == "vis":
+            F = -(-nb // per_freq)
+            cfg = synth.VisConfig(F, 16, 64, 2 ** 16, 0.01, seed=seed * 100003 + k)
+            cube = synth.visibilities_torch(cfg, device)
+            r = bsgpu.reduce_precision_c64(cube, cfg.n_samp, cfg.f)
+            x = r.view(torch.uint8).reshape(-1)[:nb].clone()
+            del cube, r
+        else:
+            x = synth.random_walk_torch(nb // es, es, seed=seed * 100003 + k, device=device)
+        xs.append(x)
+    return xs
+
+
+def oracle_batch_sample(xs, specs, seconds=15.0):
+    """The oracle compressing and decompressing whole chunks, in order, until
+    about `seconds` have passed; returns (bytes, seconds, chunks)."""
+    import oracle
+    done, t_used, n = 0, 0.0, 0
+    for x, (nb, es, _) in zip(xs, specs):
+        a = x.cpu().numpy().view({2: np.uint16, 4: np.uint32, 8: np.uint64}[es])
+        t0 = time.perf_counter()
+        s = oracle.compress(a, BATCH_BLOCK_BYTES // es)
+        rc, back = oracle.decompress(s, a.size, a.dtype, BATCH_BLOCK_BYTES // es)
+        t_used += time.perf_counter() - t0
+        if rc != 0 or not np.array_equal(back, a):
+            raise RuntimeError("oracle round trip failed")
+        done += nb
+        n += 1
+        if t_used > seconds:
+            break
+    return done, t_used, n
+
+
+def run_batch(args, rank, world, local, barrier, gpu_index):
+    import torch
+    import torch.distributed as dist
+    from paper_1503_00638_gb300 import bsgpu, engine
+
+    specs = batch_specs(args.chunks, rank)
+    xs = batch_inputs(specs, rank)
+    es_l = [es for _, es, _ in specs]
+    bl = [BATCH_BLOCK_BYTES // es for es in es_l]
+    nbytes = sum(nb for nb, _, _ in specs)
+    eng = engine.BatchCodec(xs, es_l, bl, level=LEVEL)
+    tune_c, tune_d = eng.autotune(candidates=(0, 8, 12, 16), reps=2)
+    sc, sd = eng.statuses()
+    if any(sc) or any(sd):
+        raise RuntimeError("batch status after tuning")
+    # correctness of what is timed: sampled chunks round-trip exactly
+    for i in range(0, eng.n, max(1, eng.n // 64)):
+        if not torch.equal(eng.output(i), xs[i]):
+            raise RuntimeError(f"batch round trip failed on chunk {i}")
+    slen = eng.compressed_bytes()
+    graph = eng.capture()
+    stream = torch.cuda.current_stream()
+
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(args.warmup):
+        graph.replay()
+    t_soak0 = time.time()
+    torch.cuda.synchronize()
+    # split timing of the two launches (eager, events on the launching stream)
+    c_ms, d_ms = [], []
+    for _ in range(3):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        eng.compress(stream)
+        e1.record(stream)
+        eng.decompress(stream)
+        e2.record(stream)
+        e2.synchronize()
+        c_ms.append(e0.elapsed_time(e1))
+        d_ms.append(e1.elapsed_time(e2))
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall1 = time.time()
+    ms = start.elapsed_time(end)
+    sc, sd = eng.statuses()
+    if any(sc) or any(sd):
+        raise RuntimeError("batch status after timed steps")
+    clk = clocks.summary(t_soak0, t_wall1)
+    clocks.stop()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = nbytes * world * args.steps / (ms_max / 1e3) / 1e9
+
+    # end to end through the engine with host buffers, on the leading chunks
+    # up to 4 GB (pinned host copies of the whole 40 GB are not kept)
+    sub, acc = 0, 0
+    while sub < eng.n and acc + specs[sub][0] <= (4 << 30):
+        acc += specs[sub][0]
+        sub += 1
+    sub = max(sub, 1)
+    xs_sub = xs[:sub]
+    e_sub = engine.BatchCodec(xs_sub, es_l[:sub], bl[:sub], level=LEVEL)
+    e_sub.ctas_c, e_sub.ctas_d = eng.ctas_c, eng.ctas_d
+    host_in = [x.cpu().pin_memory() for x in xs_sub]
+    e_sub.compress()
+    torch.cuda.synchronize()
+    host_stream = torch.empty(e_sub.stream_arena.numel(), dtype=torch.uint8).pin_memory()
+    host_out = torch.empty(e_sub.dec_arena.numel(), dtype=torch.uint8).pin_memory()
+    e2e_t = []
+    sub_bytes = sum(specs[i][0] for i in range(sub))
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for x, h in zip(xs_sub, host_in):
+            x.copy_(h, non_blocking=True)
+        e_sub.compress()
+        lens = e_sub.out_bytes.cpu()            # the stream lengths (8 bytes per chunk)
+        end_b = e_sub.stream_off[-1] + int(lens[-1])
+        host_stream[:end_b].copy_(e_sub.stream_arena[:end_b], non_blocking=True)
+        e_sub.stream_arena[:end_b].copy_(host_stream[:end_b], non_blocking=True)
+        e_sub.decompress()
+        host_out.copy_(e_sub.dec_arena, non_blocking=True)
+        torch.cuda.synchronize()
+        if k:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_value = sub_bytes / statistics.median(e2e_t) / 1e9
+    ok_e2e = all(torch.equal(host_out[o:o + specs[i][0]], host_in[i])
+                 for i, o in enumerate(e_sub.dec_off) if i % 7 == 0)
+
+    hbm, peak_kind = peaks()
+    cm, dm = statistics.median(c_ms), statistics.median(d_ms)
+    alg_c = nbytes + slen + 8 * eng.n_items + 8 * eng.n
+    alg_d = slen + 8 * eng.n_items + nbytes
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD if args.chunks == 4096
+                   else f"{BATCH_WORKLOAD} (first {args.chunks} chunks)",
+                   "chunks": eng.n, "items": eng.n_items, "bytes": nbytes,
+                   "block_bytes": BATCH_BLOCK_BYTES, "level": LEVEL,
+                   "ctas_per_sm": {"compress": eng.ctas_c, "decompress": eng.ctas_d},
+                   "tuning_ms": {"compress": tune_c.table, "decompress": tune_d.table},
+                   "l2": f"inputs ({nbytes / 1e9:.1f} GB) larger than L2; no flush",
+                   "step": "compress + decompress batch, one CUDA-graph replay",
+                   "parallelism": f"replicas x{world}"},
+        "compress_gbs": nbytes / (cm / 1e3) / 1e9,
+        "decompress_gbs": nbytes / (dm / 1e3) / 1e9,
+        "ratio": slen / nbytes,
+        "roofline": {"bound": "hbm", "kernel": "compress_batch_kernel",
+                     "achieved": alg_c / (cm / 1e3) / 1e9, "peak": hbm, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": alg_c / (cm / 1e3) / 1e9 / hbm, "traffic": None,
+                     "algorithmic_bytes": alg_c},
+        "decompress_roofline": {"bound": "hbm", "kernel": "decompress_batch_kernel",
+                                "achieved": alg_d / (dm / 1e3) / 1e9, "peak": hbm,
+                                "unit": "GB/s", "frac": alg_d / (dm / 1e3) / 1e9 / hbm},
+        "e2e": {"value": e2e_value, "unit": "GB/s",
+                "h2d_bytes_per_step": sub_bytes + end_b, "d2h_bytes_per_step": end_b + 8 * sub
+                + e_sub.dec_arena.numel(), "chunks": sub, "round_trip_ok": ok_e2e},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "wall_s_timed": t_wall1 - t_wall0,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nb_cpu, dt, n_cpu = oracle_batch_sample(xs, specs)
+        line["cpu_baseline"] = {"value": nb_cpu / dt / 1e9, "unit": "GB/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"first {n_cpu} chunks ({nb_cpu / 1e6:.1f} MB): "
+                                          "compress+decompress"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # -- the GPU arm ----------------------------------------------------------------
 
 def main():
@@ -220,6 +432,19 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    gpu_index = local
+    vis_dev_env = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis_dev_env:
+        try:
+            gpu_index = int(vis_dev_env.split(",")[local])
+        except ValueError:
+            gpu_index = local
+    if args.workload == "batch":
+        run_batch(args, rank, world, local, barrier, gpu_index)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     cfg = synth.VisConfig(1024, 128, 16, 2 ** 17, args.f, seed=rank, drift=True)
     F, n_in, T = args.freqs, cfg.n_inputs, cfg.n_time
@@ -266,13 +491,6 @@ def main():
     if bsgpu.status(ws_c) != 0:
         raise RuntimeError("compress status")
 
-    gpu_index = local
-    vis_dev_env = os.environ.get("CUDA_VISIBLE_DEVICES")
-    if vis_dev_env:
-        try:
-            gpu_index = int(vis_dev_env.split(",")[local])
-        except ValueError:
-            gpu_index = local
     clocks = ClockSampler(gpu_index)
     clocks.start()
     time.sleep(0.3)

@@ -136,3 +136,53 @@ def random_walk(n: int, dtype, seed: int = 0) -> np.ndarray:
             walk = walk & ((1 << (8 * dtype.itemsize)) - 1)
         return walk.astype(np.dtype(f"u{dtype.itemsize}")).view(dtype)
     return np.cumsum(steps.astype(np.float64)).astype(dtype)
+
+
+# -- the same recipes built on the GPU, for workloads too large for the host --
+# (same distributions as visibilities() / random_walk(), not the same numbers:
+# torch's generator replaces numpy's)
+
+def visibilities_torch(cfg: VisConfig, device="cuda"):
+    """A complex64 [freq][prod][time] cube following the recipe of
+    visibilities(cfg), generated on `device` with torch's generator."""
+    import torch
+    F, n, T = cfg.n_freq, cfg.n_inputs, cfg.n_time
+    g = torch.Generator(device=device)
+    g.manual_seed(int(cfg.seed))
+    ii, jj = torch.triu_indices(n, n, device=device)
+    A = 50.0 + 100.0 * torch.rand((F, n), generator=g, device=device, dtype=torch.float64)
+    if cfg.drift:
+        ph = 2 * np.pi * torch.rand(n, generator=g, device=device, dtype=torch.float64)
+        fr = torch.arange(F, device=device, dtype=torch.float64)[:, None]
+        A = A[:1] * (1.0 + 0.2 * torch.sin(2 * np.pi * 3.0 * fr / F + ph[None, :]))
+    phi = 2 * np.pi * torch.rand(ii.numel(), generator=g, device=device, dtype=torch.float64)
+    t = torch.arange(T, device=device, dtype=torch.float64)
+    z = torch.randn((F, ii.numel(), T, 2), generator=g, device=device, dtype=torch.float64)
+    Ai, Aj = A[:, ii][..., None], A[:, jj][..., None]
+    auto_re = Ai * (1.0 + z[..., 0] / np.sqrt(cfg.n_samp))
+    amp = torch.sqrt(Ai * Aj)
+    ang = 2 * np.pi * t * (jj - ii).to(torch.float64)[:, None] / (n * cfg.t_sky) + phi[:, None]
+    sig = amp / np.sqrt(2.0 * cfg.n_samp)
+    cross = (ii != jj)[:, None]
+    re = torch.where(cross, cfg.rho * amp * torch.cos(ang) + sig * z[..., 0], auto_re)
+    im = torch.where(cross, cfg.rho * amp * torch.sin(ang) + sig * z[..., 1],
+                     torch.zeros((), device=device, dtype=torch.float64))
+    return torch.complex(re.float(), im.float())
+
+
+def random_walk_torch(n: int, elem_size: int, seed: int = 0, device="cuda"):
+    """The random walk of random_walk() as the bytes of n integers of
+    elem_size bytes (wrapping), generated on `device`."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    k = torch.randint(0, 7, (n,), generator=g, device=device)
+    s = torch.randint(0, 2, (n,), generator=g, device=device) * 2 - 1
+    w = torch.cumsum(s << k, 0)
+    if elem_size == 1:
+        return (w & 0xff).to(torch.uint8)
+    if elem_size == 2:
+        return (w & 0xffff).to(torch.int32).to(torch.int16).view(torch.uint8)
+    if elem_size == 4:
+        return w.to(torch.int32).view(torch.uint8)
+    return w.view(torch.uint8)

@@ -1,5 +1,6 @@
 """The synthetic visibilities carry the thermal scatter of Sec. 3.1 (S2)."""
 import numpy as np
+import pytest
 
 from paper_1503_00638_gb300 import synth
 
@@ -55,3 +56,26 @@ def test_visibilities_int_is_the_scaled_cube():
     assert np.array_equal(a[..., 1], np.rint(v.imag.astype(np.float64) * 1000.0))
     big = synth.visibilities_int(cfg, 1e9)  # autos ~100 * 1e9: clipped to int32
     assert big.max() == np.iinfo(np.int32).max
+
+
+def test_torch_generators_follow_the_recipe():
+    torch = pytest.importorskip("torch")
+    # rho = 0: crosses are pure thermal scatter of variance A_i A_j / (2N)
+    cfg = synth.VisConfig(4, 6, 4096, 2 ** 10, 0.1, seed=3, rho=0.0)
+    v = synth.visibilities_torch(cfg, device="cpu").numpy()
+    n = cfg.n_inputs
+    ii, jj = np.triu_indices(n)
+    A = v[:, [synth.auto_product_index(i, n) for i in range(n)], :].real.mean(axis=2)
+    for p in range(ii.size):
+        i, j = ii[p], jj[p]
+        if i == j:
+            assert np.all(v[:, p].imag == 0)
+            rel = v[:, p].real / A[:, i][:, None] - 1.0
+            assert abs(rel.var() * cfg.n_samp - 1.0) < 0.1       # Var = A^2 / N
+        else:
+            want = A[:, i] * A[:, j] / (2 * cfg.n_samp)
+            got = (v[:, p].real ** 2).mean(axis=1)
+            assert np.all(np.abs(got / want - 1.0) < 0.1)
+    w = synth.random_walk_torch(10000, 4, seed=1, device="cpu").view(torch.int32).numpy()
+    d = np.diff(w.astype(np.int64))
+    assert set(np.abs(d).tolist()) <= {1, 2, 4, 8, 16, 32, 64}
