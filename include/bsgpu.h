@@ -253,7 +253,11 @@ int bsgpu_compress_noalloc(const void *in, size_t n_elem, size_t elem_size, size
  *   decompress: in = the chunk's stream of in_bytes bytes (or see
  *               d_in_bytes); out = n_elem * elem_size bytes; out_cap ignored.
  *   block_elems: a multiple of 8 with block_elems * elem_size <= 8192, or 0
- *               for the 4096-byte default. */
+ *               for the 4096-byte default.
+ *   block_offsets: NULL, or the chunk's own block index (bsgpu_num_blocks()
+ *               device uint64s, 8-byte aligned): written by a compress batch,
+ *               read by a decompress batch, in place of the batch-wide index
+ *               argument (a stream kept with its index needs no chain walk). */
 typedef struct bsgpu_chunk {
     const void *in;
     void *out;
@@ -262,6 +266,7 @@ typedef struct bsgpu_chunk {
     uint64_t out_cap;
     uint32_t elem_size;
     uint32_t block_elems;
+    uint64_t *block_offsets;
 } bsgpu_chunk;
 
 /* Bytes of the table image for n_chunks chunks (0 for none). */
@@ -309,6 +314,33 @@ int bsgpu_decompress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_it
                            const uint64_t *d_in_bytes, const uint64_t *d_block_offsets,
                            int *d_chunk_status, void *ws, size_t ws_bytes, uint32_t ctas_per_sm,
                            void *stream);
+
+/* ------------------------------------------------------------------------
+ * Offset allocator for a fixed device arena (host only; the paper has no
+ * counterpart: it serves the admission control of a server that keeps one
+ * device allocation of a fixed capacity and gives byte ranges of it to the
+ * requests it admits).  Best fit, neighbouring free ranges merged on free,
+ * every range a multiple of `align` long and aligned to it.  Thread-safe.
+ * Nothing here touches device memory.
+ * ------------------------------------------------------------------------ */
+
+/* A new arena of capacity bytes (rounded down to a multiple of align, a power
+ * of two); NULL for bad arguments or no host memory. */
+void *bsgpu_arena_create(uint64_t capacity, uint64_t align);
+void bsgpu_arena_destroy(void *arena);
+
+/* Reserve `bytes` (rounded up to align; 0 counts as 1): *offset receives the
+ * range's start.  BSGPU_ERR_SPACE when no free range is large enough (the
+ * arena is unchanged), BSGPU_ERR_ARG for a null argument. */
+int bsgpu_arena_alloc(void *arena, uint64_t bytes, uint64_t *offset);
+
+/* Release the range starting at offset; BSGPU_ERR_ARG if none starts there. */
+int bsgpu_arena_free(void *arena, uint64_t offset);
+
+/* Bytes reserved now, the largest free range, the most bytes ever reserved
+ * at once, and the number of free ranges (any pointer may be NULL). */
+int bsgpu_arena_stats(const void *arena, uint64_t *used_bytes, uint64_t *largest_free,
+                      uint64_t *high_water, uint64_t *n_free_ranges);
 
 #ifdef __cplusplus
 }

@@ -55,6 +55,11 @@ _SIGS = {
                               ctypes.c_uint32, _vp], _i),
     "bsgpu_decompress_batch": ([_vp, ctypes.c_uint32, ctypes.c_uint64, _vp, _vp, _vp, _vp, _sz,
                                 ctypes.c_uint32, _vp], _i),
+    "bsgpu_arena_create": ([ctypes.c_uint64, ctypes.c_uint64], _vp),
+    "bsgpu_arena_destroy": ([_vp], None),
+    "bsgpu_arena_alloc": ([_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)], _i),
+    "bsgpu_arena_free": ([_vp, ctypes.c_uint64], _i),
+    "bsgpu_arena_stats": ([_vp] + [ctypes.POINTER(ctypes.c_uint64)] * 4, _i),
 }
 
 
@@ -63,7 +68,7 @@ class Chunk(ctypes.Structure):
     _fields_ = [("in_ptr", ctypes.c_void_p), ("out_ptr", ctypes.c_void_p),
                 ("n_elem", ctypes.c_uint64), ("in_bytes", ctypes.c_uint64),
                 ("out_cap", ctypes.c_uint64), ("elem_size", ctypes.c_uint32),
-                ("block_elems", ctypes.c_uint32)]
+                ("block_elems", ctypes.c_uint32), ("block_offsets", ctypes.c_void_p)]
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
@@ -371,3 +376,38 @@ def decompress_batch(d_table: torch.Tensor, n_chunks: int, n_items: int,
     _check(_lib.bsgpu_decompress_batch(_ptr(d_table), n_chunks, n_items, _ptr(in_bytes),
                                        _ptr(offsets), _ptr(status), _ptr(ws), ws.numel(),
                                        ctas_per_sm, _stream(stream)), "bsgpu_decompress_batch")
+
+
+class Arena:
+    """Offsets of a fixed-capacity device arena (bsgpu_arena_*): host-side
+    bookkeeping only; the caller owns the device allocation."""
+
+    def __init__(self, capacity: int, align: int = 256):
+        self._h = _lib.bsgpu_arena_create(capacity, align)
+        if not self._h:
+            raise BsgpuError(ERR_ARG, "bsgpu_arena_create")
+        self.capacity, self.align = capacity // align * align, align
+
+    def alloc(self, nbytes: int):
+        """Offset of a new range, or None when nothing large enough is free."""
+        off = ctypes.c_uint64(0)
+        rc = _lib.bsgpu_arena_alloc(self._h, nbytes, ctypes.byref(off))
+        if rc == ERR_SPACE:
+            return None
+        _check(rc, "bsgpu_arena_alloc")
+        return off.value
+
+    def free(self, offset: int) -> None:
+        _check(_lib.bsgpu_arena_free(self._h, offset), "bsgpu_arena_free")
+
+    def stats(self) -> dict:
+        v = [ctypes.c_uint64(0) for _ in range(4)]
+        _check(_lib.bsgpu_arena_stats(self._h, *[ctypes.byref(x) for x in v]), "bsgpu_arena_stats")
+        return dict(zip(("used", "largest_free", "high_water", "free_ranges"),
+                        (x.value for x in v)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.bsgpu_arena_destroy(h)
+            self._h = None

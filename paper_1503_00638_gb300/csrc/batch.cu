@@ -28,7 +28,8 @@ struct BatchChunk {
     uint64_t out_cap;    // compress: capacity of out
     uint64_t item0;      // first item of the chunk
     uint32_t es, B, nb, last_B;
-    uint32_t tail, pad0, pad1, pad2;
+    uint32_t tail, pad0;
+    uint64_t *offs;      // the chunk's own block index, or null (batch-wide array)
 };
 static_assert(sizeof(BatchChunk) == 80, "table record layout");
 
@@ -69,7 +70,7 @@ BSG_D CodecArgs chunk_args(const BatchArgs &b, uint32_t c)
     a.in_bytes = b.in_bytes ? b.in_bytes[c] : ch.in_bytes;
     a.out_cap = ch.out_cap;
     a.out_bytes = b.out_bytes ? b.out_bytes + c : nullptr;
-    a.block_offsets = b.offsets ? b.offsets + ch.item0 : nullptr;
+    a.block_offsets = ch.offs ? ch.offs : (b.offsets ? b.offsets + ch.item0 : nullptr);
     a.tile_state = b.state ? b.state + ch.item0 : nullptr;
     a.status = b.status + c;
     a.n_elem = ch.n_elem;
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(32, 13) decompress_batch_kernel(const __grid_c
 __global__ void chain_walk_batch_kernel(const __grid_constant__ BatchArgs b)
 {
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= b.n_chunks) return;
+    if (c >= b.n_chunks || b.chunks[c].offs) return;  // a chunk with its own index
     const CodecArgs a = chunk_args(b, c);
     const uint64_t tail_b = (uint64_t)a.tail_elems * a.es;
     uint64_t D = 12;
@@ -481,7 +482,9 @@ int bsgpu_batch_plan(int op, const bsgpu_chunk *chunks, uint32_t n_chunks, void 
         if (B == 0 || B % 8 || B * es > 8192) return BSGPU_ERR_ARG;
         if ((!k.in && k.n_elem) || (!k.out && (op == BSGPU_OP_COMPRESS || k.n_elem)))
             return BSGPU_ERR_ARG;
-        if ((k.in && !aligned(k.in, 16)) || (k.out && !aligned(k.out, 16))) return BSGPU_ERR_ALIGN;
+        if ((k.in && !aligned(k.in, 16)) || (k.out && !aligned(k.out, 16)) ||
+            !aligned(k.block_offsets, 8))
+            return BSGPU_ERR_ALIGN;
         const uint64_t full = k.n_elem / B, rem = k.n_elem % B, last = rem - rem % 8;
         const uint64_t nb = full + (last ? 1 : 0);
         if (op == BSGPU_OP_COMPRESS &&
@@ -500,6 +503,7 @@ int bsgpu_batch_plan(int op, const bsgpu_chunk *chunks, uint32_t n_chunks, void 
         r.nb = (uint32_t)nb;
         r.last_B = (uint32_t)(last ? last : B);
         r.tail = (uint32_t)(rem % 8);
+        r.offs = k.block_offsets;
         std::memcpy(rec + c, &r, sizeof r);
         starts[c] = items;
         items += nb ? nb : 1;  // a chunk without blocks still takes one item

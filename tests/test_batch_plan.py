@@ -10,7 +10,8 @@ bs = pytest.importorskip("paper_1503_00638_gb300.bsgpu")
 
 REC = np.dtype([("in", "<u8"), ("out", "<u8"), ("n_elem", "<u8"), ("in_bytes", "<u8"),
                 ("out_cap", "<u8"), ("item0", "<u8"), ("es", "<u4"), ("B", "<u4"),
-                ("nb", "<u4"), ("last_B", "<u4"), ("tail", "<u4"), ("pad", "<u4", 3)])
+                ("nb", "<u4"), ("last_B", "<u4"), ("tail", "<u4"), ("pad", "<u4"),
+                ("offs", "<u8")])
 BASE = 1 << 40  # fake, 16-byte aligned device addresses
 
 
@@ -30,6 +31,7 @@ def test_table_layout_and_items():
     specs = [(0, 4, 0), (5, 8, 0), (8, 1, 8), (4099, 2, 0), (100000, 4, 2048), (1000, 8, 1024),
              (77, 1, 24)]
     ch = [chunk(n, es, B, k=i) for i, (n, es, B) in enumerate(specs)]
+    ch[3].block_offsets = BASE + (1 << 30)
     table, n_items, ws = bs.batch_plan(bs.OP_COMPRESS, ch)
     n = len(specs)
     assert bs.batch_table_bytes(n) == (80 * n + 8 * (n + 1) + 15) // 16 * 16
@@ -42,6 +44,7 @@ def test_table_layout_and_items():
         assert (r["n_elem"], r["es"], r["B"], r["nb"], r["last_B"], r["tail"]) == \
             (nel, es, Bf, nb, last_B, tail)
         assert r["in"] == ch[i].in_ptr and r["out"] == ch[i].out_ptr
+        assert r["offs"] == (ch[i].block_offsets or 0)
         assert r["item0"] == item == starts[i]
         item += max(nb, 1)
     assert starts[n] == item == n_items
@@ -79,6 +82,9 @@ def test_plan_argument_errors():
     bad = chunk(1000, 4)
     bad.in_ptr = BASE + 8
     assert _plan_rc(bs.OP_COMPRESS, [bad]) == bs.ERR_ALIGN
+    mis = chunk(1000, 4)
+    mis.block_offsets = BASE + 4
+    assert _plan_rc(bs.OP_COMPRESS, [mis]) == bs.ERR_ALIGN                     # index alignment
     nul = chunk(1000, 4)
     nul.out_ptr = None
     assert _plan_rc(bs.OP_COMPRESS, [nul]) == bs.ERR_ARG

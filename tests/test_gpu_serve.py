@@ -1,0 +1,129 @@
+"""GPU tests of the serving layer: continuous batching and the one-at-a-time
+pipeline return, for every request, the same bytes as the request processed
+alone (compressed stream and block index, or the decompressed elements);
+admission never reserves more than the cap; timestamps are ordered."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1503_00638_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DT = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_00638_gb300 import build
+    build.build()
+    from paper_1503_00638_gb300 import bsgpu, serve
+    return bsgpu, serve
+
+
+def make_requests(bs, serve, n=60, seed=0, rate=2000.0):
+    rng = np.random.default_rng(seed)
+    vis = synth.visibilities(synth.CONFIG_SMALL).view(np.uint8).reshape(-1)
+    reqs, originals = [], {}
+    t = 0.0
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        es = int(rng.choice([2, 4, 8]))
+        nbytes = int(np.exp(rng.uniform(np.log(16 << 10), np.log(6 << 20)))) // es * es
+        if i % 9 == 0:
+            nbytes = int(rng.integers(0, 8)) * es          # tiny: no blocks
+        if rng.random() < 0.5:
+            a = np.resize(vis, nbytes).copy()
+        else:
+            a = synth.random_walk(nbytes // es, DT[es], seed=i).view(np.uint8)
+        x = torch.from_numpy(a.copy()).cuda()
+        B = int(rng.choice([0, 8192 // es, 2048 // es]))
+        originals[i] = x
+        if rng.random() < 0.7:
+            reqs.append(serve.Request(i, "compress", t, x, nbytes // es, es, B))
+        else:
+            c = bs.compress(x, B, elem_size=es)
+            stream = c.buf[:c.nbytes].clone()
+            idx = c.offsets.clone() if i % 2 else None       # half carry their index
+            reqs.append(serve.Request(i, "decompress", t, stream, nbytes // es, es, B, index=idx))
+    torch.cuda.synchronize()
+    return reqs, originals
+
+
+def check(bs, reqs, results, originals):
+    for r in reqs:
+        assert r.status == 0, r.rid
+        assert r.arrival <= r.admitted <= r.done
+        out, idx = results[r.rid]
+        x = originals[r.rid]
+        if r.kind == "compress":
+            single = bs.compress(x, r.block_elems, elem_size=r.elem_size)
+            assert single.nbytes == out.numel(), r.rid
+            assert torch.equal(single.buf[:single.nbytes].cpu(), out), r.rid
+            nb = bs.num_blocks(r.n_elem, r.elem_size, r.block_elems)
+            if nb:
+                assert torch.equal(single.offsets[:nb].cpu(), idx), r.rid
+        else:
+            assert torch.equal(out, x.cpu()), r.rid
+
+
+def collector(results):
+    def on_done(server, r):
+        out = server.output(r).cpu()
+        idx = server.output_index(r).cpu() if r.kind == "compress" else None
+        results[r.rid] = (out, idx)
+    return on_done
+
+
+@pytest.mark.parametrize("cap_mb,depth", [(64, 2), (1024, 1), (1024, 3)])
+def test_batching_server_matches_alone(mods, cap_mb, depth):
+    bs, serve = mods
+    reqs, originals = make_requests(bs, serve, seed=cap_mb + depth)
+    results = {}
+    srv = serve.BatchingServer(cap_bytes=cap_mb << 20, depth=depth, max_chunks=32,
+                               on_done=collector(results))
+    srv.run(reqs)
+    check(bs, reqs, results, originals)
+    st = srv.arena.stats()
+    assert st["used"] == 0 and st["high_water"] <= srv.cap
+    assert len(srv.batches) >= 1
+    if cap_mb == 64:
+        # the small cap forced requests to wait for earlier ones to finish
+        assert len(srv.batches) > 2
+    s = serve.latency_summary(reqs)
+    assert s["n"] == len(reqs) and s["p50_ms"] <= s["p99_ms"]
+
+
+def test_serial_server_matches_alone(mods):
+    bs, serve = mods
+    reqs, originals = make_requests(bs, serve, n=30, seed=5)
+    results = {}
+    srv = serve.SerialServer(cap_bytes=256 << 20, on_done=collector(results))
+    srv.run(reqs)
+    check(bs, reqs, results, originals)
+    assert srv.arena.stats()["used"] == 0
+
+
+def test_same_bytes_alone_and_in_the_mix(mods):
+    bs, serve = mods
+    reqs, originals = make_requests(bs, serve, n=40, seed=9, rate=1e6)   # all at once
+    mixed = {}
+    serve.BatchingServer(cap_bytes=2 << 30, on_done=collector(mixed)).run(reqs)
+    for r in reqs:
+        alone = {}
+        solo = serve.Request(r.rid, r.kind, 0.0, r.data, r.n_elem, r.elem_size, r.block_elems,
+                             index=r.index)
+        serve.BatchingServer(cap_bytes=64 << 20, depth=1, on_done=collector(alone)).run([solo])
+        assert torch.equal(alone[r.rid][0], mixed[r.rid][0]), r.rid
+        if r.kind == "compress" and alone[r.rid][1] is not None:
+            assert torch.equal(alone[r.rid][1], mixed[r.rid][1]), r.rid
+
+
+def test_request_larger_than_cap_is_refused(mods):
+    bs, serve = mods
+    x = torch.zeros(4 << 20, dtype=torch.uint8, device="cuda")
+    r = serve.Request(0, "compress", 0.0, x, x.numel() // 4, 4, 0)
+    with pytest.raises(ValueError):
+        serve.BatchingServer(cap_bytes=1 << 20).run([r])
