@@ -15,6 +15,12 @@ scaling; no collective on the data path).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl bsgpu|reference]
 
+``--workload serve`` measures serving: Poisson arrivals, 70 % compress and
+30 % decompress requests of rounded visibility data with sizes log-uniform in
+[16 KiB, 256 MiB], admission capped at 40 GB of device memory; p50/p99
+latency and GB/s of the continuous-batching server against the
+one-at-a-time pipeline, with the arrival rate swept up to saturation.
+
 ``--workload batch`` measures the batched engine instead: 4096 chunks of
 log-uniform sizes in [64 KiB, 64 MiB] (about 40 GB), element sizes 2, 4 or 8
 bytes at random, half rounded visibility cubes (16 inputs x 64 time
@@ -58,7 +64,9 @@ def parse():
     p.add_argument("--freqs", type=int, default=1024,
                    help="frequencies of the cube (1024 = the full workload; fewer only for "
                         "profiling runs)")
-    p.add_argument("--workload", default="chime", choices=["chime", "batch"])
+    p.add_argument("--workload", default="chime", choices=["chime", "batch", "serve"])
+    p.add_argument("--requests", type=int, default=3000,
+                   help="serve workload: requests per arrival-rate point")
     p.add_argument("--chunks", type=int, default=4096,
                    help="batch workload: number of chunks (4096 = the full workload)")
     return p.parse_args()
@@ -408,6 +416,110 @@ def run_batch(args, rank, world, local, barrier, gpu_index):
         print(json.dumps(line), flush=True)
 
 
+# -- the serving workload --------------------------------------------------------
+
+SERVE_WORKLOAD = ("serving: Poisson arrivals, 70% compress / 30% decompress, rounded "
+                  "visibilities (16 inputs x 64 time), sizes log-uniform 16 KiB..256 MiB, "
+                  "admission cap 40 GB")
+
+
+def serve_pool(n_payloads, seed):
+    """Distinct request payloads (rounded visibility bytes, 4-byte elements)
+    with their compressed streams and block indexes."""
+    import torch
+    from paper_1503_00638_gb300 import bsgpu
+    rng = np.random.default_rng([seed, 5])
+    sizes = np.exp(rng.uniform(np.log(16 << 10), np.log(256 << 20), n_payloads)).astype(np.int64)
+    specs = [(int(b) // 4 * 4, 4, "vis") for b in sizes]
+    xs = batch_inputs(specs, seed + 17)
+    comp = []
+    for x in xs:
+        c = bsgpu.compress(x, BATCH_BLOCK_BYTES // 4, elem_size=4)
+        comp.append((c.buf[:c.nbytes].clone(), c.offsets.clone()))
+        del c
+    torch.cuda.synchronize()
+    return xs, comp
+
+
+def serve_requests(xs, comp, n, rate, seed):
+    from paper_1503_00638_gb300 import serve
+    rng = np.random.default_rng([seed, 6])
+    t = 0.0
+    reqs = []
+    for i in range(n):
+        if rate:
+            t += rng.exponential(1.0 / rate)
+        k = int(rng.integers(len(xs)))
+        x = xs[k]
+        if rng.random() < 0.7:
+            reqs.append(serve.Request(i, "compress", t, x, x.numel() // 4, 4,
+                                      BATCH_BLOCK_BYTES // 4))
+        else:
+            st, idx = comp[k]
+            reqs.append(serve.Request(i, "decompress", t, st, x.numel() // 4, 4,
+                                      BATCH_BLOCK_BYTES // 4, index=idx))
+    return reqs
+
+
+def run_serve(args, rank, world, gpu_index):
+    import torch
+    from paper_1503_00638_gb300 import serve
+    xs, comp = serve_pool(256, rank)
+    mean_bytes = statistics.mean(x.numel() for x in xs)   # payloads are drawn uniformly
+    cap = 40 << 30
+    bsrv = serve.BatchingServer(cap_bytes=cap, depth=2)
+    ssrv = serve.SerialServer(cap_bytes=cap)
+    for srv in (bsrv, ssrv):          # warm-up (kernel attributes, workspaces)
+        srv.run(serve_requests(xs, comp, 64, 0.0, 99))
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+    t_0 = time.time()
+    # saturation: every request present at t = 0
+    sat_b = serve.latency_summary(bsrv.run(serve_requests(xs, comp, args.requests, 0.0, 1)))
+    sat_s = serve.latency_summary(ssrv.run(serve_requests(xs, comp, args.requests // 4, 0.0, 1)))
+    lam_sat = sat_b["gbs"] * 1e9 / mean_bytes
+    sweep = []
+    for frac in (0.1, 0.3, 0.5, 0.7, 0.9):
+        lam = frac * lam_sat
+        point = {"rate_per_s": lam, "offered_gbs": lam * mean_bytes / 1e9, "frac_of_sat": frac}
+        rb = bsrv.run(serve_requests(xs, comp, args.requests, lam, 2))
+        point["batching"] = serve.latency_summary(rb)
+        point["batching"]["batches"] = len(bsrv.batches)
+        bsrv.batches.clear()
+        # the one-at-a-time server falls behind early: fewer requests per point
+        nser = max(200, args.requests // 4)
+        rs = ssrv.run(serve_requests(xs, comp, nser, lam, 2))
+        point["serial"] = serve.latency_summary(rs)
+        for r in rb + rs:
+            if r.status != 0:
+                raise RuntimeError(f"request {r.rid} status {r.status}")
+        sweep.append(point)
+    t_1 = time.time()
+    clk = clocks.summary(t_0, t_1)
+    clocks.stop()
+    half = [p for p in sweep if p["frac_of_sat"] == 0.5][0]
+    line = {
+        "metric": METRIC, "value": sat_b["gbs"], "unit": "GB/s", "n_gpus": world,
+        "steps": args.requests, "warmup": 64, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD, "payloads": len(xs), "requests": args.requests,
+                   "mean_request_bytes": mean_bytes, "block_bytes": BATCH_BLOCK_BYTES,
+                   "admission_cap_bytes": cap, "batch_depth": 2,
+                   "value": "batching server GB/s with every request present at t = 0",
+                   "parallelism": f"replicas x{world}"},
+        "serving": {"saturation": {"batching": sat_b, "serial": sat_s},
+                    "p50_ms_at_half_saturation": {"batching": half["batching"]["p50_ms"],
+                                                  "serial": half["serial"]["p50_ms"]},
+                    "p99_ms_at_half_saturation": {"batching": half["batching"]["p99_ms"],
+                                                  "serial": half["serial"]["p99_ms"]},
+                    "sweep": sweep},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # -- the GPU arm ----------------------------------------------------------------
 
 def main():
@@ -440,6 +552,11 @@ def main():
             gpu_index = int(vis_dev_env.split(",")[local])
         except ValueError:
             gpu_index = local
+    if args.workload == "serve":
+        run_serve(args, rank, world, gpu_index)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     if args.workload == "batch":
         run_batch(args, rank, world, local, barrier, gpu_index)
         if world > 1:
