@@ -51,7 +51,8 @@ extern "C" {
 #define BSGPU_VIS_I32 1  /* interleaved int32 (re, im), as correlators emit   */
 
 /* Flags of the _ex entry points. */
-#define BSGPU_VIS_COMPENSATE 1  /* Sec. 3.2: per-sample compensated f, see below */
+#define BSGPU_VIS_COMPENSATE 1    /* Sec. 3.2: per-sample compensated f, see below   */
+#define BSGPU_VIS_TIME_SLOWEST 2  /* input in the instrument's order, see below     */
 
 /* Library version string. */
 const char *bsgpu_version(void);
@@ -132,10 +133,25 @@ int bsgpu_reduce_precision_c64(const void *in, void *out, int64_t n_freq, int64_
  *           a negative or undefined value counting as 0, and m = 1 with one
  *           input.  c is then fl32(6 (f m) / N) with f m, 6 (f m) and the
  *           quotient in fp64.
+ *           BSGPU_VIS_TIME_SLOWEST: `in` holds the cube in the order an
+ *           instrument writes it, [n_time][n_freq][n_prod] samples (time
+ *           slowest); the output is time-fastest as always.  Sec. 2 argues
+ *           for a post-acquisition reorder to time-fastest (the order of
+ *           reading, and the order in which neighbouring values correlate);
+ *           this flag fuses that reorder into the rounding (and, in
+ *           bsgpu_compress_vis_ex, into the compression).
  * ws: bsgpu_vis_workspace_size_ex(BSGPU_OP_REDUCE_PRECISION, ..., flags). */
 int bsgpu_reduce_precision_ex(const void *in, void *out, int dtype, int64_t n_freq,
                               int64_t n_inputs, int64_t n_time, double N, double f, int flags,
                               void *ws, size_t ws_bytes, void *stream);
+
+/* Sec. 2: the post-acquisition reorder on its own.  in holds n_time rows of
+ * n_series elements of elem_size (1, 2, 4 or 8) bytes (time slowest); out
+ * receives n_series rows of n_time elements (time fastest): out[s][t] =
+ * in[t][s].  A complex64 visibility cube is n_series = n_freq n_prod
+ * elements of 8 bytes.  Buffers aligned to elem_size, not overlapping. */
+int bsgpu_reorder_time(const void *in, void *out, uint64_t n_time, uint64_t n_series,
+                       size_t elem_size, void *stream);
 
 /* Sec. 4.2 and Sec. 6 step 4: Bitshuffle.  Within each block of block_elems
  * elements (a multiple of 8; 0 = 4096 bytes), bit r of element e (r = 8 *

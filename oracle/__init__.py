@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
             L.orc_compensation_min.restype = c_f
             L.orc_reduce_precision.argtypes = [c_vp, c_vp, c_i, c_l, c_l, c_l, c_d, c_d, c_i]
             L.orc_reduce_precision.restype = None
+            L.orc_reorder_time.argtypes = [c_vp, c_vp, c_sz, c_sz, c_sz]
+            L.orc_reorder_time.restype = None
             L.orc_bitshuffle.argtypes = [c_vp, c_vp, c_sz, c_sz, c_sz, c_i]
             L.orc_bitshuffle.restype = c_i
             L.orc_lz4_bound.argtypes = [c_sz]
@@ -199,6 +201,18 @@ def _n_inputs(P: int) -> int:
     if n * (n + 1) // 2 != P:
         raise ValueError(f"{P} products is not n(n+1)/2")
     return n
+
+
+# -- Sec. 2 ------------------------------------------------------------------
+
+def reorder_time(a: np.ndarray) -> np.ndarray:
+    """[T][...] (time slowest) -> [...][T] (time fastest) by plain loops."""
+    a = np.ascontiguousarray(a)
+    T = a.shape[0]
+    S = a.size // T if T else 0
+    out = np.empty(a.shape[1:] + (T,), dtype=a.dtype)
+    lib().orc_reorder_time(_ptr(a), _ptr(out), T, S, a.itemsize)
+    return out
 
 
 # -- Sec. 4.2 ---------------------------------------------------------------

@@ -296,6 +296,22 @@ void orc_granularity_map_c64(const float *in, int32_t *kout, long n_freq, long n
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 2: the post-acquisition reorder                                       */
+/* ------------------------------------------------------------------------ */
+
+/* An instrument writes one time sample after another (time slowest); the
+ * paper reorders after acquisition so that time varies fastest.  in holds
+ * n_time rows of n_series elements of es bytes; out[s][t] = in[t][s]. */
+void orc_reorder_time(const void *vin, void *vout, size_t n_time, size_t n_series, size_t es)
+{
+    const unsigned char *in = (const unsigned char *)vin;
+    unsigned char *out = (unsigned char *)vout;
+    for (size_t t = 0; t < n_time; t++)
+        for (size_t s = 0; s < n_series; s++)
+            memcpy(out + (s * n_time + t) * es, in + (t * n_series + s) * es, es);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 4.2: Bitshuffle, the blocked bit transpose                           */
 /* ------------------------------------------------------------------------ */
 

@@ -24,6 +24,7 @@ OK, ERR_ARG, ERR_SPACE, ERR_CORRUPT, ERR_CUDA, ERR_TIMEOUT, ERR_ALIGN = 0, -1, -
 OP_COMPRESS, OP_DECOMPRESS, OP_COMPRESS_VIS, OP_REDUCE_PRECISION = 1, 2, 3, 4
 VIS_F32, VIS_I32 = 0, 1
 VIS_COMPENSATE = 1
+VIS_TIME_SLOWEST = 2
 _NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_SPACE", -3: "ERR_CORRUPT", -4: "ERR_CUDA",
           -5: "ERR_TIMEOUT", -6: "ERR_ALIGN"}
 
@@ -45,6 +46,7 @@ _SIGS = {
     "bsgpu_decompress": ([_vp, _sz, _vp, _sz, _sz, _sz, _vp, _vp, _sz, _vp], _i),
     "bsgpu_compress_vis": ([_vp, _i64, _i64, _i64, _d, _d, _sz, _i, _vp, _sz, _vp, _vp, _vp,
                             _sz, _vp], _i),
+    "bsgpu_reorder_time": ([_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, _sz, _vp], _i),
     "bsgpu_compress_vis_ex": ([_vp, _i, _i64, _i64, _i64, _d, _d, _i, _sz, _sz, _i, _vp, _sz,
                                _vp, _vp, _vp, _sz, _vp], _i),
     "bsgpu_compress_noalloc": ([_vp, _sz, _sz, _sz, _i, _vp, _sz, _vp, _vp, _vp], _i),
@@ -166,31 +168,51 @@ def reduce_precision_c64(vis: torch.Tensor, N: float, f: float, out: torch.Tenso
     return out
 
 
-def _cube(vis: torch.Tensor):
+def _cube(vis: torch.Tensor, time_slowest: bool = False):
     """(n_freq, n_inputs, n_time, dtype code) of a complex64 [F][P][T] cube or
-    an int32 [F][P][T][2] cube of (re, im) pairs."""
+    an int32 [F][P][T][2] cube of (re, im) pairs ([T][F][P] / [T][F][P][2]
+    when time_slowest)."""
     if vis.dtype == torch.complex64 and vis.dim() == 3:
-        F, P, T = vis.shape
+        a, b, c = vis.shape
+        F, P, T = (b, c, a) if time_slowest else (a, b, c)
         return F, _n_inputs(P), T, VIS_F32
     if vis.dtype == torch.int32 and vis.dim() == 4 and vis.shape[3] == 2:
-        F, P, T, _ = vis.shape
+        a, b, c, _ = vis.shape
+        F, P, T = (b, c, a) if time_slowest else (a, b, c)
         return F, _n_inputs(P), T, VIS_I32
     raise ValueError("expected a complex64 [F][P][T] or int32 [F][P][T][2] cube")
 
 
 def reduce_precision(vis: torch.Tensor, N: float, f: float, compensate: bool = False,
                      out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
-                     stream=None) -> torch.Tensor:
+                     stream=None, time_slowest: bool = False) -> torch.Tensor:
     """Round a complex64 or int32 cube, optionally with Sec. 3.2's
-    compensated f (returns out)."""
-    F, n, T, dt = _cube(vis)
-    flags = VIS_COMPENSATE if compensate else 0
-    out = torch.empty_like(vis) if out is None else out
+    compensated f and from the time-slowest order (returns out, time
+    fastest)."""
+    F, n, T, dt = _cube(vis, time_slowest)
+    flags = (VIS_COMPENSATE if compensate else 0) | (VIS_TIME_SLOWEST if time_slowest else 0)
+    if out is None:
+        P = n * (n + 1) // 2
+        shape = (F, P, T) if vis.dim() == 3 else (F, P, T, 2)
+        out = torch.empty(shape, dtype=vis.dtype, device=vis.device)
     need = vis_workspace_size_ex(OP_REDUCE_PRECISION, F, n, T, 4, 0, flags)
     ws = new_workspace(need, vis.device) if ws is None else ws
     _check(_lib.bsgpu_reduce_precision_ex(_ptr(vis), _ptr(out), dt, F, n, T, float(N), float(f),
                                           flags, _ptr(ws), ws.numel(), _stream(stream)),
            "bsgpu_reduce_precision_ex")
+    return out
+
+
+def reorder_time(x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """[T][...] (time slowest) -> [...][T] (time fastest) for a contiguous
+    tensor whose first axis is time (elements of 1, 2, 4 or 8 bytes; complex64
+    counts as one 8-byte element)."""
+    T = x.shape[0]
+    S = x.numel() // T if T else 0
+    if out is None:
+        out = torch.empty(tuple(x.shape[1:]) + (T,), dtype=x.dtype, device=x.device)
+    _check(_lib.bsgpu_reorder_time(_ptr(x), _ptr(out), T, S, x.element_size(), _stream(stream)),
+           "bsgpu_reorder_time")
     return out
 
 
@@ -283,11 +305,12 @@ def compress_vis(vis: torch.Tensor, N: float, f: float, block_elems: int = 0,
 def compress_vis_ex(vis: torch.Tensor, N: float, f: float, compensate: bool = False,
                     elem_size: int = 4, block_elems: int = 0, out: torch.Tensor | None = None,
                     with_offsets: bool = True, ws: torch.Tensor | None = None, stream=None,
-                    level: int = 0) -> Compressed:
-    """Precision reduction (complex64 or int32 cube, optionally compensated)
-    + Bitshuffle + LZ4 with 4-byte components or 8-byte samples as elements."""
-    F, n_in, T, dt = _cube(vis)
-    flags = VIS_COMPENSATE if compensate else 0
+                    level: int = 0, time_slowest: bool = False) -> Compressed:
+    """Precision reduction (complex64 or int32 cube, optionally compensated,
+    optionally from the time-slowest order) + Bitshuffle + LZ4 with 4-byte
+    components or 8-byte samples as elements."""
+    F, n_in, T, dt = _cube(vis, time_slowest)
+    flags = (VIS_COMPENSATE if compensate else 0) | (VIS_TIME_SLOWEST if time_slowest else 0)
     n = F * (n_in * (n_in + 1) // 2) * T * 8 // elem_size
     cap = compress_bound(n, elem_size, block_elems)
     if cap == 0:

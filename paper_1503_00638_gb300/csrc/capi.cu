@@ -81,21 +81,23 @@ struct WsLayout {
 
 // Whether compress takes the fast kernel (full blocks of at most 8 KiB of 4-
 // or 8-byte elements; a cube of 4-byte components also needs n_time % 16 == 0).
-bool fast_shape(const Geometry &g, uint64_t n_time)
+bool fast_shape(const Geometry &g, uint64_t n_time, bool tslow = false)
 {
-    return shuffle_inplace_ok(g.es, g.B) && (n_time == 0 || g.es == 8 || n_time % 16 == 0);
+    // a time-slowest cube is gathered block by block: the general kernel
+    return !tslow && shuffle_inplace_ok(g.es, g.B) &&
+           (n_time == 0 || g.es == 8 || n_time % 16 == 0);
 }
 
 // n_ft: entries of the per-(freq, time) compensated-c table (0 = none)
 WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint64_t n_time = 0,
-                   size_t n_ft = 0)
+                   size_t n_ft = 0, bool tslow = false)
 {
     WsLayout L{};
     size_t o = WS_HEADER;
     if (op == BSGPU_OP_COMPRESS || op == BSGPU_OP_COMPRESS_VIS) {
         L.state = o;
         o += r256((size_t)g.nb * 8);
-        if (g.nb && fast_shape(g, n_time)) {
+        if (g.nb && fast_shape(g, n_time, tslow)) {
             L.slots = o;
             o += (size_t)FAST_MAX_WARPS * 2 * FAST_SLOT_BYTES;
         }
@@ -134,10 +136,12 @@ int vis_check(int64_t n_freq, int64_t n_in, int64_t n_time, double N, double f, 
 }
 
 VisParams vis_params(const WsLayout &L, void *ws, uint64_t n_in, uint64_t n_time, uint64_t n_prod,
-                     double N, double f, int is_int = 0)
+                     double N, double f, int is_int = 0, int tslow = 0, uint64_t n_freq = 0)
 {
     VisParams v{};
     v.is_int = is_int;
+    v.tslow = tslow;
+    v.FP = (uint32_t)(n_freq * n_prod);
     v.cft = L.cft ? reinterpret_cast<const float *>((uint8_t *)ws + L.cft) : nullptr;
     v.autos = reinterpret_cast<const float *>((uint8_t *)ws + L.autos);
     v.pairs = reinterpret_cast<const uint32_t *>((uint8_t *)ws + L.pairs);
@@ -155,7 +159,7 @@ VisParams vis_params(const WsLayout &L, void *ws, uint64_t n_in, uint64_t n_time
 int vis_dtype_ok(int dtype, int flags)
 {
     if (dtype != BSGPU_VIS_F32 && dtype != BSGPU_VIS_I32) return 0;
-    return (flags & ~BSGPU_VIS_COMPENSATE) == 0;
+    return (flags & ~(BSGPU_VIS_COMPENSATE | BSGPU_VIS_TIME_SLOWEST)) == 0;
 }
 
 // The tables (autos, product indices) and, when asked, the compensated c
@@ -163,10 +167,7 @@ int vis_dtype_ok(int dtype, int flags)
 int vis_prepare(const void *vis, const VisParams &v, int64_t n_freq, int64_t n_inputs,
                 int64_t n_time, double N, double f, cudaStream_t s)
 {
-    cudaError_t e = launch_vis_tables(reinterpret_cast<const float *>(vis),
-                                      const_cast<float *>(v.autos),
-                                      const_cast<uint32_t *>(v.pairs), (uint32_t)n_freq,
-                                      (uint32_t)n_inputs, (uint32_t)n_time, v.is_int, s);
+    cudaError_t e = launch_vis_tables(reinterpret_cast<const float *>(vis), v, (uint32_t)n_freq, s);
     if (e != cudaSuccess) return BSGPU_ERR_CUDA;
     if (v.cft) e = launch_vis_compensation(vis, v, (uint32_t)n_freq, f, N, s);
     return e == cudaSuccess ? BSGPU_OK : BSGPU_ERR_CUDA;
@@ -213,7 +214,8 @@ size_t bsgpu_vis_workspace_size_ex(int op, int64_t n_freq, int64_t n_inputs, int
         if (geometry(n_cplx * 8 / elem_size, elem_size, block_elems, g) != BSGPU_OK) return 0;
     }
     const size_t n_ft = (flags & BSGPU_VIS_COMPENSATE) ? (size_t)n_freq * n_time : 0;
-    return ws_layout(op, g, (uint64_t)n_freq * n_inputs * n_time, n_prod, (uint64_t)n_time, n_ft)
+    return ws_layout(op, g, (uint64_t)n_freq * n_inputs * n_time, n_prod, (uint64_t)n_time, n_ft,
+                     (flags & BSGPU_VIS_TIME_SLOWEST) != 0)
         .total;
 }
 
@@ -252,7 +254,8 @@ int bsgpu_reduce_precision_ex(const void *in, void *out, int dtype, int64_t n_fr
     if (ws_bytes < L.total) return BSGPU_ERR_SPACE;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(ws, 0, WS_HEADER, s) != cudaSuccess) return BSGPU_ERR_CUDA;
-    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32);
+    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32,
+                             (flags & BSGPU_VIS_TIME_SLOWEST) != 0, (uint64_t)n_freq);
     rc = vis_prepare(in, v, n_freq, n_inputs, n_time, N, f, s);
     if (rc) return rc;
     // 256-thread blocks, each warp rounding runs of 1024 samples
@@ -273,6 +276,18 @@ int bsgpu_reduce_precision_c64(const void *in, void *out, int64_t n_freq, int64_
 {
     return bsgpu_reduce_precision_ex(in, out, BSGPU_VIS_F32, n_freq, n_inputs, n_time, N, f, 0,
                                      ws, ws_bytes, stream);
+}
+
+int bsgpu_reorder_time(const void *in, void *out, uint64_t n_time, uint64_t n_series,
+                       size_t elem_size, void *stream)
+{
+    if (elem_size != 1 && elem_size != 2 && elem_size != 4 && elem_size != 8) return BSGPU_ERR_ARG;
+    if (n_time == 0 || n_series == 0) return BSGPU_OK;
+    if (!in || !out) return BSGPU_ERR_ARG;
+    if (((uintptr_t)in | (uintptr_t)out) & (elem_size - 1)) return BSGPU_ERR_ALIGN;
+    if (n_time > (1ull << 40) / n_series) return BSGPU_ERR_ARG;
+    return cuda_err(launch_reorder_time(in, out, n_time, n_series, (uint32_t)elem_size,
+                                        (cudaStream_t)stream));
 }
 
 static int shuffle_common(const void *in, void *out, size_t n_elem, size_t elem_size,
@@ -405,11 +420,13 @@ int bsgpu_compress_vis_ex(const void *vis, int dtype, int64_t n_freq, int64_t n_
         return BSGPU_ERR_ALIGN;
     uint64_t n_auto = (uint64_t)n_freq * n_inputs * n_time;
     const size_t n_ft = (flags & BSGPU_VIS_COMPENSATE) ? (size_t)n_freq * n_time : 0;
-    WsLayout L = ws_layout(BSGPU_OP_COMPRESS_VIS, g, n_auto, n_prod, (uint64_t)n_time, n_ft);
+    const bool tslow = (flags & BSGPU_VIS_TIME_SLOWEST) != 0;
+    WsLayout L = ws_layout(BSGPU_OP_COMPRESS_VIS, g, n_auto, n_prod, (uint64_t)n_time, n_ft, tslow);
     if (ws_bytes < L.total) return BSGPU_ERR_SPACE;
     if (level < 0 || level > 1) return BSGPU_ERR_ARG;
     if (out_cap < stream_bound(g)) return BSGPU_ERR_SPACE;
-    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32);
+    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32, tslow,
+                             (uint64_t)n_freq);
     cudaStream_t s = (cudaStream_t)stream;
     rc = vis_prepare(vis, v, n_freq, n_inputs, n_time, N, f, s);
     if (rc) return rc;

@@ -83,6 +83,25 @@ BSG_D bool load_block(uint8_t *dst, const uint8_t *src, uint32_t bytes, uint64_t
     return false;
 }
 
+// Block `tile` of a stream into shared `dst`: a bulk copy (returns true: wait
+// on `bar`) or, for a time-slowest visibility cube, a gather of its complex
+// samples into time-fastest order (8-byte loads; consecutive lanes take
+// consecutive output samples, so the shared stores are conflict-free and the
+// strided global reads share cache lines across a warp's successive steps).
+BSG_D bool load_block_any(const CodecArgs &a, uint8_t *dst, uint32_t tile, uint64_t *bar,
+                          uint32_t lane)
+{
+    const uint32_t bytes = block_elems_of(a, tile) * a.es;
+    if (!a.vis.enabled || !a.vis.tslow)
+        return load_block(dst, a.in + (uint64_t)tile * a.B * a.es, bytes, bar, lane);
+    const uint64_t c0 = ((uint64_t)tile * a.B * a.es) >> 3;
+    const uint2 *src = reinterpret_cast<const uint2 *>(a.in);
+    uint2 *d = reinterpret_cast<uint2 *>(dst);
+    for (uint32_t k = lane; k < bytes / 8; k += 32) d[k] = __ldg(src + vis_src(a.vis, c0 + k));
+    __syncwarp();
+    return false;
+}
+
 // Copy len bytes from 16-byte aligned shared `s` to global `g` (any alignment):
 // byte stores up to g's next 16-byte boundary, then 16-byte stores assembled
 // from two aligned shared vectors and a funnel shift, then the ragged end.
@@ -420,7 +439,9 @@ BSG_D void compress_place(const CodecArgs &a, uint32_t tile, const uint8_t *blk,
             const uint64_t c0 = first * a.es / 4;
             if (lane < tc) {
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(a.in);
-                const uint32_t u = reduce_component_at(src[c0 + lane], c0 + lane, a.vis);
+                const uint64_t fi = c0 + lane;
+                const uint32_t x = src[2 * vis_src(a.vis, fi >> 1) + (fi & 1)];
+                const uint32_t u = reduce_component_at(x, fi, a.vis);
                 for (int k = 0; k < 4; k++) a.out[end + 4 * lane + k] = (uint8_t)(u >> (8 * k));
             }
         } else {

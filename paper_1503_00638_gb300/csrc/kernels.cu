@@ -30,10 +30,12 @@ uint32_t shuffle_smem_bytes(uint32_t maxb)
 
 // Tables for the rounding: autos[f][i][t] = Re V(f, (i,i), t) and
 // pairs[p] = i | j << 16 for the upper-triangle product order.
-__global__ void vis_tables_kernel(const float *__restrict__ vis, float *__restrict__ autos,
-                                  uint32_t *__restrict__ pairs, uint32_t n_freq, uint32_t n_in,
-                                  uint32_t T, int is_int)
+__global__ void vis_tables_kernel(const float *__restrict__ vis, VisParams V, uint32_t n_freq)
 {
+    float *autos = const_cast<float *>(V.autos);
+    uint32_t *pairs = const_cast<uint32_t *>(V.pairs);
+    const uint32_t n_in = V.n_in, T = V.T;
+    const int is_int = V.is_int;
     const uint32_t P = n_in * (n_in + 1) / 2;
     const uint64_t n_auto = (uint64_t)n_freq * n_in * T;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -43,7 +45,7 @@ __global__ void vis_tables_kernel(const float *__restrict__ vis, float *__restri
         uint32_t i = (uint32_t)(fi % n_in);
         uint64_t f = fi / n_in;
         uint64_t pii = (uint64_t)i * n_in - (uint64_t)i * (i - 1) / 2;
-        const size_t at = ((f * P + pii) * T + t) * 2;
+        const size_t at = vis_src(V, (f * P + pii) * T + t) * 2;
         // int32 autos are converted to float32 (round to nearest)
         autos[x] = is_int ? __int2float_rn(reinterpret_cast<const int32_t *>(vis)[at]) : vis[at];
     }
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(256) vis_compensation_kernel(const void *__res
             if (i == j) continue;
             const float Ai = __ldg(P.autos + ((size_t)fr * P.n_in + i) * P.T + t);
             const float Aj = __ldg(P.autos + ((size_t)fr * P.n_in + j) * P.T + t);
-            const size_t at = (((size_t)fr * P.P + p) * P.T + t) * 2;
+            const size_t at = vis_src(P, ((size_t)fr * P.P + p) * P.T + t) * 2;
             float re, im;
             if (P.is_int) {
                 re = __int2float_rn(reinterpret_cast<const int32_t *>(vis)[at]);
@@ -119,6 +121,17 @@ __global__ void __launch_bounds__(256) reduce_precision_kernel(const uint2 *__re
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     constexpr uint32_t RUN = 1024;
+    if (P.tslow) {
+        // the post-acquisition reorder fused in: gather each output sample
+        // from its time-slowest place (output writes stay coalesced)
+        for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cplx;
+             c += (uint64_t)gridDim.x * blockDim.x) {
+            const uint32_t fp = (uint32_t)(c / P.T), t = (uint32_t)(c % P.T);
+            const uint32_t f = fp / P.P, p = fp - f * P.P;
+            out[c] = reduce_sample(__ldg(in + vis_src(P, c)), __ldg(P.pairs + p), f, t, P);
+        }
+        return;
+    }
     for (uint64_t r = warp * RUN; r < n_cplx; r += nwarps * RUN) {
         uint32_t cnt = (uint32_t)(n_cplx - r < RUN ? n_cplx - r : RUN);
         if ((P.T & 1u) == 0)  // r is even and so is cnt (n_cplx = F P T is even)
@@ -152,8 +165,7 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 9 : 1)
     __syncwarp();
     uint32_t parity = 0;
     uint32_t tile = a.tile_begin + grab_tile(a.tile_counter, lane);
-    bool pend = tile < a.tile_end && load_block(in, a.in + (uint64_t)tile * a.B * a.es,
-                                                block_elems_of(a, tile) * a.es, bar, lane);
+    bool pend = tile < a.tile_end && load_block_any(a, in, tile, bar, lane);
     while (tile < a.tile_end) {
         if (pend) {
             if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);
@@ -167,8 +179,7 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 9 : 1)
             // the transpose's reads of `in` (generic proxy) precede the async write
             fence_proxy_async_smem();
             __syncwarp();
-            pend = load_block(in, a.in + (uint64_t)nxt * a.B * a.es, block_elems_of(a, nxt) * a.es,
-                              bar, lane);
+            pend = load_block_any(a, in, nxt, bar, lane);
         }
         compress_finish<MAXB, LEVEL>(a, tile, tmp, out, scratch, lane);
         __syncwarp();
@@ -300,7 +311,8 @@ __global__ void compress_small_kernel(const __grid_constant__ CodecArgs a)
     if (a.vis.enabled) {
         if (lane < tb / 4) {
             const uint32_t *src = reinterpret_cast<const uint32_t *>(a.in);
-            const uint32_t u = reduce_component_at(src[lane], lane, a.vis);
+            const uint32_t x = src[2 * vis_src(a.vis, lane >> 1) + (lane & 1)];
+            const uint32_t u = reduce_component_at(x, lane, a.vis);
             for (int k = 0; k < 4; k++) a.out[12 + 4 * lane + k] = (uint8_t)(u >> (8 * k));
         }
     } else {
@@ -543,16 +555,56 @@ cudaError_t launch_vis_compensation(const void *vis, const VisParams &P, uint32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_vis_tables(const float *vis, float *autos, uint32_t *pairs, uint32_t n_freq,
-                              uint32_t n_in, uint32_t T, int is_int, cudaStream_t s)
+cudaError_t launch_vis_tables(const float *vis, const VisParams &V, uint32_t n_freq,
+                              cudaStream_t s)
 {
-    uint64_t n = (uint64_t)n_freq * n_in * T;
-    uint64_t P = (uint64_t)n_in * (n_in + 1) / 2;
+    uint64_t n = (uint64_t)n_freq * V.n_in * V.T;
+    uint64_t P = (uint64_t)V.n_in * (V.n_in + 1) / 2;
     uint64_t work = n > P ? n : P;
     uint32_t blocks = (uint32_t)((work + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (blocks == 0) blocks = 1;
-    vis_tables_kernel<<<blocks, 256, 0, s>>>(vis, autos, pairs, n_freq, n_in, T, is_int);
+    vis_tables_kernel<<<blocks, 256, 0, s>>>(vis, V, n_freq);
+    return cudaGetLastError();
+}
+
+// Post-acquisition reorder (Sec. 2): [T][S] elements (time slowest, the
+// order an instrument writes) to [S][T] (time fastest), through 32 x 32
+// tiles in shared memory so that reads and writes are both coalesced.
+template <typename E>
+__global__ void __launch_bounds__(256) reorder_time_kernel(const E *__restrict__ in,
+                                                           E *__restrict__ out, uint64_t T,
+                                                           uint64_t S)
+{
+    __shared__ E tile[32][33];
+    const uint64_t ntx = (S + 31) / 32, nty = (T + 31) / 32;
+    for (uint64_t b = blockIdx.x; b < ntx * nty; b += gridDim.x) {
+        const uint64_t s0 = (b % ntx) * 32, t0 = (b / ntx) * 32;
+        __syncthreads();
+        for (uint32_t k = threadIdx.y; k < 32; k += blockDim.y) {
+            const uint64_t t = t0 + k, sx = s0 + threadIdx.x;
+            if (t < T && sx < S) tile[k][threadIdx.x] = in[t * S + sx];
+        }
+        __syncthreads();
+        for (uint32_t k = threadIdx.y; k < 32; k += blockDim.y) {
+            const uint64_t sx = s0 + k, t = t0 + threadIdx.x;
+            if (t < T && sx < S) out[sx * T + t] = tile[threadIdx.x][k];
+        }
+    }
+}
+
+cudaError_t launch_reorder_time(const void *in, void *out, uint64_t T, uint64_t S, uint32_t es,
+                                cudaStream_t s)
+{
+    const uint64_t tiles = ((S + 31) / 32) * ((T + 31) / 32);
+    const uint32_t grid = (uint32_t)(tiles < 65536 ? (tiles ? tiles : 1) : 65536);
+    const dim3 blk(32, 8);
+    switch (es) {
+    case 1: reorder_time_kernel<<<grid, blk, 0, s>>>((const uint8_t *)in, (uint8_t *)out, T, S); break;
+    case 2: reorder_time_kernel<<<grid, blk, 0, s>>>((const uint16_t *)in, (uint16_t *)out, T, S); break;
+    case 4: reorder_time_kernel<<<grid, blk, 0, s>>>((const uint32_t *)in, (uint32_t *)out, T, S); break;
+    default: reorder_time_kernel<<<grid, blk, 0, s>>>((const uint2 *)in, (uint2 *)out, T, S); break;
+    }
     return cudaGetLastError();
 }
 

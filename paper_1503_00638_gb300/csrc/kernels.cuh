@@ -16,8 +16,18 @@ struct VisParams {
     float c, c2;            // fl32(6 f / N) and 2 c
     const float *cft;       // per (freq, time) compensated c (Sec. 3.2), or null
     int is_int;             // components are int32 (else float32)
+    int tslow;              // the input is time-slowest: [T][n_freq n_prod] samples
+    uint32_t FP;            // n_freq n_prod (series of T samples)
     int enabled;
 };
+
+// Input sample holding time-fastest complex index c ((f, p) series c / T,
+// time c % T): the same index, or its place in a time-slowest input (the
+// instrument's order before the post-acquisition reorder of Sec. 2).
+__host__ __device__ __forceinline__ uint64_t vis_src(const VisParams &P, uint64_t c)
+{
+    return P.tslow ? (c % P.T) * P.FP + c / P.T : c;
+}
 
 // c (2c for the real part of an auto) of the sample at (f, t)
 __device__ __forceinline__ float vis_c(const VisParams &P, uint32_t f, uint32_t t, bool is_auto)
@@ -53,8 +63,11 @@ uint32_t decompress_smem_bytes(uint32_t maxb);
 uint32_t shuffle_smem_bytes(uint32_t maxb);
 
 // Launchers (return cudaGetLastError()).  `grid` warps of 32 threads.
-cudaError_t launch_vis_tables(const float *vis, float *autos, uint32_t *pairs, uint32_t n_freq,
-                              uint32_t n_in, uint32_t T, int is_int, cudaStream_t s);
+cudaError_t launch_vis_tables(const float *vis, const VisParams &P, uint32_t n_freq,
+                              cudaStream_t s);
+// time-slowest [T][S] elements of es bytes -> time-fastest [S][T]
+cudaError_t launch_reorder_time(const void *in, void *out, uint64_t T, uint64_t S, uint32_t es,
+                                cudaStream_t s);
 // per (freq, time) compensated c of Sec. 3.2 into P.cft (needs the tables)
 cudaError_t launch_vis_compensation(const void *vis, const VisParams &P, uint32_t n_freq,
                                     double f, double N, cudaStream_t s);
