@@ -82,6 +82,16 @@ def lib() -> ctypes.CDLL:
             L.orc_compensation_min.restype = c_f
             L.orc_reduce_precision.argtypes = [c_vp, c_vp, c_i, c_l, c_l, c_l, c_d, c_d, c_i]
             L.orc_reduce_precision.restype = None
+            L.orc_full_index.argtypes = [c_l, c_i, c_i, c_i]
+            L.orc_full_index.restype = c_l
+            L.orc_full_cov_matrix.argtypes = [c_vp, c_i, c_d, c_vp]
+            L.orc_full_cov_matrix.restype = None
+            L.orc_invert_spd.argtypes = [c_vp, c_l, c_vp]
+            L.orc_invert_spd.restype = c_i
+            L.orc_full_noise_var.argtypes = [c_vp, c_i, c_d, c_vp]
+            L.orc_full_noise_var.restype = c_i
+            L.orc_reduce_precision_full.argtypes = [c_vp, c_vp, c_i, c_l, c_l, c_l, c_d, c_d]
+            L.orc_reduce_precision_full.restype = None
             L.orc_reorder_time.argtypes = [c_vp, c_vp, c_sz, c_sz, c_sz]
             L.orc_reorder_time.restype = None
             L.orc_bitshuffle.argtypes = [c_vp, c_vp, c_sz, c_sz, c_sz, c_i]
@@ -201,6 +211,44 @@ def _n_inputs(P: int) -> int:
     if n * (n + 1) // 2 != P:
         raise ValueError(f"{P} products is not n(n+1)/2")
     return n
+
+
+# -- Sec. 3.1, full covariance (small arrays) ---------------------------------
+
+def full_index(n: int, i: int, j: int, alpha: int) -> int:
+    return lib().orc_full_index(n, i, j, alpha)
+
+
+def full_cov_matrix(V: np.ndarray, N: float) -> np.ndarray:
+    """M x M covariance (Eq. rad_full1-3) of the n^2 components of one sample."""
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    n = V.shape[0]
+    C = np.empty((n * n, n * n))
+    lib().orc_full_cov_matrix(_ptr(V), n, N, _ptr(C))
+    return C
+
+
+def invert_spd(A: np.ndarray):
+    A = np.array(A, dtype=np.float64, order="C")
+    out = np.empty_like(A)
+    rc = lib().orc_invert_spd(_ptr(A), A.shape[0], _ptr(out))
+    return rc, out
+
+
+def full_noise_var(V: np.ndarray, N: float):
+    """(rc, s^2 per component) of Eq. noise with the full covariance."""
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    n = V.shape[0]
+    s2 = np.empty(n * n)
+    rc = lib().orc_full_noise_var(_ptr(V), n, N, _ptr(s2))
+    return rc, s2
+
+
+def reduce_precision_full(vis: np.ndarray, N: float, f: float) -> np.ndarray:
+    F, P, T, is_int, a = _cube(vis)
+    out = np.empty_like(a)
+    lib().orc_reduce_precision_full(_ptr(a), _ptr(out), is_int, F, _n_inputs(P), T, N, f)
+    return out
 
 
 # -- Sec. 2 ------------------------------------------------------------------

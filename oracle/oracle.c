@@ -34,8 +34,13 @@
  *       nearest multiple above INT32_MAX is replaced by the lower multiple.
  *   R18 the compensated f of Sec. 3.2 is evaluated per (freq, time) sample,
  *       in float32 as stated at orc_compensation_min.
+ *   R20 full-covariance noise: components after the redundancy removal of
+ *       Sec. 3.1 in the order of orc_full_index; C from Eq. rad_full1-3 in
+ *       fp64 from the float32 (or int32) values; s^2 = 1/(C^-1)_kk; a sample
+ *       whose C is not positive definite is left unrounded; q = fl32(12 f s^2).
  */
 #include <stddef.h>
+#include <stdlib.h>
 #include <stdint.h>
 #include <string.h>
 #include <math.h>
@@ -266,6 +271,143 @@ void orc_reduce_precision(const void *in, void *out, int is_int, long n_freq, lo
             }
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1: noise from the full covariance (small arrays)                   */
+/* ------------------------------------------------------------------------ */
+
+/* After the redundancy removal of Sec. 3.1 (Re V_ji = Re V_ij, Im V_ji =
+ * -Im V_ij, Im V_ii = 0 is dropped) the components of one (freq, time) sample
+ * are, in this order: Re of every product p (p = 0 .. P-1, upper-triangle
+ * row-major), then Im of every cross product (i < j) in the same order.
+ * M = 2P - n = n^2 components.  Reading R20. */
+long orc_full_index(long n, int i, int j, int alpha)
+{
+    long P = n * (n + 1) / 2;
+    long p = (long)i * n - (long)i * (i - 1) / 2 + (j - i);
+    return alpha == 0 ? p : P + p - i - 1;   /* i + 1 autos precede (i, j) */
+}
+
+/* The M x M covariance of Eq. rad_full1-3 (row-major) for the complex n x n
+ * correlation matrix V (row-major, interleaved re/im, Hermitian). */
+void orc_full_cov_matrix(const double *V, int n, double N, double *C)
+{
+    long M = (long)n * n;
+    for (int i = 0; i < n; i++)
+        for (int j = i; j < n; j++)
+            for (int a = 0; a < 2; a++) {
+                if (a == 1 && i == j) continue;
+                long r = orc_full_index(n, i, j, a);
+                for (int g = 0; g < n; g++)
+                    for (int h = g; h < n; h++)
+                        for (int b = 0; b < 2; b++) {
+                            if (b == 1 && g == h) continue;
+                            long c = orc_full_index(n, g, h, b);
+                            C[r * M + c] = orc_rad_full_cov(V, n, a, i, j, b, g, h, N);
+                        }
+            }
+}
+
+/* Inverse of the M x M matrix A (destroyed) into Ainv by Gauss-Jordan
+ * elimination without pivoting, which is exact arithmetic's route for a
+ * positive definite matrix (every pivot is a Schur complement, hence > 0).
+ * Returns 0, or -1 when a pivot is not positive and finite (the matrix is
+ * not positive definite as far as fp64 can tell; reading R20). */
+int orc_invert_spd(double *A, long M, double *Ainv)
+{
+    for (long r = 0; r < M; r++)
+        for (long c = 0; c < M; c++) Ainv[r * M + c] = (r == c) ? 1.0 : 0.0;
+    for (long k = 0; k < M; k++) {
+        double piv = A[k * M + k];
+        if (!(piv > 0.0) || !isfinite(piv)) return -1;
+        for (long c = 0; c < M; c++) {
+            A[k * M + c] /= piv;
+            Ainv[k * M + c] /= piv;
+        }
+        for (long r = 0; r < M; r++) {
+            if (r == k) continue;
+            double m = A[r * M + k];
+            if (m == 0.0) continue;
+            for (long c = 0; c < M; c++) {
+                A[r * M + c] -= m * A[k * M + c];
+                Ainv[r * M + c] -= m * Ainv[k * M + c];
+            }
+        }
+    }
+    return 0;
+}
+
+/* Eq. noise: s^2 = 1 / (C^-1)_kk for every component of one sample, C from
+ * Eq. rad_full1-3.  Returns 0, or -1 when C is not positive definite (s2 is
+ * then all zero: no rounding for the sample).  fp64. */
+int orc_full_noise_var(const double *V, int n, double N, double *s2)
+{
+    long M = (long)n * n;
+    double *C = (double *)malloc(sizeof(double) * M * M);
+    double *Ci = (double *)malloc(sizeof(double) * M * M);
+    int rc = -1;
+    if (C && Ci) {
+        orc_full_cov_matrix(V, n, N, C);
+        rc = orc_invert_spd(C, M, Ci);
+        for (long k = 0; k < M; k++) s2[k] = rc == 0 ? 1.0 / Ci[k * M + k] : 0.0;
+    }
+    free(C);
+    free(Ci);
+    return rc;
+}
+
+/* Rounding of a float32 (is_int = 0) or int32 cube with the noise of Eq.
+ * noise from the full covariance: per component q = fl32(12 f s^2) (the
+ * product in fp64, rounded once), then the granularity and rounding of
+ * orc_reduce_precision (R2-R7, R17).  Imaginary parts of autos stay. */
+void orc_reduce_precision_full(const void *in, void *out, int is_int, long n_freq, long n_in,
+                               long n_time, double N, double f)
+{
+    long n_prod = n_in * (n_in + 1) / 2, M = n_in * n_in;
+    double *V = (double *)malloc(sizeof(double) * 2 * n_in * n_in);
+    double *s2 = (double *)malloc(sizeof(double) * M);
+    if (!V || !s2) {
+        free(V);
+        free(s2);
+        return;
+    }
+    for (long fr = 0; fr < n_freq; fr++) {
+        for (long t = 0; t < n_time; t++) {
+            long p = 0;
+            for (long i = 0; i < n_in; i++)
+                for (long j = i; j < n_in; j++, p++) {
+                    long e = ((fr * n_prod + p) * n_time + t) * 2;
+                    double re = comp_value(in, is_int, e), im = comp_value(in, is_int, e + 1);
+                    V[2 * (i * n_in + j)] = re;
+                    V[2 * (i * n_in + j) + 1] = im;
+                    V[2 * (j * n_in + i)] = re;
+                    V[2 * (j * n_in + i) + 1] = -im;
+                }
+            orc_full_noise_var(V, (int)n_in, N, s2);
+            p = 0;
+            for (long i = 0; i < n_in; i++)
+                for (long j = i; j < n_in; j++, p++)
+                    for (int part = 0; part < 2; part++) {
+                        long e = ((fr * n_prod + p) * n_time + t) * 2 + part;
+                        int rounded = !(i == j && part == 1);
+                        int k = 0, ok = 0;
+                        if (rounded) {
+                            float q = (float)(12.0 * f * s2[orc_full_index(n_in, (int)i, (int)j, part)]);
+                            ok = orc_granularity_exponent(q, &k);
+                        }
+                        if (is_int) {
+                            int32_t x = ((const int32_t *)in)[e];
+                            ((int32_t *)out)[e] = ok ? orc_round_int(x, k) : x;
+                        } else {
+                            float x = ((const float *)in)[e];
+                            ((float *)out)[e] = ok ? orc_round_pow2(x, k) : x;
+                        }
+                    }
+        }
+    }
+    free(V);
+    free(s2);
 }
 
 /* The granularity exponent chosen for every float of the cube (for tests of
