@@ -53,6 +53,7 @@ extern "C" {
 /* Flags of the _ex entry points. */
 #define BSGPU_VIS_COMPENSATE 1    /* Sec. 3.2: per-sample compensated f, see below   */
 #define BSGPU_VIS_TIME_SLOWEST 2  /* input in the instrument's order, see below     */
+#define BSGPU_VIS_FULL_COV 4      /* Sec. 3.1 full covariance (small arrays), below */
 
 /* Library version string. */
 const char *bsgpu_version(void);
@@ -140,10 +141,31 @@ int bsgpu_reduce_precision_c64(const void *in, void *out, int64_t n_freq, int64_
  *           reading, and the order in which neighbouring values correlate);
  *           this flag fuses that reorder into the rounding (and, in
  *           bsgpu_compress_vis_ex, into the compression).
+ *           BSGPU_VIS_FULL_COV (n_inputs <= 16; not with COMPENSATE): the
+ *           noise of Eq. noise from the full covariance of Eq.
+ *           rad_full1-3 instead of Eq. rad_simple: for every (freq, time)
+ *           sample the n^2 components left after the redundancy removal of
+ *           Sec. 3.1 (Re of every product, Im of every cross product) get
+ *           s^2 = 1 / (C^-1)_kk, computed in fp64 (Cholesky factorisation,
+ *           then the inverse factor); q = fl32(12 f s^2).  A sample whose C
+ *           is not positive definite is left unrounded.  Sec. 3.1 keeps
+ *           this to arrays of a few dozen inputs at most; the workspace
+ *           grows as n^4.
  * ws: bsgpu_vis_workspace_size_ex(BSGPU_OP_REDUCE_PRECISION, ..., flags). */
 int bsgpu_reduce_precision_ex(const void *in, void *out, int dtype, int64_t n_freq,
                               int64_t n_inputs, int64_t n_time, double N, double f, int flags,
                               void *ws, size_t ws_bytes, void *stream);
+
+/* Eq. noise with the full covariance of Eq. rad_full1-3 (Sec. 3.1), on its
+ * own: d_s2 receives [n_freq][n_time][n_inputs^2] fp64 unmarginalized
+ * variances s^2 = 1/(C^-1)_kk in the component order of BSGPU_VIS_FULL_COV
+ * (0 for a sample whose C is not positive definite).  flags: 0 or
+ * BSGPU_VIS_TIME_SLOWEST.  n_inputs <= 16.  ws:
+ * bsgpu_vis_workspace_size_ex(BSGPU_OP_REDUCE_PRECISION, ..., flags |
+ * BSGPU_VIS_FULL_COV). */
+int bsgpu_full_noise_var(const void *vis, int dtype, int64_t n_freq, int64_t n_inputs,
+                         int64_t n_time, double N, int flags, double *d_s2, void *ws,
+                         size_t ws_bytes, void *stream);
 
 /* Sec. 2: the post-acquisition reorder on its own.  in holds n_time rows of
  * n_series elements of elem_size (1, 2, 4 or 8) bytes (time slowest); out

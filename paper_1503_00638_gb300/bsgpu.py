@@ -25,6 +25,7 @@ OP_COMPRESS, OP_DECOMPRESS, OP_COMPRESS_VIS, OP_REDUCE_PRECISION = 1, 2, 3, 4
 VIS_F32, VIS_I32 = 0, 1
 VIS_COMPENSATE = 1
 VIS_TIME_SLOWEST = 2
+VIS_FULL_COV = 4
 _NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_SPACE", -3: "ERR_CORRUPT", -4: "ERR_CUDA",
           -5: "ERR_TIMEOUT", -6: "ERR_ALIGN"}
 
@@ -47,6 +48,7 @@ _SIGS = {
     "bsgpu_compress_vis": ([_vp, _i64, _i64, _i64, _d, _d, _sz, _i, _vp, _sz, _vp, _vp, _vp,
                             _sz, _vp], _i),
     "bsgpu_reorder_time": ([_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, _sz, _vp], _i),
+    "bsgpu_full_noise_var": ([_vp, _i, _i64, _i64, _i64, _d, _i, _vp, _vp, _sz, _vp], _i),
     "bsgpu_compress_vis_ex": ([_vp, _i, _i64, _i64, _i64, _d, _d, _i, _sz, _sz, _i, _vp, _sz,
                                _vp, _vp, _vp, _sz, _vp], _i),
     "bsgpu_compress_noalloc": ([_vp, _sz, _sz, _sz, _i, _vp, _sz, _vp, _vp, _vp], _i),
@@ -183,14 +185,20 @@ def _cube(vis: torch.Tensor, time_slowest: bool = False):
     raise ValueError("expected a complex64 [F][P][T] or int32 [F][P][T][2] cube")
 
 
+def _flags(compensate=False, time_slowest=False, full_cov=False) -> int:
+    return ((VIS_COMPENSATE if compensate else 0) | (VIS_TIME_SLOWEST if time_slowest else 0) |
+            (VIS_FULL_COV if full_cov else 0))
+
+
 def reduce_precision(vis: torch.Tensor, N: float, f: float, compensate: bool = False,
                      out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
-                     stream=None, time_slowest: bool = False) -> torch.Tensor:
+                     stream=None, time_slowest: bool = False,
+                     full_cov: bool = False) -> torch.Tensor:
     """Round a complex64 or int32 cube, optionally with Sec. 3.2's
-    compensated f and from the time-slowest order (returns out, time
-    fastest)."""
+    compensated f, from the time-slowest order, or with the full-covariance
+    noise of Sec. 3.1 (returns out, time fastest)."""
     F, n, T, dt = _cube(vis, time_slowest)
-    flags = (VIS_COMPENSATE if compensate else 0) | (VIS_TIME_SLOWEST if time_slowest else 0)
+    flags = _flags(compensate, time_slowest, full_cov)
     if out is None:
         P = n * (n + 1) // 2
         shape = (F, P, T) if vis.dim() == 3 else (F, P, T, 2)
@@ -201,6 +209,22 @@ def reduce_precision(vis: torch.Tensor, N: float, f: float, compensate: bool = F
                                           flags, _ptr(ws), ws.numel(), _stream(stream)),
            "bsgpu_reduce_precision_ex")
     return out
+
+
+def full_noise_var(vis: torch.Tensor, N: float, time_slowest: bool = False,
+                   stream=None) -> torch.Tensor:
+    """s^2 = 1/(C^-1)_kk of Eq. noise with the full covariance, as a
+    [n_freq][n_time][n_inputs^2] float64 tensor."""
+    F, n, T, dt = _cube(vis, time_slowest)
+    flags = _flags(time_slowest=time_slowest)
+    need = vis_workspace_size_ex(OP_REDUCE_PRECISION, F, n, T, 4, 0, flags | VIS_FULL_COV)
+    if need == 0:
+        raise BsgpuError(ERR_ARG, "bsgpu_vis_workspace_size_ex")
+    ws = new_workspace(need, vis.device)
+    s2 = torch.empty((F, T, n * n), dtype=torch.float64, device=vis.device)
+    _check(_lib.bsgpu_full_noise_var(_ptr(vis), dt, F, n, T, float(N), flags, _ptr(s2), _ptr(ws),
+                                     ws.numel(), _stream(stream)), "bsgpu_full_noise_var")
+    return s2
 
 
 def reorder_time(x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -305,12 +329,13 @@ def compress_vis(vis: torch.Tensor, N: float, f: float, block_elems: int = 0,
 def compress_vis_ex(vis: torch.Tensor, N: float, f: float, compensate: bool = False,
                     elem_size: int = 4, block_elems: int = 0, out: torch.Tensor | None = None,
                     with_offsets: bool = True, ws: torch.Tensor | None = None, stream=None,
-                    level: int = 0, time_slowest: bool = False) -> Compressed:
+                    level: int = 0, time_slowest: bool = False,
+                    full_cov: bool = False) -> Compressed:
     """Precision reduction (complex64 or int32 cube, optionally compensated,
     optionally from the time-slowest order) + Bitshuffle + LZ4 with 4-byte
     components or 8-byte samples as elements."""
     F, n_in, T, dt = _cube(vis, time_slowest)
-    flags = (VIS_COMPENSATE if compensate else 0) | (VIS_TIME_SLOWEST if time_slowest else 0)
+    flags = _flags(compensate, time_slowest, full_cov)
     n = F * (n_in * (n_in + 1) // 2) * T * 8 // elem_size
     cap = compress_bound(n, elem_size, block_elems)
     if cap == 0:

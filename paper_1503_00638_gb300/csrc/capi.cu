@@ -76,8 +76,31 @@ uint32_t persistent_grid(uint32_t smem_per_cta, uint64_t work)
 }
 
 struct WsLayout {
-    size_t state, autos, pairs, cft, offsets, slots, total;
+    size_t state, autos, pairs, cft, qtab, fscr, offsets, slots, total;
 };
+
+// What the flags of the visibility entry points add to the workspace.
+struct VisOpts {
+    bool tslow = false, full = false;
+    size_t n_ft = 0;                    // compensated c per (freq, time)
+    size_t qtab_bytes = 0, fscr_bytes = 0;
+    uint32_t full_grid = 0;             // CTAs of the full-covariance kernel
+};
+
+VisOpts vis_opts(int flags, int64_t n_freq, int64_t n_in, int64_t n_time)
+{
+    VisOpts o;
+    o.tslow = (flags & BSGPU_VIS_TIME_SLOWEST) != 0;
+    o.full = (flags & BSGPU_VIS_FULL_COV) != 0;
+    if (flags & BSGPU_VIS_COMPENSATE) o.n_ft = (size_t)n_freq * n_time;
+    if (o.full) {
+        const uint64_t ft = (uint64_t)n_freq * n_time, M = (uint64_t)n_in * n_in;
+        o.full_grid = (uint32_t)(ft < 256 ? ft : 256);
+        o.qtab_bytes = ft * M * 4;
+        o.fscr_bytes = (size_t)o.full_grid * M * M * 8;
+    }
+    return o;
+}
 
 // Whether compress takes the fast kernel (full blocks of at most 8 KiB of 4-
 // or 8-byte elements; a cube of 4-byte components also needs n_time % 16 == 0).
@@ -90,8 +113,9 @@ bool fast_shape(const Geometry &g, uint64_t n_time, bool tslow = false)
 
 // n_ft: entries of the per-(freq, time) compensated-c table (0 = none)
 WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint64_t n_time = 0,
-                   size_t n_ft = 0, bool tslow = false)
+                   const VisOpts &opts = VisOpts())
 {
+    const bool tslow = opts.tslow || opts.full;  // both take the general compress kernel
     WsLayout L{};
     size_t o = WS_HEADER;
     if (op == BSGPU_OP_COMPRESS || op == BSGPU_OP_COMPRESS_VIS) {
@@ -107,9 +131,15 @@ WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint
         o += r256(n_auto * 4);
         L.pairs = o;
         o += r256(n_prod * 4);
-        if (n_ft) {
+        if (opts.n_ft) {
             L.cft = o;
-            o += r256(n_ft * 4);
+            o += r256(opts.n_ft * 4);
+        }
+        if (opts.full) {
+            L.qtab = o;
+            o += r256(opts.qtab_bytes);
+            L.fscr = o;
+            o += r256(opts.fscr_bytes);
         }
     }
     if (op == BSGPU_OP_DECOMPRESS) {
@@ -136,12 +166,15 @@ int vis_check(int64_t n_freq, int64_t n_in, int64_t n_time, double N, double f, 
 }
 
 VisParams vis_params(const WsLayout &L, void *ws, uint64_t n_in, uint64_t n_time, uint64_t n_prod,
-                     double N, double f, int is_int = 0, int tslow = 0, uint64_t n_freq = 0)
+                     double N, double f, int is_int = 0, const VisOpts &o = VisOpts(),
+                     uint64_t n_freq = 0)
 {
     VisParams v{};
     v.is_int = is_int;
-    v.tslow = tslow;
+    v.tslow = o.tslow;
     v.FP = (uint32_t)(n_freq * n_prod);
+    v.qtab = L.qtab ? reinterpret_cast<const float *>((uint8_t *)ws + L.qtab) : nullptr;
+    v.M = (uint32_t)(n_in * n_in);
     v.cft = L.cft ? reinterpret_cast<const float *>((uint8_t *)ws + L.cft) : nullptr;
     v.autos = reinterpret_cast<const float *>((uint8_t *)ws + L.autos);
     v.pairs = reinterpret_cast<const uint32_t *>((uint8_t *)ws + L.pairs);
@@ -156,20 +189,29 @@ VisParams vis_params(const WsLayout &L, void *ws, uint64_t n_in, uint64_t n_time
     return v;
 }
 
-int vis_dtype_ok(int dtype, int flags)
+// dtype and flags valid, and the full covariance only for small arrays
+// (and not with the compensation, which corrects the diagonal approximation)
+int vis_dtype_ok(int dtype, int flags, int64_t n_inputs = 1)
 {
     if (dtype != BSGPU_VIS_F32 && dtype != BSGPU_VIS_I32) return 0;
-    return (flags & ~(BSGPU_VIS_COMPENSATE | BSGPU_VIS_TIME_SLOWEST)) == 0;
+    if (flags & ~(BSGPU_VIS_COMPENSATE | BSGPU_VIS_TIME_SLOWEST | BSGPU_VIS_FULL_COV)) return 0;
+    if (flags & BSGPU_VIS_FULL_COV)
+        return !(flags & BSGPU_VIS_COMPENSATE) && n_inputs <= (int64_t)FULL_MAX_INPUTS;
+    return 1;
 }
 
 // The tables (autos, product indices) and, when asked, the compensated c
-// per (freq, time): everything the rounding kernels read besides the cube.
-int vis_prepare(const void *vis, const VisParams &v, int64_t n_freq, int64_t n_inputs,
-                int64_t n_time, double N, double f, cudaStream_t s)
+// per (freq, time) or the full-covariance q table: everything the rounding
+// kernels read besides the cube.
+int vis_prepare(const void *vis, const VisParams &v, const WsLayout &L, const VisOpts &o,
+                void *ws, int64_t n_freq, double N, double f, cudaStream_t s, double *s2 = nullptr)
 {
     cudaError_t e = launch_vis_tables(reinterpret_cast<const float *>(vis), v, (uint32_t)n_freq, s);
     if (e != cudaSuccess) return BSGPU_ERR_CUDA;
     if (v.cft) e = launch_vis_compensation(vis, v, (uint32_t)n_freq, f, N, s);
+    if (e == cudaSuccess && v.qtab)
+        e = launch_full_noise(vis, v, (uint32_t)n_freq, f, N,
+                              reinterpret_cast<double *>((uint8_t *)ws + L.fscr), o.full_grid, s2, s);
     return e == cudaSuccess ? BSGPU_OK : BSGPU_ERR_CUDA;
 }
 
@@ -206,16 +248,15 @@ size_t bsgpu_vis_workspace_size_ex(int op, int64_t n_freq, int64_t n_inputs, int
 {
     uint64_t n_prod, n_cplx;
     if (op != BSGPU_OP_COMPRESS_VIS && op != BSGPU_OP_REDUCE_PRECISION) return 0;
-    if (!vis_dtype_ok(BSGPU_VIS_F32, flags)) return 0;
+    if (!vis_dtype_ok(BSGPU_VIS_F32, flags, n_inputs)) return 0;
     if (vis_check(n_freq, n_inputs, n_time, 1.0, 0.0, n_prod, n_cplx) != BSGPU_OK) return 0;
     Geometry g{};
     if (op == BSGPU_OP_COMPRESS_VIS) {
         if (elem_size != 4 && elem_size != 8) return 0;
         if (geometry(n_cplx * 8 / elem_size, elem_size, block_elems, g) != BSGPU_OK) return 0;
     }
-    const size_t n_ft = (flags & BSGPU_VIS_COMPENSATE) ? (size_t)n_freq * n_time : 0;
-    return ws_layout(op, g, (uint64_t)n_freq * n_inputs * n_time, n_prod, (uint64_t)n_time, n_ft,
-                     (flags & BSGPU_VIS_TIME_SLOWEST) != 0)
+    return ws_layout(op, g, (uint64_t)n_freq * n_inputs * n_time, n_prod, (uint64_t)n_time,
+                     vis_opts(flags, n_freq, n_inputs, n_time))
         .total;
 }
 
@@ -242,21 +283,21 @@ int bsgpu_reduce_precision_ex(const void *in, void *out, int dtype, int64_t n_fr
                               void *ws, size_t ws_bytes, void *stream)
 {
     uint64_t n_prod, n_cplx;
-    if (!vis_dtype_ok(dtype, flags)) return BSGPU_ERR_ARG;
+    if (!vis_dtype_ok(dtype, flags, n_inputs)) return BSGPU_ERR_ARG;
     int rc = vis_check(n_freq, n_inputs, n_time, N, f, n_prod, n_cplx);
     if (rc) return rc;
     if (!in || !out || !ws) return BSGPU_ERR_ARG;
     if (!aligned16(in) || !aligned16(out) || !aligned16(ws)) return BSGPU_ERR_ALIGN;
     Geometry g{};
     uint64_t n_auto = (uint64_t)n_freq * n_inputs * n_time;
-    const size_t n_ft = (flags & BSGPU_VIS_COMPENSATE) ? (size_t)n_freq * n_time : 0;
-    WsLayout L = ws_layout(BSGPU_OP_REDUCE_PRECISION, g, n_auto, n_prod, 0, n_ft);
+    const VisOpts o = vis_opts(flags, n_freq, n_inputs, n_time);
+    WsLayout L = ws_layout(BSGPU_OP_REDUCE_PRECISION, g, n_auto, n_prod, 0, o);
     if (ws_bytes < L.total) return BSGPU_ERR_SPACE;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(ws, 0, WS_HEADER, s) != cudaSuccess) return BSGPU_ERR_CUDA;
-    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32,
-                             (flags & BSGPU_VIS_TIME_SLOWEST) != 0, (uint64_t)n_freq);
-    rc = vis_prepare(in, v, n_freq, n_inputs, n_time, N, f, s);
+    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32, o,
+                             (uint64_t)n_freq);
+    rc = vis_prepare(in, v, L, o, ws, n_freq, N, f, s);
     if (rc) return rc;
     // 256-thread blocks, each warp rounding runs of 1024 samples
     uint64_t runs = (n_cplx + 1023) / 1024;
@@ -276,6 +317,30 @@ int bsgpu_reduce_precision_c64(const void *in, void *out, int64_t n_freq, int64_
 {
     return bsgpu_reduce_precision_ex(in, out, BSGPU_VIS_F32, n_freq, n_inputs, n_time, N, f, 0,
                                      ws, ws_bytes, stream);
+}
+
+int bsgpu_full_noise_var(const void *vis, int dtype, int64_t n_freq, int64_t n_inputs,
+                         int64_t n_time, double N, int flags, double *d_s2, void *ws,
+                         size_t ws_bytes, void *stream)
+{
+    uint64_t n_prod, n_cplx;
+    flags |= BSGPU_VIS_FULL_COV;
+    if (!vis_dtype_ok(dtype, flags, n_inputs) || (flags & BSGPU_VIS_COMPENSATE))
+        return BSGPU_ERR_ARG;
+    int rc = vis_check(n_freq, n_inputs, n_time, N, 0.0, n_prod, n_cplx);
+    if (rc) return rc;
+    if (!vis || !d_s2 || !ws) return BSGPU_ERR_ARG;
+    if (!aligned16(vis) || !aligned16(ws) || ((uintptr_t)d_s2 & 7u)) return BSGPU_ERR_ALIGN;
+    Geometry g{};
+    const VisOpts o = vis_opts(flags, n_freq, n_inputs, n_time);
+    WsLayout L = ws_layout(BSGPU_OP_REDUCE_PRECISION, g, (uint64_t)n_freq * n_inputs * n_time,
+                           n_prod, 0, o);
+    if (ws_bytes < L.total) return BSGPU_ERR_SPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(ws, 0, WS_HEADER, s) != cudaSuccess) return BSGPU_ERR_CUDA;
+    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, 0.0, dtype == BSGPU_VIS_I32, o,
+                             (uint64_t)n_freq);
+    return vis_prepare(vis, v, L, o, ws, n_freq, N, 0.0, s, d_s2);
 }
 
 int bsgpu_reorder_time(const void *in, void *out, uint64_t n_time, uint64_t n_series,
@@ -408,7 +473,8 @@ int bsgpu_compress_vis_ex(const void *vis, int dtype, int64_t n_freq, int64_t n_
                           size_t ws_bytes, void *stream)
 {
     uint64_t n_prod, n_cplx;
-    if (!vis_dtype_ok(dtype, flags) || (elem_size != 4 && elem_size != 8)) return BSGPU_ERR_ARG;
+    if (!vis_dtype_ok(dtype, flags, n_inputs) || (elem_size != 4 && elem_size != 8))
+        return BSGPU_ERR_ARG;
     int rc = vis_check(n_freq, n_inputs, n_time, N, f, n_prod, n_cplx);
     if (rc) return rc;
     Geometry g;
@@ -419,16 +485,15 @@ int bsgpu_compress_vis_ex(const void *vis, int dtype, int64_t n_freq, int64_t n_
         ((uintptr_t)d_block_offsets & 7u))
         return BSGPU_ERR_ALIGN;
     uint64_t n_auto = (uint64_t)n_freq * n_inputs * n_time;
-    const size_t n_ft = (flags & BSGPU_VIS_COMPENSATE) ? (size_t)n_freq * n_time : 0;
-    const bool tslow = (flags & BSGPU_VIS_TIME_SLOWEST) != 0;
-    WsLayout L = ws_layout(BSGPU_OP_COMPRESS_VIS, g, n_auto, n_prod, (uint64_t)n_time, n_ft, tslow);
+    const VisOpts o = vis_opts(flags, n_freq, n_inputs, n_time);
+    WsLayout L = ws_layout(BSGPU_OP_COMPRESS_VIS, g, n_auto, n_prod, (uint64_t)n_time, o);
     if (ws_bytes < L.total) return BSGPU_ERR_SPACE;
     if (level < 0 || level > 1) return BSGPU_ERR_ARG;
     if (out_cap < stream_bound(g)) return BSGPU_ERR_SPACE;
-    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32, tslow,
+    VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32, o,
                              (uint64_t)n_freq);
     cudaStream_t s = (cudaStream_t)stream;
-    rc = vis_prepare(vis, v, n_freq, n_inputs, n_time, N, f, s);
+    rc = vis_prepare(vis, v, L, o, ws, n_freq, N, f, s);
     if (rc) return rc;
     return compress_common(vis, g, level, out, out_cap, d_out_bytes, d_block_offsets, ws,
                            ws_bytes, stream, &v, L);

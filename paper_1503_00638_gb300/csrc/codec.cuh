@@ -164,13 +164,24 @@ BSG_D void write_chunk_header(uint8_t *out, uint64_t total, uint32_t block_bytes
 // ---------------------------------------------------------------------------
 // Precision reduction of complex samples (Sec. 3.2, Sec. 6 steps 1-3)
 // ---------------------------------------------------------------------------
+// Product index of (i, j), i <= j, in upper-triangle row-major order.
+BSG_D uint32_t ij_prod(const VisParams &P, uint32_t i, uint32_t j)
+{
+    return i * P.n_in - i * (i - 1) / 2 + (j - i);
+}
+
 // Round one complex sample (re, im bits) of product p = (i, j) at (f, t).
 BSG_D uint2 reduce_sample(uint2 v, uint32_t ij, uint32_t f, uint32_t t, const VisParams &P)
 {
     const uint32_t i = ij & 0xffffu, j = ij >> 16;
+    const bool is_auto = i == j;
+    if (P.qtab) {  // full covariance: q per component from the table
+        v.x = reduce_bits(v.x, vis_q_full(P, f, t, ij_prod(P, i, j), i, false), P.is_int);
+        if (!is_auto) v.y = reduce_bits(v.y, vis_q_full(P, f, t, ij_prod(P, i, j), i, true), P.is_int);
+        return v;
+    }
     const uint32_t row = f * P.n_in;
     const float Ai = __ldg(P.autos + (size_t)(row + i) * P.T + t);
-    const bool is_auto = i == j;
     // autos: s^2 = V_ii^2 / N, q = (2 c A_i) A_i, Im V_ii has no noise and stays;
     // crosses: s^2 = V_ii V_jj / (2N), q = (c A_i) A_j for both components
     const float Aj = is_auto ? Ai : __ldg(P.autos + (size_t)(row + j) * P.T + t);
@@ -223,19 +234,25 @@ BSG_D void reduce_run2(const uint4 *src, uint4 *dst, uint32_t c0, uint32_t ncplx
     const uint32_t q64 = 64 / P.T, r64 = 64 % P.T;
     for (uint32_t k = lane; k < ncplx / 2; k += 32) {
         const uint32_t ij = __ldg(P.pairs + p);
-        const uint32_t i = ij & 0xffffu, j = ij >> 16;
-        const uint32_t row = f * P.n_in;
-        const float2 Ai = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + i) * P.T + t));
-        const float2 Aj = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + j) * P.T + t));
-        const bool is_auto = i == j;
-        const float qa = __fmul_rn(__fmul_rn(vis_c(P, f, t, is_auto), Ai.x), Aj.x);
-        const float qb = __fmul_rn(__fmul_rn(vis_c(P, f, t + 1, is_auto), Ai.y), Aj.y);
         uint4 v = src[k];
-        v.x = reduce_bits(v.x, qa, P.is_int);
-        v.z = reduce_bits(v.z, qb, P.is_int);
-        if (!is_auto) {
-            v.y = reduce_bits(v.y, qa, P.is_int);
-            v.w = reduce_bits(v.w, qb, P.is_int);
+        if (P.qtab) {  // full covariance: per-component q from the table
+            const uint2 a = reduce_sample(make_uint2(v.x, v.y), ij, f, t, P);
+            const uint2 b = reduce_sample(make_uint2(v.z, v.w), ij, f, t + 1, P);
+            v = make_uint4(a.x, a.y, b.x, b.y);
+        } else {
+            const uint32_t i = ij & 0xffffu, j = ij >> 16;
+            const uint32_t row = f * P.n_in;
+            const float2 Ai = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + i) * P.T + t));
+            const float2 Aj = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + j) * P.T + t));
+            const bool is_auto = i == j;
+            const float qa = __fmul_rn(__fmul_rn(vis_c(P, f, t, is_auto), Ai.x), Aj.x);
+            const float qb = __fmul_rn(__fmul_rn(vis_c(P, f, t + 1, is_auto), Ai.y), Aj.y);
+            v.x = reduce_bits(v.x, qa, P.is_int);
+            v.z = reduce_bits(v.z, qb, P.is_int);
+            if (!is_auto) {
+                v.y = reduce_bits(v.y, qa, P.is_int);
+                v.w = reduce_bits(v.w, qb, P.is_int);
+            }
         }
         dst[k] = v;
         t += r64;
@@ -394,7 +411,7 @@ BSG_D void compress_prepare(const CodecArgs &a, uint32_t tile, uint8_t *in, uint
     // the block starts at a whole complex sample (B is a multiple of 8)
     const uint32_t c0 = (uint32_t)(((uint64_t)tile * a.B * a.es) >> 3);
     const uint32_t ncplx = Bb * a.es / 8;
-    if (a.vis.enabled && a.es == 4 && Bb % 32u == 0 && a.vis.T % 16u == 0) {
+    if (a.vis.enabled && !a.vis.qtab && a.es == 4 && Bb % 32u == 0 && a.vis.T % 16u == 0) {
         round_shuffle4_vis(in, tmp, Bb, c0, a.vis, lane);
         return;
     }

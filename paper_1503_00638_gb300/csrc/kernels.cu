@@ -112,7 +112,125 @@ __global__ void __launch_bounds__(256) vis_compensation_kernel(const void *__res
     }
 }
 
-// Standalone precision reduction: each warp rounds runs of 1024 samples.
+// Sec. 3.1's full covariance for small arrays (Eq. rad_full1-3) and the noise
+// of Eq. noise, s^2 = 1 / (C^-1)_kk, for every component of every (freq,
+// time) sample; q = fl32(12 f s^2) goes to P.qtab.  One CTA of 256 threads
+// per sample at a time (persistent), fp64 throughout: V in shared memory,
+// the lower triangle of C in this CTA's global scratch (M^2 doubles, L2
+// resident), a right-looking Cholesky C = L L^T with the pivot column staged
+// in shared memory, then W = L^-1 row by row, thread k owning column k
+// (stored transposed in the free upper triangle) and summing
+// (C^-1)_kk = sum_i W_ik^2.  A non-positive pivot leaves the sample
+// unrounded (q = 0).
+__global__ void __launch_bounds__(256) full_noise_kernel(const void *__restrict__ vis, VisParams P,
+                                                         uint32_t n_freq, double f, double N,
+                                                         double *scratch, double *s2_out)
+{
+    __shared__ double Vre[FULL_MAX_INPUTS][FULL_MAX_INPUTS], Vim[FULL_MAX_INPUTS][FULL_MAX_INPUTS];
+    __shared__ uint8_t ci[256], cj[256], ca[256];   // component -> (i, j, Re/Im)
+    __shared__ double col[256];
+    const uint32_t n = P.n_in, M = n * n, NP = P.P, tid = threadIdx.x, nt = blockDim.x;
+    double *A = scratch + (size_t)blockIdx.x * M * M;
+    float *qtab = const_cast<float *>(P.qtab);
+    for (uint32_t p = tid; p < NP; p += nt) {
+        const uint32_t ij = P.pairs[p], i = ij & 0xffffu, j = ij >> 16;
+        ci[p] = (uint8_t)i, cj[p] = (uint8_t)j, ca[p] = 0;
+        if (i < j) {
+            const uint32_t x = NP + p - i - 1;
+            ci[x] = (uint8_t)i, cj[x] = (uint8_t)j, ca[x] = 1;
+        }
+    }
+    for (uint64_t smp = blockIdx.x; smp < (uint64_t)n_freq * P.T; smp += gridDim.x) {
+        const uint32_t fr = (uint32_t)(smp / P.T), t = (uint32_t)(smp % P.T);
+        __syncthreads();
+        for (uint32_t p = tid; p < NP; p += nt) {
+            const uint32_t ij = P.pairs[p], i = ij & 0xffffu, j = ij >> 16;
+            const size_t at = vis_src(P, ((size_t)fr * NP + p) * P.T + t) * 2;
+            double re, im;
+            if (P.is_int) {
+                re = (double)(float)reinterpret_cast<const int32_t *>(vis)[at];
+                im = (double)(float)reinterpret_cast<const int32_t *>(vis)[at + 1];
+            } else {
+                re = reinterpret_cast<const float *>(vis)[at];
+                im = reinterpret_cast<const float *>(vis)[at + 1];
+            }
+            Vre[i][j] = re, Vim[i][j] = im, Vre[j][i] = re, Vim[j][i] = -im;
+        }
+        __syncthreads();
+        // C, lower triangle (r >= c).  With X = V_ig V_jh^*, Y = V_ih V_jg^*:
+        // Re,Re: Re(X + Y); Im,Im: Re(X - Y); Re ij,Im gh: Im(Y - X); all / 2N
+        for (uint32_t e = tid; e < M * M; e += nt) {
+            const uint32_t r = e / M, c = e - r * M;
+            if (c > r) continue;
+            uint32_t i = ci[r], j = cj[r], g = ci[c], h = cj[c];
+            const uint32_t a = ca[r], b = ca[c];
+            if (a == 1 && b == 0) {  // C_{Im ij, Re gh} = C_{Re gh, Im ij}
+                uint32_t x = i; i = g; g = x;
+                x = j; j = h; h = x;
+            }
+            const double xr = Vre[i][g] * Vre[j][h] + Vim[i][g] * Vim[j][h];
+            const double xi = Vim[i][g] * Vre[j][h] - Vre[i][g] * Vim[j][h];
+            const double yr = Vre[i][h] * Vre[j][g] + Vim[i][h] * Vim[j][g];
+            const double yi = Vim[i][h] * Vre[j][g] - Vre[i][h] * Vim[j][g];
+            double v;
+            if (a == 0 && b == 0) v = xr + yr;
+            else if (a == 1 && b == 1) v = xr - yr;
+            else v = yi - xi;
+            A[(size_t)r * M + c] = v / (2.0 * N);
+        }
+        __syncthreads();
+        bool ok = true;
+        for (uint32_t j = 0; j < M; j++) {
+            const double d = A[(size_t)j * M + j];
+            if (!(d > 0.0) || !isfinite(d)) {  // every thread sees the same value
+                ok = false;
+                break;
+            }
+            const double ljj = sqrt(d);
+            for (uint32_t i = j + tid; i < M; i += nt) {
+                const double x = i == j ? ljj : A[(size_t)i * M + j] / ljj;
+                A[(size_t)i * M + j] = x;
+                col[i] = x;
+            }
+            __syncthreads();
+            const uint32_t m = M - j - 1;
+            for (uint32_t e = tid; e < m * m; e += nt) {
+                const uint32_t ii = j + 1 + e / m, kk = j + 1 + e % m;
+                if (kk <= ii) A[(size_t)ii * M + kk] -= col[ii] * col[kk];
+            }
+            __syncthreads();
+        }
+        double acc = 0.0, wkk = 0.0;
+        const uint32_t k = tid;
+        if (ok) {
+            for (uint32_t i = 0; i < M; i++) {
+                for (uint32_t m = tid; m <= i; m += nt) col[m] = A[(size_t)i * M + m];
+                __syncthreads();
+                if (k <= i && k < M) {
+                    double w;
+                    if (k == i) {
+                        w = 1.0 / col[i];
+                        wkk = w;
+                    } else {
+                        double sum = col[k] * wkk;
+                        for (uint32_t m = k + 1; m < i; m++) sum += col[m] * A[(size_t)k * M + m];
+                        w = -sum / col[i];
+                        A[(size_t)k * M + i] = w;   // W_ik, transposed into the upper triangle
+                    }
+                    acc += w * w;
+                }
+                __syncthreads();
+            }
+        }
+        if (k < M) {
+            const double s2 = ok ? 1.0 / acc : 0.0;
+            qtab[smp * M + k] = ok ? (float)(12.0 * f * s2) : 0.0f;
+            if (s2_out) s2_out[smp * M + k] = s2;
+        }
+    }
+}
+
+// Standalone precision reduction: each warp rounds runs of 1024 samples.// Standalone precision reduction: each warp rounds runs of 1024 samples.
 __global__ void __launch_bounds__(256) reduce_precision_kernel(const uint2 *__restrict__ in,
                                                                uint2 *__restrict__ out,
                                                                uint64_t n_cplx, VisParams P)
@@ -552,6 +670,14 @@ cudaError_t launch_vis_compensation(const void *vis, const VisParams &P, uint32_
     const uint32_t grid = (uint32_t)(work < 8192 ? work : 8192);
     vis_compensation_kernel<<<grid ? grid : 1, 256, 0, s>>>(vis, P, const_cast<float *>(P.cft),
                                                             n_freq, f, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_full_noise(const void *vis, const VisParams &P, uint32_t n_freq, double f,
+                              double N, double *scratch, uint32_t grid, double *s2,
+                              cudaStream_t s)
+{
+    full_noise_kernel<<<grid ? grid : 1, 256, 0, s>>>(vis, P, n_freq, f, N, scratch, s2);
     return cudaGetLastError();
 }
 

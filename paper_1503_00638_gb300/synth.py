@@ -22,7 +22,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["VisConfig", "CONFIG_SMALL", "CONFIG_CHIME", "visibilities", "random_walk",
+__all__ = ["VisConfig", "CONFIG_SMALL", "CONFIG_CHIME", "visibilities", "visibilities_physical",
+           "random_walk",
            "n_products", "auto_product_index"]
 
 
@@ -109,6 +110,39 @@ def visibilities(cfg: VisConfig, freq_lo: int = 0, freq_hi: int | None = None) -
         w = np.where(cross[:, None], im, 0.0)
         out[k].real = v
         out[k].imag = w
+    return out
+
+
+def visibilities_physical(cfg: VisConfig) -> np.ndarray:
+    """A [freq][prod][time] complex64 cube whose every (freq, time) matrix is
+    a sample covariance of Gaussian voltages (so positive definite, as a
+    correlator's output is): true covariance R_ij = sqrt(A_i A_j) (rho
+    e^{i(th_i - th_j)} + (1 - rho) delta_ij), a point source of fraction
+    rho of the power drifting through the phases th_i(t) = 2 pi t i / (n T_s)
+    + th_i0, then V = L W L^H / N with L L^H = R and W a complex Wishart
+    matrix with N degrees of freedom (drawn by its Bartlett decomposition:
+    W = B B^H, B lower triangular, |B_ii|^2 ~ Gamma(N - i, 1), B_ij ~ CN(0, 1)
+    below the diagonal)."""
+    F, n, T = cfg.n_freq, cfg.n_inputs, cfg.n_time
+    N = int(cfg.n_samp)
+    g = np.random.Generator(np.random.PCG64([cfg.seed, 11]))
+    A = g.uniform(50.0, 150.0, size=(F, n))
+    th0 = g.uniform(0.0, 2 * np.pi, size=n)
+    ii, jj = np.triu_indices(n)
+    out = np.empty((F, ii.size, T), dtype=np.complex64)
+    for fr in range(F):
+        sa = np.sqrt(A[fr])
+        for t in range(T):
+            u = np.exp(1j * (2 * np.pi * t * np.arange(n) / (n * cfg.t_sky) + th0))
+            R = np.outer(sa * u, np.conj(sa * u)) * cfg.rho + np.diag(A[fr]) * (1 - cfg.rho)
+            L = np.linalg.cholesky(R)
+            B = np.zeros((n, n), dtype=np.complex128)
+            B[np.diag_indices(n)] = np.sqrt(g.gamma(N - np.arange(n), 1.0))
+            lo = np.tril_indices(n, -1)
+            B[lo] = (g.standard_normal(lo[0].size) + 1j * g.standard_normal(lo[0].size)) / np.sqrt(2)
+            LB = L @ B
+            V = LB @ LB.conj().T / N
+            out[fr, :, t] = V[ii, jj]
     return out
 
 

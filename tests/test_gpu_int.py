@@ -145,7 +145,7 @@ def test_ex_argument_errors(bs):
     s = torch.cuda.current_stream().cuda_stream
     rp = lib.bsgpu_reduce_precision_ex
     assert rp(p, q, 2, 2, 2, 16, 1e3, 0.1, 0, w, ws.numel(), s) == bs.ERR_ARG      # dtype
-    assert rp(p, q, 1, 2, 2, 16, 1e3, 0.1, 4, w, ws.numel(), s) == bs.ERR_ARG      # flags
+    assert rp(p, q, 1, 2, 2, 16, 1e3, 0.1, 8, w, ws.numel(), s) == bs.ERR_ARG      # flags
     assert rp(p, q, 1, 2, 2, 16, 1e3, 0.1, 1, w, 64, s) == bs.ERR_SPACE            # workspace
     cap = 1 << 16
     buf = torch.empty(cap, dtype=torch.uint8, device="cuda")

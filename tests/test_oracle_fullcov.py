@@ -111,9 +111,11 @@ def test_full_rounding_matches_plain_when_uncorrelated(orc):
 
 
 def test_full_rounding_is_finer_with_a_bright_sky(orc):
+    # a physical cube (positive definite samples) dominated by a source
     cfg = synth.VisConfig(2, 4, 8, 2 ** 12, 0.1, seed=4, rho=0.9)
-    v = synth.visibilities(cfg)
+    v = synth.visibilities_physical(cfg)
     x = v.view(np.float32).astype(np.float64)
     full = orc.reduce_precision_full(v, cfg.n_samp, cfg.f).view(np.float32)
     plain = orc.reduce_precision_c64(v, cfg.n_samp, cfg.f).view(np.float32)
+    assert np.any(full != x)          # the full-covariance path did round
     assert np.abs(full - x).sum() < np.abs(plain - x).sum()

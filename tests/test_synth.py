@@ -79,3 +79,21 @@ def test_torch_generators_follow_the_recipe():
     w = synth.random_walk_torch(10000, 4, seed=1, device="cpu").view(torch.int32).numpy()
     d = np.diff(w.astype(np.int64))
     assert set(np.abs(d).tolist()) <= {1, 2, 4, 8, 16, 32, 64}
+
+
+def test_physical_visibilities_are_sample_covariances():
+    # the mean over many (freq, time) draws of the same R approaches R, and
+    # every sample matrix is positive definite
+    cfg = synth.VisConfig(1, 3, 4000, 64, 0.1, seed=1, rho=0.6, t_sky=1e12)  # no drift
+    v = synth.visibilities_physical(cfg)
+    n = 3
+    ii, jj = np.triu_indices(n)
+    mats = np.zeros((cfg.n_time, n, n), dtype=np.complex128)
+    mats[:, ii, jj] = v[0].T
+    mats[:, jj, ii] = np.conj(v[0].T)
+    assert np.all(np.linalg.eigvalsh(mats).min(axis=1) > 0)
+    mean = mats.mean(axis=0)
+    A = np.real(np.diag(mean))
+    # |R_ij| = rho sqrt(A_i A_j) off the diagonal
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        assert abs(abs(mean[i, j]) / np.sqrt(A[i] * A[j]) - 0.6) < 0.02
