@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(32, 16) compress_batch_kernel(const __grid_con
                 cs = lz4_encode_warp<1, L::HBITS>(tmp, S, Bb / 8, slot0 + 4,
                                                   static_cast<uint16_t *>(scratch));
             else if (S % 128u == 0)
-                cs = lz4_encode_bitmap_fast(tmp, S, Bb / 8, slot0 + 4);
+                cs = lz4_encode_bitmap_fast(tmp, S, Bb / 8, slot0 + 4,
+                                            static_cast<uint32_t *>(scratch));
             else
                 cs = lz4_encode_bitmap(tmp, S, Bb / 8, slot0 + 4, static_cast<uint32_t *>(scratch));
             if (cs == 0xffffffffu) {  // progress guard (not reachable for valid sizes)

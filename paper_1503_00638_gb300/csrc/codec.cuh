@@ -509,7 +509,8 @@ struct FastPlan {
     static constexpr uint32_t MAXB = 8192;
     static constexpr uint32_t TMP = r16(MAXB + 16);  // staged block, then its bit-rows
     static constexpr int HBITS = 11;
-    static constexpr uint32_t SCR = LEVEL >= 1 ? (2u << HBITS) : 2u * 4u * (MAXB / 128u + 2u);
+    // level 1: the hash table; level 0: the fast encoder's bitmaps and tables
+    static constexpr uint32_t SCR = LEVEL >= 1 ? (2u << HBITS) : LZ4_FAST_SCRATCH;
     static constexpr uint32_t BYTES = TMP + r16(SCR) + 16;
 };
 

@@ -391,7 +391,8 @@ __global__ void __launch_bounds__(32, 16) compress_fast_kernel(const __grid_cons
         __syncwarp();
         uint32_t cs;
         if (LEVEL == 0 && (Bb * ES) % 128u == 0) {
-            cs = lz4_encode_bitmap_fast(tmp, Bb * ES, Bb / 8, slot0 + 4);
+            cs = lz4_encode_bitmap_fast(tmp, Bb * ES, Bb / 8, slot0 + 4,
+                                        static_cast<uint32_t *>(scratch));
             if (lane == 0) put_be32(slot0, cs);
             __syncwarp();
         } else {

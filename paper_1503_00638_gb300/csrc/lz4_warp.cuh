@@ -65,6 +65,38 @@ BSG_D void warp_copy(uint8_t *dst, uint32_t d, const uint8_t *src, uint32_t s, u
     for (uint32_t w = (a0 >> 2) + lane; w < (a1 >> 2); w += 32) d32[w] = ld32u(src, s + 4 * w - d);
 }
 
+// Copy of up to 32 independent byte ranges, range k (k < n) held by lane k as
+// (source offset a, destination offset d, length len): four ranges at a time,
+// eight lanes each (head bytes up to dst's word boundary, whole words from
+// funnel-shifted loads, ragged end), so that short runs do not each cost a
+// whole-warp pass.  The ranges must not overlap each other or the sources.
+BSG_D void warp_copy_ranges(uint8_t *dst, const uint8_t *src, uint32_t n, uint32_t a, uint32_t d,
+                            uint32_t len, uint32_t lane)
+{
+#ifdef BSG_WARP_EMU
+    emu_check_aligned4(dst);
+    emu_check_aligned4(src);
+#endif
+    const uint32_t g = lane >> 3, sl = lane & 7u;
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t base = 0; base < n; base += 4) {
+        const uint32_t k = base + g;
+        const uint32_t ak = __shfl_sync(FULL, a, k & 31u), dk = __shfl_sync(FULL, d, k & 31u);
+        const uint32_t lk0 = __shfl_sync(FULL, len, k & 31u);
+        const uint32_t lk = k < n ? lk0 : 0u;
+        if (lk == 0) continue;
+        if (lk <= 8) {
+            if (sl < lk) dst[dk + sl] = src[ak + sl];
+            continue;
+        }
+        const uint32_t a0 = (dk + 3u) & ~3u, a1 = (dk + lk) & ~3u;
+        const uint32_t head = a0 - dk, tail = dk + lk - a1;
+        if (sl < head) dst[dk + sl] = src[ak + sl];
+        if (sl >= 4 && sl - 4 < tail) dst[a1 + sl - 4] = src[ak + (a1 - dk) + sl - 4];
+        for (uint32_t w = (a0 >> 2) + sl; w < (a1 >> 2); w += 8) d32[w] = ld32u(src, ak + 4 * w - dk);
+    }
+}
+
 // Warp fill of len bytes at dst[d..] with the byte b.
 BSG_D void warp_fill(uint8_t *dst, uint32_t d, uint32_t b, uint32_t len, uint32_t lane)
 {
@@ -406,36 +438,62 @@ BSG_D uint32_t lz4_encode_bitmap(const uint8_t *src, uint32_t S, uint32_t rowlen
     return o;
 }
 
-// First set bit at or after position `from` (and at most `to`) of a bitmap of
-// up to 2048 bits held two words per lane (word q = lane + 32 j in w[j]);
-// ~0u if none.
-BSG_D uint32_t regmap_first_set(const uint32_t (&w)[2], uint32_t from, uint32_t to, uint32_t lane)
+// Shared scratch of lz4_encode_bitmap_fast: four 64-word bitmaps and three
+// "next non-zero word" tables of 65 entries.
+constexpr uint32_t LZ4_FAST_SCRATCH = 4u * 64u * 4u + 3u * 80u;
+
+// First set bit in [from, to] of a 64-word shared bitmap, through its table
+// nnz[k] = first k' >= k with bm[k'] != 0 (64 when none): one or two
+// broadcast loads instead of a warp vote.  ~0u when none.
+BSG_D uint32_t smap_first_set(const uint32_t *bm, const uint8_t *nnz, uint32_t from, uint32_t to)
 {
-#pragma unroll
-    for (int j = 0; j < 2; j++) {
-        const uint32_t q = lane + 32u * j;
-        uint32_t m = w[j];
-        const int lo = (int)from - (int)(32 * q), hi = (int)to - (int)(32 * q);
-        if (lo > 0) m = lo >= 32 ? 0u : (m & (~0u << lo));
-        if (hi < 31) m = hi < 0 ? 0u : (m & ((2u << hi) - 1u));
-        const uint32_t b = __ballot_sync(FULL, m != 0);
-        if (b) {
-            const uint32_t fl = __ffs(b) - 1;
-            const uint32_t mm = __shfl_sync(FULL, m, fl);
-            return 32u * (fl + 32u * j) + (__ffs(mm) - 1);
-        }
+    if (from > to) return ~0u;
+    uint32_t k = from >> 5;
+    uint32_t m = bm[k] & (~0u << (from & 31u));
+    if (m == 0) {
+        k = nnz[k + 1];
+        if (k >= 64) return ~0u;
+        m = bm[k];
     }
-    return ~0u;
+    const uint32_t w = 32u * k + (uint32_t)(__ffs(m) - 1);
+    return w <= to ? w : ~0u;
+}
+
+// A lane's two words (k = lane, lane + 32) of a 64-word bitmap into shared
+// memory with its next-non-zero table.
+BSG_D void smap_store(uint32_t *bm, uint8_t *nnz, const uint32_t (&w)[2], uint32_t lane)
+{
+    bm[lane] = w[0];
+    bm[lane + 32] = w[1];
+    const uint32_t b0 = __ballot_sync(FULL, w[0] != 0), b1 = __ballot_sync(FULL, w[1] != 0);
+#pragma unroll
+    for (uint32_t j = 0; j < 2; j++) {
+        const uint32_t k = lane + 32u * j;
+        // set words at or after k: bits k.. of the 64-bit mask b1:b0
+        const uint32_t lo = j == 0 ? (b0 >> lane) : 0u;
+        const uint32_t hi = j == 0 ? b1 : (b1 >> lane);
+        uint32_t nk;
+        if (j == 0)
+            nk = lo ? k + (uint32_t)(__ffs(lo) - 1) : (hi ? 32u + (uint32_t)(__ffs(hi) - 1) : 64u);
+        else
+            nk = hi ? k + (uint32_t)(__ffs(hi) - 1) : 64u;
+        nnz[k] = (uint8_t)nk;
+    }
+    if (lane == 0) nnz[64] = 64;
 }
 
 // Level-0 encoder for the fast path (S a multiple of 128, at most 8192): the
-// same parse as lz4_encode_bitmap, with the equality bitmaps kept in
-// registers (two words per lane) and the sequences emitted 32 at a time in
-// parallel: the parse collects up to 32 (literal start, match start, match
-// length, offset) descriptors, one per lane; a warp scan of their encoded
-// lengths places them; each lane writes its own token, length and offset
-// bytes; the literal runs are copied one after another by the whole warp.
-BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t rowlen, uint8_t *dst)
+// same parse as lz4_encode_bitmap.  The equality bitmaps are built in
+// registers (two words per lane) and kept in shared memory `scr`
+// (LZ4_FAST_SCRATCH bytes, 4-byte aligned) with next-non-zero tables, so
+// that each step of the (inherently sequential) parse is a few broadcast
+// loads.  The sequences are emitted 32 at a time in parallel: the parse
+// collects up to 32 (literal start, match start, match length, offset)
+// descriptors, one per lane; a warp scan of their encoded lengths places
+// them; each lane writes its own token, length and offset bytes; the literal
+// runs are copied one after another by the whole warp.
+BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t rowlen, uint8_t *dst,
+                                      uint32_t *scr)
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
@@ -478,8 +536,16 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
         Crow[j] = Erow[j] & ((Erow[j] >> 1) | (nr << 31));
         Crun[j] = Erun[j] & ((Erun[j] >> 1) | (nu << 31));
     }
-    uint32_t Cany[2] = {Crow[0] | Crun[0], Crow[1] | Crun[1]};
-    uint32_t Zrow[2] = {~Erow[0], ~Erow[1]}, Zrun[2] = {~Erun[0], ~Erun[1]};
+    const uint32_t Cany[2] = {Crow[0] | Crun[0], Crow[1] | Crun[1]};
+    const uint32_t Zrow[2] = {~Erow[0], ~Erow[1]}, Zrun[2] = {~Erun[0], ~Erun[1]};
+    uint32_t *sCany = scr, *sCrow = scr + 64, *sZrow = scr + 128, *sZrun = scr + 192;
+    uint8_t *nCany = reinterpret_cast<uint8_t *>(scr + 256), *nZrow = nCany + 80, *nZrun = nZrow + 80;
+    smap_store(sCany, nCany, Cany, lane);
+    smap_store(sZrow, nZrow, Zrow, lane);
+    smap_store(sZrun, nZrun, Zrun, lane);
+    sCrow[lane] = Crow[0];
+    sCrow[lane + 32] = Crow[1];
+    __syncwarp();
 
     uint32_t anchor = 0, o = 0;
     if (S >= LZ4_MFLIMIT + 1) {
@@ -493,17 +559,16 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
             uint32_t my_anchor = 0, my_mp = 0, my_len = 0, my_off = 0, n = 0;
             for (; n < 32; n++) {
                 const uint32_t w0 = (pos + 3) / 4;
-                const uint32_t w = w0 <= wlim ? regmap_first_set(Cany, w0, wlim, lane) : ~0u;
+                const uint32_t w = smap_first_set(sCany, nCany, w0, wlim);
                 if (w == ~0u) {
                     more = false;
                     break;
                 }
                 // the previous bit-row wins a tie
-                const uint32_t qi = w >> 5, bit = w & 31u;
-                const uint32_t crw = __shfl_sync(FULL, (qi >> 5) ? Crow[1] : Crow[0], qi & 31u);
-                const uint32_t isrow = (crw >> bit) & 1u;
+                const uint32_t isrow = (sCrow[w >> 5] >> (w & 31u)) & 1u;
                 const uint32_t off = isrow ? rowlen : 4u;
-                uint32_t wz = regmap_first_set(isrow ? Zrow : Zrun, w + 2, cap - 1, lane);
+                uint32_t wz = isrow ? smap_first_set(sZrow, nZrow, w + 2, cap - 1)
+                                    : smap_first_set(sZrun, nZrun, w + 2, cap - 1);
                 if (wz == ~0u) wz = cap;
                 uint32_t len = 4 * (wz - w);
                 if (4 * wz < matchlimit) {
@@ -554,13 +619,7 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
                 for (uint32_t k = 0; k < nml; k++)
                     dst[tr + 2 + k] = k + 1 < nml ? 255u : (uint8_t)((ML - 15) % 255u);
             }
-            for (uint32_t k = 0; k < n; k++) {
-                const uint32_t lk = __shfl_sync(FULL, LL, k);
-                if (lk == 0) continue;
-                const uint32_t ak = __shfl_sync(FULL, my_anchor, k);
-                const uint32_t dk = __shfl_sync(FULL, base + 1 + nll, k);
-                warp_copy(dst, dk, src, ak, lk, lane);
-            }
+            warp_copy_ranges(dst, src, n, my_anchor, base + 1 + nll, LL, lane);
             o += __shfl_sync(FULL, incl, 31);
             anchor = pos;
         }

@@ -18,6 +18,7 @@ int32_t orc_round_int(int32_t x, int k);
 using namespace bsg;
 alignas(16) static uint8_t A[70000], Bf[70000], C[70000], T[65536];
 alignas(16) static uint8_t D2[70000];
+alignas(16) static uint32_t FS[LZ4_FAST_SCRATCH / 4];
 
 static int test_transpose(std::mt19937 &rng)
 {
@@ -208,7 +209,7 @@ static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc
                 uint32_t cs3 = 0;
                 memset(E, 0xCD, S + 64);
                 run_warp([&] {
-                    uint32_t o = lz4_encode_bitmap_fast(A, S, rows[ci], E);
+                    uint32_t o = lz4_encode_bitmap_fast(A, S, rows[ci], E, FS);
                     if (threadIdx.x == 0) cs3 = o;
                 });
                 if (cs3 != cs || memcmp(E, Bf, cs)) {
