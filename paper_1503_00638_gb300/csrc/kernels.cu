@@ -342,7 +342,7 @@ uint32_t compress_fast_blocks_per_sm(int level, uint32_t es)
 // published theirs, so the look-back rarely waits.  GEN (4-byte elements of a
 // cube only): int32 components or a compensated c (see round_group).
 template <int LEVEL, int ES, bool GEN>
-__global__ void __launch_bounds__(32, 16) compress_fast_kernel(const __grid_constant__ CodecArgs a)
+__global__ void __launch_bounds__(32, 20) compress_fast_kernel(const __grid_constant__ CodecArgs a)
 {
     using L = FastPlan<LEVEL>;
     extern __shared__ __align__(128) uint8_t sm[];

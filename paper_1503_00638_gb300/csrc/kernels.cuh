@@ -103,7 +103,7 @@ uint32_t compress_fast_smem_bytes(int level);
 uint32_t compress_fast_blocks_per_sm(int level, uint32_t es);
 // staging slot size of the fast path and the warp count its slots cover
 constexpr uint32_t FAST_SLOT_BYTES = 8304;
-constexpr uint32_t FAST_MAX_WARPS = 2560;
+constexpr uint32_t FAST_MAX_WARPS = 3072;
 cudaError_t launch_compress_small(const CodecArgs &a, cudaStream_t s);
 cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s);
 cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, cudaStream_t s);

@@ -62,6 +62,13 @@ BSG_D void warp_copy(uint8_t *dst, uint32_t d, const uint8_t *src, uint32_t s, u
     if (lane < head) dst[d + lane] = src[s + lane];
     if (lane >= 28 && lane - 28 < tail) dst[a1 + lane - 28] = src[s + (a1 - d) + lane - 28];
     uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    if (((d - s) & 3u) == 0) {
+        // source and destination share their word alignment: plain word copy
+        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
+        const int sh = (int)(s - d) / 4;  // signed word distance (exact: a multiple of 4)
+        for (uint32_t w = (a0 >> 2) + lane; w < (a1 >> 2); w += 32) d32[w] = s32[(int)w + sh];
+        return;
+    }
     for (uint32_t w = (a0 >> 2) + lane; w < (a1 >> 2); w += 32) d32[w] = ld32u(src, s + 4 * w - d);
 }
 
@@ -567,8 +574,8 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
                 // the previous bit-row wins a tie
                 const uint32_t isrow = (sCrow[w >> 5] >> (w & 31u)) & 1u;
                 const uint32_t off = isrow ? rowlen : 4u;
-                uint32_t wz = isrow ? smap_first_set(sZrow, nZrow, w + 2, cap - 1)
-                                    : smap_first_set(sZrun, nZrun, w + 2, cap - 1);
+                uint32_t wz = smap_first_set(isrow ? sZrow : sZrun, isrow ? nZrow : nZrun, w + 2,
+                                             cap - 1);
                 if (wz == ~0u) wz = cap;
                 uint32_t len = 4 * (wz - w);
                 if (4 * wz < matchlimit) {
@@ -577,24 +584,25 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
                     if (eq > matchlimit - 4 * wz) eq = matchlimit - 4 * wz;
                     len += eq;
                 }
-                uint32_t mp = 4 * w;
-                // back up over up to 3 equal bytes (never before the literal anchor)
-                if (mp > pos && mp > off) {
-                    const uint32_t x = ld32u(src, mp - 4) ^ ld32u(src, mp - 4 - off);
-                    uint32_t back = (x ? __clz(x) : 32u) >> 3;
-                    if (back > 3) back = 3;
-                    if (back > mp - pos) back = mp - pos;
-                    if (back > mp - off) back = mp - off;
-                    mp -= back;
-                    len += back;
-                }
+                const uint32_t mp = 4 * w;
                 if (lane == n) {
                     my_anchor = pos;
                     my_mp = mp;
                     my_len = len;
                     my_off = off;
                 }
-                pos = mp + len;
+                pos = mp + len;  // the backward extension below leaves the match end alone
+            }
+            // each lane backs its match up over up to 3 equal bytes (never
+            // before its literal anchor), off the parse's critical path
+            if (lane < n && my_mp > my_anchor && my_mp > my_off) {
+                const uint32_t x = ld32u(src, my_mp - 4) ^ ld32u(src, my_mp - 4 - my_off);
+                uint32_t back = (x ? __clz(x) : 32u) >> 3;
+                if (back > 3) back = 3;
+                if (back > my_mp - my_anchor) back = my_mp - my_anchor;
+                if (back > my_mp - my_off) back = my_mp - my_off;
+                my_mp -= back;
+                my_len += back;
             }
             // emit the n sequences of this batch
             const bool mine = lane < n;
@@ -635,6 +643,15 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
 BSG_D bool lz4_read_len(const uint8_t *src, uint32_t clen, uint32_t &ip, uint32_t &len,
                         uint32_t lane)
 {
+    // nearly always one byte below 255: no warp vote
+    if (ip < clen) {
+        const uint32_t b0 = src[ip];
+        if (b0 != 255u) {
+            len += b0;
+            ip += 1;
+            return true;
+        }
+    }
     for (uint32_t g = 0; g <= clen; g += 32) {
         uint32_t idx = ip + lane;
         uint32_t b = idx < clen ? src[idx] : 0u;
