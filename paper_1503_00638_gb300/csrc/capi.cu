@@ -181,6 +181,8 @@ VisParams vis_params(const WsLayout &L, void *ws, uint64_t n_in, uint64_t n_time
     v.n_in = (uint32_t)n_in;
     v.T = (uint32_t)n_time;
     v.P = (uint32_t)n_prod;
+    v.dT = fastdiv_init(v.T);
+    v.dP = fastdiv_init(v.P);
     v.qT = (uint32_t)(32 / n_time);
     v.rT = (uint32_t)(32 % n_time);
     v.c = (float)(6.0 * f / N);   // q = 12 f s^2 with s^2 = A_i A_j / (2N)

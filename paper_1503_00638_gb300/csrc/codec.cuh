@@ -564,9 +564,9 @@ struct VisGroupRound {
     {
         const uint32_t rot = g & 7u;
         const uint32_t cg = c_blk + 16 * g;
-        const uint32_t fp = cg / P->T;
+        const uint32_t fp = fastdiv(cg, P->dT);
         const uint32_t t0 = cg - fp * P->T;
-        const uint32_t f = fp / P->P;
+        const uint32_t f = fastdiv(fp, P->dP);
         const uint32_t p = fp - f * P->P;
         const uint32_t ij = __ldg(P->pairs + p);
         const uint32_t i = ij & 0xffffu, j = ij >> 16;

@@ -160,6 +160,37 @@ BSG_HD int32_t round_int_pow2(int32_t x, int k)
     return (int32_t)y;
 }
 
+// Division by an invariant 32-bit divisor d >= 1 through a multiply-high
+// (the round-up method for division by invariant integers): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (t + ((n - t) >> 1)) >> (l - 1) where t = mulhi(m, n), exact for
+// every 32-bit n; d = 1 is kept apart (l - 1 would be negative).
+struct FastDiv {
+    uint32_t m, sh, d;
+};
+
+inline FastDiv fastdiv_init(uint32_t d)
+{
+    FastDiv f{0u, 0u, d};
+    if (d <= 1) return f;
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < d) l++;
+    f.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+    f.sh = l - 1;
+    return f;
+}
+
+BSG_HD uint32_t fastdiv(uint32_t n, const FastDiv &f)
+{
+    if (f.d == 1) return n;
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(f.m, n);
+#else
+    const uint32_t t = (uint32_t)(((uint64_t)f.m * n) >> 32);
+#endif
+    return (t + ((n - t) >> 1)) >> f.sh;
+}
+
 // granularity exponent k = max{k : 4^k < q} from q's bits (see magic_bits)
 BSG_HD int granularity_k(uint32_t Q) { return (int)((Q + 0x007fffffu) >> 24) - 64; }
 

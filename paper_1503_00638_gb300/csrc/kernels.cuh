@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 namespace bsg {
 
 // Visibility-cube geometry for the precision reduction (Sec. 3).
@@ -20,6 +22,7 @@ struct VisParams {
     uint32_t FP;            // n_freq n_prod (series of T samples)
     const float *qtab;      // full-covariance q per component [n_freq][T][M], or null
     uint32_t M;             // components per sample (n_in^2) when qtab is set
+    FastDiv dT, dP;         // division by T and by P
     int enabled;
 };
 

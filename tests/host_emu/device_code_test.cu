@@ -55,6 +55,32 @@ static int test_granularity_bits(std::mt19937 &rng)
     return bad;
 }
 
+// multiply-high division against '/', over edge and random numerators
+static int test_fastdiv(std::mt19937 &rng)
+{
+    int bad = 0;
+    const uint32_t ds[] = {1, 2, 3, 5, 7, 16, 64, 136, 1000, 8256, 33024, 65535, 65536, 65537,
+                           (1u << 31) - 1, 1u << 31, (1u << 31) + 1, 0xfffffffeu, 0xffffffffu};
+    for (uint32_t d : ds) {
+        const FastDiv f = fastdiv_init(d);
+        const uint32_t ns[] = {0, 1, d - 1, d, d + 1, 2 * d - 1, 2 * d, 0x7fffffffu, 0x80000000u,
+                               0xfffffffeu, 0xffffffffu};
+        for (uint32_t n : ns) bad += fastdiv(n, f) != n / d;
+        for (int it = 0; it < 20000; it++) {
+            const uint32_t n = (uint32_t)rng();
+            bad += fastdiv(n, f) != n / d;
+        }
+    }
+    for (int it = 0; it < 20000; it++) {
+        const uint32_t d = (uint32_t)rng() >> (rng() % 32);
+        if (!d) continue;
+        const FastDiv f = fastdiv_init(d);
+        const uint32_t n = (uint32_t)rng();
+        bad += fastdiv(n, f) != n / d;
+    }
+    return bad;
+}
+
 // integer rounding against the oracle's, over random and extreme values
 static int test_round_int(std::mt19937 &rng)
 {
@@ -254,6 +280,7 @@ int main()
     std::mt19937 rng(7);
     int t = test_transpose(rng), g = test_granularity_bits(rng), s = test_shuffles(rng);
     g += test_round_int(rng);
+    g += test_fastdiv(rng);
     s += test_inplace_unshuffle(rng);
     printf("in-place shapes %d\n", g_inplace_cases);
     if (g_inplace_cases != 20) s++;  // es 2: 7 shapes, es 4: 7, es 8: 6
