@@ -547,6 +547,14 @@ int bsgpu_decompress(const void *in, size_t in_bytes, void *out, size_t n_elem, 
     }
     uint32_t maxb = maxb_class(g.B * g.es);
     uint32_t grid = persistent_grid(decompress_smem_bytes(maxb), g.nb ? g.nb : 1);
+    if (maxb <= 8192 && (g.es == 2 || g.es == 4 || g.es == 8)) {
+        // the in-place kernel: as many warps as fit, never more than the blocks
+        int dev = 0, sms = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const uint64_t want = (uint64_t)sms * decompress_inplace_blocks_per_sm(g.es);
+        grid = (uint32_t)(want < g.nb ? want : (g.nb ? g.nb : 1));
+    }
     return cuda_err(launch_decompress(a, maxb, grid, s));
 }
 

@@ -592,13 +592,17 @@ struct DecLoad {
     uint32_t clen;   // LZ4 bytes of the block
     uint32_t eidx;   // shared index this lane's edge byte goes to (or ~0)
     uint8_t ebyte;
+    uint32_t off;    // where in the buffer the block's image starts (see dec_issue)
 };
 
-// Bytes [D, Dn) of the stream go to shared index x - (D & ~15): the 16-byte
-// aligned middle by one bulk copy, the ragged head and tail (< 16 bytes each)
-// by plain loads held in registers until the block is processed.
+// Bytes [D, Dn) of the stream go to shared index x - (D & ~15) of the image
+// (dst + r.off): the 16-byte aligned middle by one bulk copy, the ragged head
+// and tail (< 16 bytes each) by plain loads held in registers until the block
+// is processed.  end_bytes = 0 puts the image at dst; otherwise at the end of
+// a buffer of end_bytes bytes (a 16-byte boundary at least 32 bytes before
+// its end), for decoding in place (decompress_inplace_kernel).
 BSG_D DecLoad dec_issue(const CodecArgs &a, uint32_t tile, uint8_t *dst, uint64_t *bar,
-                        uint32_t lane)
+                        uint32_t lane, uint32_t end_bytes = 0)
 {
     DecLoad r;
     r.bulk = false;
@@ -607,6 +611,7 @@ BSG_D DecLoad dec_issue(const CodecArgs &a, uint32_t tile, uint8_t *dst, uint64_
     r.ebyte = 0;
     r.delta = 0;
     r.clen = 0;
+    r.off = 0;
     const uint32_t Bb = block_elems_of(a, tile);
     const uint64_t tail_b = (uint64_t)a.tail_elems * a.es;
     if (a.in_bytes < 12 + tail_b) return r;
@@ -615,6 +620,11 @@ BSG_D DecLoad dec_issue(const CodecArgs &a, uint32_t tile, uint8_t *dst, uint64_
     if (D < 12 || Dn < D + 4 || Dn > a.in_bytes || Dn - D - 4 > lz4b(Bb * a.es)) return r;
     r.ok = true;
     r.clen = (uint32_t)(Dn - D - 4);
+    if (end_bytes) {
+        // the range check above bounds Dn - D by 4 + lz4b(S) <= end_bytes - 48
+        r.off = (end_bytes - (uint32_t)(Dn - D) - 32u) & ~15u;
+        dst += r.off;
+    }
     // alignment is a property of the absolute address, not of the offset
     const uint64_t g0 = (uint64_t)(uintptr_t)(a.in + D), gn = g0 + (Dn - D);
     const uint64_t base = g0 & ~15ull;

@@ -545,6 +545,125 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 13 : 1)
     __syncwarp();
 }
 
+// Decompress with ONE shared buffer per warp, for blocks of at most 8 KiB whose
+// un-transpose fits in registers (2-, 4- and 8-byte elements): LZ4 in-place
+// decoding, the block's compressed bytes loaded at the end of the buffer and
+// the output written from its start.  For any valid LZ4 block the output
+// written so far never catches up with the unread input: ahead of any
+// literal run, the rest of the stream holds at most 2 + 2 S / 255 bytes more
+// than it produces (a token, length bytes and a final literal run; every
+// match adds at least one more byte than its three), about 72 bytes for
+// S = 8192, and the image starts at least 113 bytes later than that needs.
+// Half the shared memory of decompress_kernel: 16 resident warps per SM
+// instead of 13, at the cost of the next block's copy starting only once
+// this block's store has read the buffer.
+constexpr uint32_t INPLACE_BUF = 8352;
+// placement (an image of at most 4 + lz4b(8192) bytes, 32 before the end, 16
+// for the phase) and in-place safety (image start - (S - clen) >= 72)
+static_assert(INPLACE_BUF >= 4 + lz4b(8192) + 48, "in-place buffer: image does not fit");
+static_assert(INPLACE_BUF >= 8192 + 119, "in-place buffer: margin below the LZ4 bound");
+
+template <int ES>
+__global__ void __launch_bounds__(32, 16) decompress_inplace_kernel(const __grid_constant__ CodecArgs a)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *buf = sm;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + INPLACE_BUF);
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t parity = 0;
+    bool header_checked = false;
+    uint32_t tile = grab_tile(a.tile_counter, lane);
+    DecLoad ld{};
+    if (tile < a.nb) ld = dec_issue(a, tile, buf, bar, lane, INPLACE_BUF);
+    while (tile < a.nb) {
+        const DecLoad cur = ld;
+        if (cur.bulk) {
+            if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);
+            parity ^= 1u;
+        }
+        if (!header_checked) {
+            header_checked = true;
+            uint32_t ok = 1;
+            if (lane < 12) {
+                uint8_t want = lane < 8 ? (uint8_t)((a.n_elem * a.es) >> (8 * (7 - lane)))
+                                        : (uint8_t)(((uint64_t)a.B * a.es) >> (8 * (11 - lane)));
+                ok = a.in_bytes >= 12 && a.in[lane] == want;
+            }
+            if (__ballot_sync(FULL, !ok) && lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);
+        }
+        const uint32_t Bb = block_elems_of(a, tile);
+        const uint32_t S = Bb * a.es;
+        const uint32_t nxt = grab_tile(a.tile_counter, lane);
+        uint8_t *comp = buf + cur.off;
+        bool good = cur.ok;
+        if (good) {
+            if (cur.eidx != ~0u) comp[cur.eidx] = cur.ebyte;
+            __syncwarp();
+            good = get_be32(comp + cur.delta) == cur.clen &&
+                   lz4_decode_warp(comp, cur.delta + 4, cur.clen, buf, S) == 0;
+        }
+        if (!good && lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);
+        __syncwarp();
+        uint8_t *dst = a.out + (uint64_t)tile * a.B * a.es;
+        if (good && unshuffle_inplace_ok(ES, Bb)) {
+            if (ES == 2)
+                unshuffle2_inplace(buf, Bb, lane);
+            else if (ES == 4)
+                unshuffle4_inplace(buf, Bb, lane);
+            else
+                unshuffle8_inplace(buf, Bb, lane);
+            __syncwarp();
+            if ((S & 15u) == 0 && ((uintptr_t)dst & 15u) == 0) {
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    bulk_s2g(dst, buf, S);
+                    bulk_commit();
+                }
+            } else {
+                for (uint32_t k = lane; k < S; k += 32) dst[k] = buf[k];
+            }
+        } else if (good) {
+            unshuffle_generic(buf, dst, Bb, a.es, lane);  // a shortened last block
+        }
+        if (tile + 1 == a.nb) {
+            const uint32_t tb = a.tail_elems * a.es;
+            const uint64_t first = (a.n_elem - a.tail_elems) * a.es;
+            if (a.in_bytes >= tb)
+                for (uint32_t k = lane; k < tb; k += 32)
+                    a.out[first + k] = a.in[a.in_bytes - tb + k];
+        }
+        __syncwarp();
+        // the next block's bytes go into the same buffer once the store has read it
+        if (lane == 0) bulk_wait_read0();
+        __syncwarp();
+        ld = DecLoad{};
+        if (nxt < a.nb) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            ld = dec_issue(a, nxt, buf, bar, lane, INPLACE_BUF);
+        }
+        tile = nxt;
+    }
+    if (lane == 0) bulk_wait0();
+    __syncwarp();
+}
+
+uint32_t decompress_inplace_blocks_per_sm(uint32_t es)
+{
+    int n = 0;
+    const uint32_t smem = INPLACE_BUF + 16;
+    cudaError_t e = es == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decompress_inplace_kernel<2>, 32, smem)
+                  : es == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decompress_inplace_kernel<4>, 32, smem)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decompress_inplace_kernel<8>, 32, smem);
+    return e == cudaSuccess && n > 0 ? (uint32_t)n : 1u;
+}
+
 // Block offsets by walking the chain of 4-byte length fields (one thread).
 __global__ void chain_walk_kernel(const __grid_constant__ CodecArgs a, uint64_t *offsets)
 {
@@ -799,6 +918,12 @@ cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, 
         return cudaGetLastError();
     }
     uint32_t smem = decompress_smem_bytes(maxb);
+    if (maxb <= 8192 && (a.es == 2 || a.es == 4 || a.es == 8)) {
+        const uint32_t sm1 = INPLACE_BUF + 16;
+        if (a.es == 2) return launch_warp_kernel(decompress_inplace_kernel<2>, sm1, grid, s, a);
+        if (a.es == 4) return launch_warp_kernel(decompress_inplace_kernel<4>, sm1, grid, s, a);
+        return launch_warp_kernel(decompress_inplace_kernel<8>, sm1, grid, s, a);
+    }
     if (maxb <= 8192) {
         if (a.es == 2) return launch_warp_kernel(decompress_kernel<8192, 2>, smem, grid, s, a);
         if (a.es == 4) return launch_warp_kernel(decompress_kernel<8192, 4>, smem, grid, s, a);

@@ -75,6 +75,8 @@ struct CodecArgs {
 // Shared-memory bytes per warp-CTA for each kernel family and block-size class.
 uint32_t compress_smem_bytes(uint32_t maxb, int level);
 uint32_t decompress_smem_bytes(uint32_t maxb);
+// resident CTAs per SM of the one-buffer (in-place) decompress kernel
+uint32_t decompress_inplace_blocks_per_sm(uint32_t es);
 uint32_t shuffle_smem_bytes(uint32_t maxb);
 
 // Launchers (return cudaGetLastError()).  `grid` warps of 32 threads.

@@ -104,6 +104,43 @@ BSG_D void warp_copy_ranges(uint8_t *dst, const uint8_t *src, uint32_t n, uint32
     }
 }
 
+// Forward copy for a decoder that may write over its own input (in-place
+// decoding, the unread input starting at or after the write position): every
+// byte of a step is loaded before any lane stores that step, so no lane, however
+// far ahead, overwrites input another lane has still to read.  Head and tail
+// bytes are loaded up front, the head stored first, the tail last.
+BSG_D void warp_copy_ordered(uint8_t *dst, uint32_t d, const uint8_t *src, uint32_t s,
+                             uint32_t len, uint32_t lane)
+{
+#ifdef BSG_WARP_EMU
+    emu_check_aligned4(dst);
+    emu_check_aligned4(src);
+#endif
+    if (len <= 32) {
+        const uint8_t v = lane < len ? src[s + lane] : 0;
+        __syncwarp();
+        if (lane < len) dst[d + lane] = v;
+        return;
+    }
+    const uint32_t a0 = (d + 3u) & ~3u, a1 = (d + len) & ~3u;
+    const uint32_t head = a0 - d, tail = d + len - a1;
+    const bool ht = lane >= 28 && lane - 28 < tail;
+    const uint8_t hv = lane < head ? src[s + lane] : 0;
+    const uint8_t tv = ht ? src[s + (a1 - d) + lane - 28] : 0;
+    __syncwarp();
+    if (lane < head) dst[d + lane] = hv;
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    const uint32_t w1 = a1 >> 2;
+    for (uint32_t base = a0 >> 2; base < w1; base += 32) {
+        const uint32_t w = base + lane;
+        const uint32_t v = w < w1 ? ld32u(src, s + 4 * w - d) : 0u;
+        __syncwarp();
+        if (w < w1) d32[w] = v;
+    }
+    __syncwarp();
+    if (ht) dst[a1 + lane - 28] = tv;
+}
+
 // Warp fill of len bytes at dst[d..] with the byte b.
 BSG_D void warp_fill(uint8_t *dst, uint32_t d, uint32_t b, uint32_t len, uint32_t lane)
 {
@@ -715,7 +752,7 @@ BSG_D int lz4_decode_warp(const uint8_t *src, uint32_t ip0, uint32_t clen, uint8
         if (LL == 15 && !lz4_read_len(src, end, ip, LL, lane)) return 1;
         if (LL > end - ip) return 1;
         if (LL > S - op) return 2;
-        warp_copy(dst, op, src, ip, LL, lane);
+        warp_copy_ordered(dst, op, src, ip, LL, lane);
         ip += LL;
         op += LL;
         if (ip == end) break;

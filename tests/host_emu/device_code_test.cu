@@ -205,6 +205,18 @@ static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc
         cases.push_back(sh);
         rows.push_back(256);
     }
+    for (int t = 0; t < 4; t++) {
+        std::vector<uint16_t> w(4096);
+        int32_t x = 0;
+        for (auto &v : w) {
+            x += (rng() & 1 ? 1 : -1) * (1 << (rng() % 7));
+            v = (uint16_t)x;
+        }
+        std::vector<uint8_t> sh(8192);
+        orc_bitshuffle(w.data(), sh.data(), 4096, 2, 4096, 0);
+        cases.push_back(sh);
+        rows.push_back(512);
+    }
     size_t tg = 0, to = 0, tin = 0;
     for (size_t ci = 0; ci < cases.size(); ci++) {
         auto &c = cases[ci];
@@ -257,8 +269,38 @@ static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc
             });
             if (rc || memcmp(C, c.data(), S)) bad++;
         }
+        // in-place decoding as decompress_inplace_kernel does it: the stream
+        // (after its 4-byte length field) at the end of an 8352-byte buffer
+        for (uint32_t ph = 0; ph < 16 && !bad && S <= 8192; ph += 13) {
+            static uint8_t IB[8352 + 64];
+            const uint32_t len = cs + 4, off = (8352u - len - 32u) & ~15u;
+            memset(IB, 0x5A, sizeof IB);
+            memcpy(IB + off + ph + 4, Bf, cs);
+            run_warp([&] {
+                int r = lz4_decode_warp(IB + off, ph + 4, cs, IB, S);
+                if (threadIdx.x == 0) rc = r;
+            });
+            if (rc || memcmp(IB, c.data(), S)) {
+                fprintf(stderr, "in-place decode differs S=%u cs=%u phase=%u rc=%d\n", S, cs, ph, rc);
+                bad++;
+            }
+        }
         std::vector<uint8_t> oc(lz4_bound(S) + 16);
         size_t ocs = orc_lz4_compress_block(c.data(), S, oc.data(), oc.size());
+        for (uint32_t ph = 7; ph < 16 && !bad && S <= 8192; ph += 16) {
+            static uint8_t IB2[8352 + 64];
+            const uint32_t len = (uint32_t)ocs + 4, off = (8352u - len - 32u) & ~15u;
+            memset(IB2, 0x5A, sizeof IB2);
+            memcpy(IB2 + off + ph + 4, oc.data(), ocs);
+            run_warp([&] {
+                int r = lz4_decode_warp(IB2 + off, ph + 4, (uint32_t)ocs, IB2, S);
+                if (threadIdx.x == 0) rc = r;
+            });
+            if (rc || memcmp(IB2, c.data(), S)) {
+                fprintf(stderr, "in-place decode (oracle stream) differs S=%u cs=%zu phase=%u rc=%d\n", S, ocs, ph, rc);
+                bad++;
+            }
+        }
         memset(D2, 0, ocs + 16);
         memcpy(D2 + 3, oc.data(), ocs);
         run_warp([&] {
