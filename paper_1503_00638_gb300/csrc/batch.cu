@@ -234,14 +234,14 @@ BSG_D void copy_tail(const CodecArgs &a, uint32_t lane)
         set_status(a.status, BSGPU_ERR_CORRUPT);
 }
 
-// Start fetching item t's stream bytes into `comp` (nothing for a chunk
-// without blocks).
+// Start fetching item t's stream bytes into the end of the buffer `comp`
+// (nothing for a chunk without blocks).
 BSG_D DecLoad batch_issue(const BatchArgs &b, uint32_t c, uint32_t t, uint8_t *comp,
                           uint64_t *bar, uint32_t lane)
 {
     const CodecArgs a = chunk_args(b, c);
     if (a.nb == 0) return DecLoad{};
-    return dec_issue(a, t - (uint32_t)b.chunks[c].item0, comp, bar, lane);
+    return dec_issue(a, t - (uint32_t)b.chunks[c].item0, comp, bar, lane, INPLACE_BUF);
 }
 
 // LZ4-decode block `tile` of chunk c (stream bytes in `comp`) into `dec`;
@@ -262,17 +262,16 @@ BSG_D bool batch_decode(const BatchArgs &b, uint32_t c, uint32_t tile, const Dec
     return good;
 }
 
-// One warp per CTA, persistent (as decompress_kernel<8192, ES>): per item,
-// wait for its stream bytes, LZ4-decode, start the next item's copy (of
-// whichever chunk it belongs to), un-transpose and store.  As in the
-// compressor only chunk indices and block numbers live across an item.
-__global__ void __launch_bounds__(32, 13) decompress_batch_kernel(const __grid_constant__ BatchArgs b)
+// One warp per CTA, persistent, one shared buffer decoded in place (as
+// decompress_inplace_kernel): per item, wait for its stream bytes, LZ4-decode,
+// un-transpose and store, then fetch the next item's bytes (of whichever chunk
+// it belongs to) once the store has read the buffer.  As in the compressor
+// only chunk indices and block numbers live across an item.
+__global__ void __launch_bounds__(32, 16) decompress_batch_kernel(const __grid_constant__ BatchArgs b)
 {
-    using L = DecPlan<8192>;
     extern __shared__ __align__(128) uint8_t sm[];
-    uint8_t *comp = sm;
-    uint8_t *dec = sm + L::COMP;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(dec + L::DEC);
+    uint8_t *buf = sm;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + INPLACE_BUF);
     const uint32_t lane = threadIdx.x & 31u;
     if (lane == 0) {
         mbar_init(bar, 1);
@@ -285,7 +284,7 @@ __global__ void __launch_bounds__(32, 13) decompress_batch_kernel(const __grid_c
     DecLoad ld{};
     if (t < b.n_items) {
         c = find_chunk(b.starts, b.n_chunks, t);
-        ld = batch_issue(b, c, t, comp, bar, lane);
+        ld = batch_issue(b, c, t, buf, bar, lane);
     }
     while (t < b.n_items) {
         const uint32_t tile = t - (uint32_t)b.chunks[c].item0;
@@ -298,57 +297,47 @@ __global__ void __launch_bounds__(32, 13) decompress_batch_kernel(const __grid_c
         if (tile == 0) check_header(chunk_args(b, c), lane);
         const uint32_t nxt = grab_tile(b.counter, lane);
         const uint32_t nc = nxt < b.n_items ? find_chunk(b.starts, b.n_chunks, nxt) : c;
-        // the previous block's bulk store must have finished reading `dec`
-        if (lane == 0) bulk_wait_read0();
-        __syncwarp();
-        bool good = false, inplace = false;
         if (nb) {
-            good = batch_decode(b, c, tile, cur, comp, dec, lane);
-            const BatchChunk &ch = b.chunks[c];
-            const uint32_t Bb = tile + 1 == nb ? ch.last_B : ch.B;
-            inplace = unshuffle_inplace_ok(ch.es, Bb);
-            if (good && !inplace) {
-                const uint32_t S = Bb * ch.es;
-                uint8_t *dst = ch.out + (uint64_t)tile * ch.B * ch.es;
-                unshuffle_block(dec, comp, Bb, ch.es, lane);
-                __syncwarp();
-                for (uint32_t k = lane; k < S; k += 32) dst[k] = comp[k];
-            }
-        }
-        __syncwarp();
-        ld = DecLoad{};
-        if (nxt < b.n_items) {
-            // `comp` was last read by the generic proxy
-            fence_proxy_async_smem();
+            const bool good = batch_decode(b, c, tile, cur, buf + cur.off, buf, lane);
             __syncwarp();
-            ld = batch_issue(b, nc, nxt, comp, bar, lane);
-        }
-        if (good && inplace) {
             const BatchChunk &ch = b.chunks[c];
             const uint32_t es = ch.es;
             const uint32_t Bb = tile + 1 == nb ? ch.last_B : ch.B;
             const uint32_t S = Bb * es;
             uint8_t *dst = ch.out + (uint64_t)tile * ch.B * es;
-            if (es == 2)
-                unshuffle2_inplace(dec, Bb, lane);
-            else if (es == 4)
-                unshuffle4_inplace(dec, Bb, lane);
-            else
-                unshuffle8_inplace(dec, Bb, lane);
-            __syncwarp();
-            if ((S & 15u) == 0 && ((uintptr_t)dst & 15u) == 0) {
-                fence_proxy_async_smem();
+            if (good && unshuffle_inplace_ok(es, Bb)) {
+                if (es == 2)
+                    unshuffle2_inplace(buf, Bb, lane);
+                else if (es == 4)
+                    unshuffle4_inplace(buf, Bb, lane);
+                else
+                    unshuffle8_inplace(buf, Bb, lane);
                 __syncwarp();
-                if (lane == 0) {
-                    bulk_s2g(dst, dec, S);
-                    bulk_commit();
+                if ((S & 15u) == 0 && ((uintptr_t)dst & 15u) == 0) {
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        bulk_s2g(dst, buf, S);
+                        bulk_commit();
+                    }
+                } else {
+                    for (uint32_t k = lane; k < S; k += 32) dst[k] = buf[k];
                 }
-            } else {
-                for (uint32_t k = lane; k < S; k += 32) dst[k] = dec[k];
+            } else if (good) {
+                unshuffle_generic(buf, dst, Bb, es, lane);  // 1-byte elements, a shortened block
             }
         }
         if (nb == 0 || tile + 1 == nb) copy_tail(chunk_args(b, c), lane);
         __syncwarp();
+        // the next item's bytes go into the same buffer once the store has read it
+        if (lane == 0) bulk_wait_read0();
+        __syncwarp();
+        ld = DecLoad{};
+        if (nxt < b.n_items) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            ld = batch_issue(b, nc, nxt, buf, bar, lane);
+        }
         t = nxt;
         c = nc;
     }
@@ -587,7 +576,7 @@ int bsgpu_decompress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_it
         chain_walk_batch_kernel<<<(n_chunks + 127) / 128, 128, 0, s>>>(b);
         if (cudaGetLastError() != cudaSuccess) return BSGPU_ERR_CUDA;
     }
-    const uint32_t smem = decompress_smem_bytes(8192);
+    const uint32_t smem = INPLACE_BUF + 16;
     const uint32_t g = batch_grid(occupancy(decompress_batch_kernel, smem), ctas_per_sm, n_items);
     return launch_batch(decompress_batch_kernel, smem, g, s, b) == cudaSuccess ? BSGPU_OK
                                                                                : BSGPU_ERR_CUDA;

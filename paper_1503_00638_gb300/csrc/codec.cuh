@@ -585,6 +585,15 @@ struct NoRound {
 // Decompress: LZ4 decode -> bit un-transpose, every block at once
 // ---------------------------------------------------------------------------
 
+// One shared buffer for in-place decoding of blocks of at most 8 KiB: the
+// block's compressed image at its end, the output from its start (see
+// decompress_inplace_kernel for the margin).  Placement (an image of at most
+// 4 + lz4b(8192) bytes, 32 before the end, 16 for the phase) and in-place
+// safety (image start - (S - clen) >= 72).
+constexpr uint32_t INPLACE_BUF = 8352;
+static_assert(INPLACE_BUF >= 4 + lz4b(8192) + 48, "in-place buffer: image does not fit");
+static_assert(INPLACE_BUF >= 8192 + 119, "in-place buffer: margin below the LZ4 bound");
+
 struct DecLoad {
     bool bulk;       // a bulk copy is in flight on the barrier
     bool ok;         // offsets passed the range checks

@@ -557,11 +557,6 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 13 : 1)
 // Half the shared memory of decompress_kernel: 16 resident warps per SM
 // instead of 13, at the cost of the next block's copy starting only once
 // this block's store has read the buffer.
-constexpr uint32_t INPLACE_BUF = 8352;
-// placement (an image of at most 4 + lz4b(8192) bytes, 32 before the end, 16
-// for the phase) and in-place safety (image start - (S - clen) >= 72)
-static_assert(INPLACE_BUF >= 4 + lz4b(8192) + 48, "in-place buffer: image does not fit");
-static_assert(INPLACE_BUF >= 8192 + 119, "in-place buffer: margin below the LZ4 bound");
 
 template <int ES>
 __global__ void __launch_bounds__(32, 16) decompress_inplace_kernel(const __grid_constant__ CodecArgs a)
