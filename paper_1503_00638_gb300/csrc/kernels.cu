@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 13 : 1)
 // this block's store has read the buffer.
 
 template <int ES>
-__global__ void __launch_bounds__(32, 16) decompress_inplace_kernel(const __grid_constant__ CodecArgs a)
+__global__ void __launch_bounds__(32, 20) decompress_inplace_kernel(const __grid_constant__ CodecArgs a)
 {
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t *buf = sm;
