@@ -1,0 +1,170 @@
+"""Compressing visibility cubes that live in host memory.
+
+The paper stores data in chunks, each compressed on its own (HDF5 chunks,
+Sec. 2.3; blocks within a chunk, Sec. 4.2.1).  `HostVisCodec` does the same
+with frequency slabs of a host cube: every slab is one framed stream (as
+``bsgpu_compress_vis`` writes it) with its block index, and slabs are
+software-pipelined over three CUDA streams so that the upload of one slab,
+the kernels of another and the download of a third overlap, and uploads run
+beside downloads.  Slabs are independent: the noise of Sec. 3.1 only needs a
+slab's own autocorrelations.
+
+Host orchestration only (pinned buffers, streams, events); the rounding,
+shuffling and coding run in libbsgpu's kernels.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import bsgpu
+
+
+@dataclass
+class Chunk:
+    freq: tuple           # (f0, f1)
+    nbytes: int           # stream length
+    stream: torch.Tensor  # pinned host bytes [nbytes]
+    index: torch.Tensor   # pinned host int64 block offsets
+
+
+class HostVisCodec:
+    """Round + compress a [F][P][T] complex64 host cube slab by slab, and
+    decompress such slabs back into host memory, with copies and kernels
+    overlapped.
+
+    slab_freq : frequencies per slab (one stream each)
+    depth     : slabs in flight (device buffers are allocated per slot)
+    """
+
+    def __init__(self, n_freq: int, n_inputs: int, n_time: int, N: float, f: float,
+                 block_elems: int = 2048, level: int = 0, slab_freq: int = 64, depth: int = 3,
+                 device="cuda"):
+        self.F, self.n_in, self.T = n_freq, n_inputs, n_time
+        self.P = n_inputs * (n_inputs + 1) // 2
+        self.N, self.f, self.B, self.level = float(N), float(f), block_elems, level
+        self.slabs = [(f0, min(n_freq, f0 + slab_freq)) for f0 in range(0, n_freq, slab_freq)]
+        self.depth = min(depth, len(self.slabs))
+        dev = torch.device(device)
+        self.dev = dev
+        sf = slab_freq
+        self.slab_elems = sf * self.P * n_time * 2          # float32 components
+        self.cap = bsgpu.compress_bound(self.slab_elems, 4, block_elems)
+        self.nblk = bsgpu.num_blocks(self.slab_elems, 4, block_elems)
+        wsc = bsgpu.vis_workspace_size(bsgpu.OP_COMPRESS_VIS, sf, n_inputs, n_time, block_elems)
+        wsd = bsgpu.workspace_size(bsgpu.OP_DECOMPRESS, self.slab_elems, 4, block_elems)
+        self.slot = []
+        for _ in range(self.depth):
+            self.slot.append({
+                "vis": torch.empty((sf, self.P, n_time), dtype=torch.complex64, device=dev),
+                "stream": torch.empty(self.cap, dtype=torch.uint8, device=dev),
+                "offs": torch.empty(max(self.nblk, 1), dtype=torch.int64, device=dev),
+                "nb": torch.zeros(1, dtype=torch.int64, device=dev),
+                "h_nb": torch.zeros(1, dtype=torch.int64).pin_memory(),
+                "ws_c": bsgpu.new_workspace(wsc, dev),
+                "ws_d": bsgpu.new_workspace(wsd, dev),
+                "out": torch.empty(self.slab_elems * 4, dtype=torch.uint8, device=dev),
+                "ev_in": torch.cuda.Event(), "ev_c": torch.cuda.Event(),
+                "ev_d2h": torch.cuda.Event(), "ev_dc": torch.cuda.Event(),
+                "free": torch.cuda.Event(),
+            })
+        self.s_h2d = torch.cuda.Stream(device=dev)
+        self.s_k = torch.cuda.Stream(device=dev)
+        self.s_d2h = torch.cuda.Stream(device=dev)
+        self.h_streams = [torch.empty(self.cap, dtype=torch.uint8).pin_memory() for _ in self.slabs]
+        self.h_index = [torch.empty(max(self.nblk, 1), dtype=torch.int64).pin_memory()
+                        for _ in self.slabs]
+
+    # -- helpers ------------------------------------------------------------
+
+    def _compress_slab(self, sl, F):
+        b = bsgpu
+        b._check(b._lib.bsgpu_compress_vis(
+            sl["vis"].data_ptr(), F, self.n_in, self.T, self.N, self.f, self.B, self.level,
+            sl["stream"].data_ptr(), self.cap, sl["nb"].data_ptr(), sl["offs"].data_ptr(),
+            sl["ws_c"].data_ptr(), sl["ws_c"].numel(), self.s_k.cuda_stream), "bsgpu_compress_vis")
+
+    def _decompress_slab(self, sl, F, L):
+        b = bsgpu
+        n = F * self.P * self.T * 2
+        b._check(b._lib.bsgpu_decompress(
+            sl["stream"].data_ptr(), L, sl["out"].data_ptr(), n, 4, self.B, sl["offs"].data_ptr(),
+            sl["ws_d"].data_ptr(), sl["ws_d"].numel(), self.s_k.cuda_stream), "bsgpu_decompress")
+
+    # -- the pipelined round trip -------------------------------------------
+
+    def round_trip(self, h_vis: torch.Tensor, h_out: torch.Tensor, lag: int = 1) -> list:
+        """Compress the pinned host cube h_vis ([F][P][T] complex64) slab by slab
+        into pinned host streams, then decompress every stream (read back from
+        host memory) into the pinned host tensor h_out (same shape), with
+        uploads, kernels and downloads of different slabs overlapped.
+        Returns the chunks (freq range, length, host stream and index)."""
+        n = len(self.slabs)
+        # slab k reuses the slot of slab k - depth, whose copies back are
+        # enqueued `lag` steps after its kernels: the slot must be free first
+        lag = max(0, min(lag, self.depth - 1))
+        lens = [0] * n
+        for sl in self.slot:
+            sl["free"].record(self.s_d2h)
+        for step in range(n + lag):
+            k = step
+            if k < n:
+                sl = self.slot[k % self.depth]
+                f0, f1 = self.slabs[k]
+                F = f1 - f0
+                self.s_h2d.wait_event(sl["free"])
+                with torch.cuda.stream(self.s_h2d):
+                    sl["vis"][:F].copy_(h_vis[f0:f1], non_blocking=True)
+                    sl["ev_in"].record(self.s_h2d)
+                self.s_k.wait_event(sl["ev_in"])
+                with torch.cuda.stream(self.s_k):
+                    self._compress_slab(sl, F)
+                    sl["h_nb"].copy_(sl["nb"], non_blocking=True)
+                    sl["ev_c"].record(self.s_k)
+            j = step - lag
+            if j >= 0:
+                sl = self.slot[j % self.depth]
+                f0, f1 = self.slabs[j]
+                F = f1 - f0
+                sl["ev_c"].synchronize()              # the stream length, for exact copies
+                L = int(sl["h_nb"][0])
+                lens[j] = L
+                nb = bsgpu.num_blocks(F * self.P * self.T * 2, 4, self.B)
+                self.s_d2h.wait_event(sl["ev_c"])
+                with torch.cuda.stream(self.s_d2h):
+                    self.h_streams[j][:L].copy_(sl["stream"][:L], non_blocking=True)
+                    self.h_index[j][:nb].copy_(sl["offs"][:nb], non_blocking=True)
+                    sl["ev_d2h"].record(self.s_d2h)
+                # decompression reads the stream back from host memory
+                self.s_h2d.wait_event(sl["ev_d2h"])
+                with torch.cuda.stream(self.s_h2d):
+                    sl["stream"][:L].copy_(self.h_streams[j][:L], non_blocking=True)
+                    sl["offs"][:nb].copy_(self.h_index[j][:nb], non_blocking=True)
+                    sl["ev_in"].record(self.s_h2d)
+                self.s_k.wait_event(sl["ev_in"])
+                with torch.cuda.stream(self.s_k):
+                    self._decompress_slab(sl, F, L)
+                    sl["ev_dc"].record(self.s_k)
+                self.s_d2h.wait_event(sl["ev_dc"])
+                with torch.cuda.stream(self.s_d2h):
+                    nbytes = F * self.P * self.T * 8
+                    h_out.view(torch.uint8).reshape(-1)[f0 * self.P * self.T * 8:
+                                                       f0 * self.P * self.T * 8 + nbytes].copy_(
+                        sl["out"][:nbytes], non_blocking=True)
+                    sl["free"].record(self.s_d2h)
+        torch.cuda.synchronize(self.dev)
+        return [Chunk(self.slabs[j], lens[j], self.h_streams[j][:lens[j]],
+                      self.h_index[j][:bsgpu.num_blocks((self.slabs[j][1] - self.slabs[j][0]) *
+                                                         self.P * self.T * 2, 4, self.B)])
+                for j in range(n)]
+
+    def statuses(self):
+        return [(bsgpu.status(sl["ws_c"]), bsgpu.status(sl["ws_d"])) for sl in self.slot]
+
+    def bytes_moved(self, chunks):
+        """(host-to-device, device-to-host) bytes of one round trip."""
+        cube = self.F * self.P * self.T * 8
+        streams = sum(c.nbytes for c in chunks)
+        idx = sum(c.index.numel() * 8 for c in chunks)
+        return cube + streams + idx, streams + idx + cube + 8 * len(chunks)
