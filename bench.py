@@ -199,18 +199,30 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(scale_units):
-    """dram bytes per launch of the compress kernel from profiles/traffic.json,
-    if it was taken on the current kernel source; scaled to this launch."""
+def recorded_profile(scale_units, key="dram_bytes_per_launch"):
+    """A per-launch figure of the compress kernel from profiles/traffic.json
+    (DRAM bytes, or warp instructions with key="inst_per_launch"), if it was
+    taken on the current kernel source; scaled to this launch."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    if d.get("source_hash") != kernel_source_hash():
+    if d.get("source_hash") != kernel_source_hash() or key not in d:
         return None
-    per_unit = d["dram_bytes_per_launch"] / d["units_per_launch"]
-    return per_unit * scale_units
+    return d[key] / d["units_per_launch"] * scale_units
+
+
+def recorded_traffic(scale_units):
+    return recorded_profile(scale_units)
+
+
+def issue_peak_ginst(sm_mhz):
+    """Warp instructions per second the SMs can issue: 4 schedulers per SM,
+    one instruction per scheduler per cycle."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return sms * 4 * (sm_mhz or 2070.0) * 1e6 / 1e9
 
 
 # -- the batched-engine workload ------------------------------------------------
@@ -712,6 +724,17 @@ def main():
     achieved = alg_c / (comp_avg_ms / 1e3) / 1e9
     alg_d = slen + nblk * 8 + nbytes
     traffic = recorded_traffic(nblk)
+    # the compress kernel against the instruction-issue ceiling (the bound
+    # that holds for it, DRAM being at ~10 %): warp instructions per launch
+    # from the profile of the same source, over the measured launch time
+    inst = recorded_profile(nblk, "inst_per_launch")
+    issue_line = None
+    if inst:
+        peak_i = issue_peak_ginst(clk.get("sm_mhz"))
+        ach_i = inst / (comp_avg_ms / 1e3) / 1e9
+        issue_line = {"bound": "issue", "kernel": "compress_fast_kernel", "achieved": ach_i,
+                      "peak": peak_i, "unit": "G warp-instructions/s", "frac": ach_i / peak_i,
+                      "inst_per_launch": inst}
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -731,6 +754,7 @@ def main():
         "decompress_roofline": {"bound": "hbm", "achieved": alg_d / (dec_avg_ms / 1e3) / 1e9,
                                 "peak": hbm, "unit": "GB/s",
                                 "frac": alg_d / (dec_avg_ms / 1e3) / 1e9 / hbm},
+        "issue_roofline": issue_line,
         "e2e": {"value": pipe_value, "unit": "GB/s", "h2d_bytes_per_step": pipe_h2d,
                 "d2h_bytes_per_step": pipe_d2h, "round_trip_ok": ok_pipe,
                 "api": "hostio.HostVisCodec.round_trip (64-frequency slabs, pipelined)",
