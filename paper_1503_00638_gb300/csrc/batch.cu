@@ -141,7 +141,7 @@ BSG_D void batch_place(const BatchArgs &b, uint32_t c, uint32_t tile, const uint
 // chunk index and local block number live across an item; the chunk's
 // fields are re-read from its (cached) table record where they are used.
 template <int LEVEL>
-__global__ void __launch_bounds__(32, 16) compress_batch_kernel(const __grid_constant__ BatchArgs b)
+__global__ void __launch_bounds__(32, 20) compress_batch_kernel(const __grid_constant__ BatchArgs b)
 {
     using L = FastPlan<LEVEL>;
     extern __shared__ __align__(128) uint8_t sm[];
@@ -267,7 +267,7 @@ BSG_D bool batch_decode(const BatchArgs &b, uint32_t c, uint32_t tile, const Dec
 // un-transpose and store, then fetch the next item's bytes (of whichever chunk
 // it belongs to) once the store has read the buffer.  As in the compressor
 // only chunk indices and block numbers live across an item.
-__global__ void __launch_bounds__(32, 16) decompress_batch_kernel(const __grid_constant__ BatchArgs b)
+__global__ void __launch_bounds__(32, 20) decompress_batch_kernel(const __grid_constant__ BatchArgs b)
 {
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t *buf = sm;
