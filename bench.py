@@ -190,10 +190,15 @@ def run_reference(args, rank):
 
 # -- traffic recorded from an ncu capture of the current kernel source ----------
 
+# the sources the profiled compress kernel is compiled from
+KERNEL_SOURCES = ("kernels.cu", "kernels.cuh", "codec.cuh", "common.cuh", "lz4_warp.cuh",
+                  "shuffle.cuh")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1503_00638_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
