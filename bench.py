@@ -64,7 +64,8 @@ def parse():
     p.add_argument("--freqs", type=int, default=1024,
                    help="frequencies of the cube (1024 = the full workload; fewer only for "
                         "profiling runs)")
-    p.add_argument("--workload", default="chime", choices=["chime", "batch", "serve"])
+    p.add_argument("--workload", default="chime",
+                   choices=["chime", "batch", "serve"] + sorted(VARIANTS))
     p.add_argument("--requests", type=int, default=3000,
                    help="serve workload: requests per arrival-rate point")
     p.add_argument("--chunks", type=int, default=4096,
@@ -537,6 +538,190 @@ def run_serve(args, rank, world, gpu_index):
         print(json.dumps(line), flush=True)
 
 
+# -- variants of the visibility path (the int32 path, the fused reorder, the
+#    compensated f, 8-byte samples, the full covariance) ------------------------
+
+VARIANTS = {
+    "chime-int32": {"dtype": "i32", "es": 4, "tslow": False, "comp": False, "full": False,
+                    "what": "int32 (re, im) cube (the CHIME-shaped cube x 4096, rounded to integers)"},
+    "chime-tslow": {"dtype": "f32", "es": 4, "tslow": True, "comp": False, "full": False,
+                    "what": "complex64 cube in the instrument's order [T][F][P], reorder fused"},
+    "chime-compensated": {"dtype": "f32", "es": 4, "tslow": False, "comp": True, "full": False,
+                          "what": "complex64 cube, compensated f of Sec. 3.2 per sample"},
+    "chime-samples8": {"dtype": "f32", "es": 8, "tslow": False, "comp": False, "full": False,
+                       "what": "complex64 cube bitshuffled as 8-byte samples"},
+    "fullcov8": {"dtype": "f32", "es": 4, "tslow": False, "comp": False, "full": True,
+                 "what": "8-input array, 1024 freq x 36 products x 64 time, full covariance"},
+}
+
+
+def run_variant(args, rank, world, gpu_index, barrier):
+    import torch
+    import torch.distributed as dist
+    import numpy as _np
+    from paper_1503_00638_gb300 import bsgpu, synth
+    v = VARIANTS[args.workload]
+    if v["full"]:
+        cfg = synth.VisConfig(1024, 8, 64, 2 ** 16, args.f, seed=rank, rho=0.5)
+        host = synth.visibilities_physical(cfg)
+    else:
+        cfg = synth.VisConfig(1024, 128, 16, 2 ** 17, args.f, seed=rank, drift=True)
+        host = synth.visibilities_int(cfg, 4096.0) if v["dtype"] == "i32" else synth.visibilities(cfg)
+    F, n_in, T = cfg.n_freq, cfg.n_inputs, cfg.n_time
+    host_in = _np.ascontiguousarray(_np.moveaxis(host, 2, 0)) if v["tslow"] else host
+    nbytes = host.nbytes
+    es = v["es"]
+    B = 8192 // es
+    n_el = nbytes // es
+    flags = ((bsgpu.VIS_COMPENSATE if v["comp"] else 0) |
+             (bsgpu.VIS_TIME_SLOWEST if v["tslow"] else 0) |
+             (bsgpu.VIS_FULL_COV if v["full"] else 0))
+    dt = bsgpu.VIS_I32 if v["dtype"] == "i32" else bsgpu.VIS_F32
+    pin = torch.from_numpy(host_in).pin_memory()
+    d_in = pin.cuda()
+    stream = torch.cuda.current_stream()
+    cap = bsgpu.compress_bound(n_el, es, B)
+    nblk = bsgpu.num_blocks(n_el, es, B)
+    comp = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    offs = torch.empty(max(nblk, 1), dtype=torch.int64, device="cuda")
+    nb_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws_c = bsgpu.new_workspace(bsgpu.vis_workspace_size_ex(bsgpu.OP_COMPRESS_VIS, F, n_in, T, es,
+                                                           B, flags))
+    ws_d = bsgpu.new_workspace(bsgpu.workspace_size(bsgpu.OP_DECOMPRESS, n_el, es, B))
+    dec = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    lib = bsgpu._lib
+
+    def compress():
+        bsgpu._check(lib.bsgpu_compress_vis_ex(
+            d_in.data_ptr(), dt, F, n_in, T, cfg.n_samp, cfg.f, flags, es, B, LEVEL,
+            comp.data_ptr(), cap, nb_dev.data_ptr(), offs.data_ptr(), ws_c.data_ptr(),
+            ws_c.numel(), stream.cuda_stream), "bsgpu_compress_vis_ex")
+
+    def decompress(slen):
+        bsgpu._check(lib.bsgpu_decompress(
+            comp.data_ptr(), slen, dec.data_ptr(), n_el, es, B, offs.data_ptr(), ws_d.data_ptr(),
+            ws_d.numel(), stream.cuda_stream), "bsgpu_decompress")
+
+    compress()
+    slen = int(nb_dev.item())
+    decompress(slen)
+    torch.cuda.synchronize()
+    if bsgpu.status(ws_c) or bsgpu.status(ws_d):
+        raise RuntimeError("variant status")
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(args.warmup):
+        compress()
+        decompress(slen)
+    torch.cuda.synchronize()
+    t_soak0 = time.time()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        compress()
+        evs[k][1].record(stream)
+        decompress(slen)
+        evs[k][2].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall1 = time.time()
+    clk = clocks.summary(t_soak0, t_wall1)
+    clocks.stop()
+    if bsgpu.status(ws_c) or bsgpu.status(ws_d):
+        raise RuntimeError("variant status after timed steps")
+    ms = start.elapsed_time(end)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    cm = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    dm = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    # the output is the time-fastest rounded cube
+    ref = bsgpu.reduce_precision(d_in, cfg.n_samp, cfg.f, compensate=v["comp"],
+                                 time_slowest=v["tslow"], full_cov=v["full"])
+    ok = bool(torch.equal(ref.view(torch.uint8).reshape(-1), dec))
+    # end to end, one stream: upload, compress, download the stream, upload it,
+    # decompress, download the cube
+    h_stream = torch.empty(cap, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    e2e_t = []
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_in.view(torch.uint8).reshape(-1).copy_(pin.view(torch.uint8).reshape(-1),
+                                                 non_blocking=True)
+        compress()
+        L = int(nb_dev.item())
+        h_stream[:L].copy_(comp[:L], non_blocking=True)
+        comp[:L].copy_(h_stream[:L], non_blocking=True)
+        decompress(L)
+        h_out.copy_(dec, non_blocking=True)
+        torch.cuda.synchronize()
+        if k:
+            e2e_t.append(time.perf_counter() - t0)
+    hbm, peak_kind = peaks()
+    autos = F * n_in * T * 4
+    alg_c = nbytes + slen + nblk * 8 + autos
+    alg_d = slen + nblk * 8 + nbytes
+    line = {
+        "metric": METRIC, "value": nbytes * world * args.steps / (ms_max / 1e3) / 1e9,
+        "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i32" if v["dtype"] == "i32" else "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {v['what']}", "f": cfg.f, "N": cfg.n_samp,
+                   "elem_bytes": es, "block_bytes": 8192, "cube_bytes": nbytes,
+                   "l2": f"inputs ({nbytes / 1e9:.2f} GB) larger than L2; no flush",
+                   "parallelism": f"replicas x{world}"},
+        "compress_gbs": nbytes / (cm / 1e3) / 1e9, "decompress_gbs": nbytes / (dm / 1e3) / 1e9,
+        "ratio": slen / nbytes, "round_trip_ok": ok,
+        "roofline": {"bound": "hbm", "kernel": "compress (round + shuffle + LZ4)",
+                     "achieved": alg_c / (cm / 1e3) / 1e9, "peak": hbm, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": alg_c / (cm / 1e3) / 1e9 / hbm, "traffic": None,
+                     "algorithmic_bytes": alg_c},
+        "decompress_roofline": {"bound": "hbm", "achieved": alg_d / (dm / 1e3) / 1e9,
+                                "peak": hbm, "unit": "GB/s",
+                                "frac": alg_d / (dm / 1e3) / 1e9 / hbm},
+        "e2e": {"value": nbytes * world / statistics.median(e2e_t) / 1e9, "unit": "GB/s",
+                "h2d_bytes_per_step": nbytes + slen, "d2h_bytes_per_step": slen + nbytes + 8},
+        # per step: the tables, the compensated c or the full-covariance q
+        # when asked, one compress kernel (no shortened block at these
+        # sizes), one decompress kernel
+        "gpu_launches": args.steps * (3 + int(v["comp"]) + int(v["full"])),
+        "clocks": clk, "wall_s_timed": t_wall1 - t_wall0,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        fs = 2 if v["full"] else 16
+        sub = host[:fs]
+        t0 = time.perf_counter()
+        if v["full"]:
+            r = oracle.reduce_precision_full(sub, cfg.n_samp, cfg.f)
+        else:
+            src = oracle.reorder_time(_np.ascontiguousarray(_np.moveaxis(sub, 2, 0))) \
+                if v["tslow"] else sub
+            r = oracle.reduce_precision(src, cfg.n_samp, cfg.f, v["comp"])
+        flat = _np.ascontiguousarray(r).view(_np.uint32 if es == 4 else _np.uint64).reshape(-1)
+        st = oracle.compress(flat, B)
+        rc, back = oracle.decompress(st, flat.size, flat.dtype, B)
+        dt_cpu = time.perf_counter() - t0
+        if rc or not _np.array_equal(back, flat):
+            raise RuntimeError("oracle round trip")
+        line["cpu_baseline"] = {"value": sub.nbytes / dt_cpu / 1e9, "unit": "GB/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"first {fs} of {F} frequencies ({sub.nbytes / 1e6:.1f} "
+                                          "MB): round+compress+decompress"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # -- the GPU arm ----------------------------------------------------------------
 
 def main():
@@ -569,6 +754,11 @@ def main():
             gpu_index = int(vis_dev_env.split(",")[local])
         except ValueError:
             gpu_index = local
+    if args.workload in VARIANTS:
+        run_variant(args, rank, world, gpu_index, barrier)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     if args.workload == "serve":
         run_serve(args, rank, world, gpu_index)
         if world > 1:

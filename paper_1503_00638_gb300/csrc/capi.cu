@@ -97,7 +97,8 @@ VisOpts vis_opts(int flags, int64_t n_freq, int64_t n_in, int64_t n_time)
         const uint64_t ft = (uint64_t)n_freq * n_time, M = (uint64_t)n_in * n_in;
         o.full_grid = (uint32_t)(ft < 256 ? ft : 256);
         o.qtab_bytes = ft * M * 4;
-        o.fscr_bytes = (size_t)o.full_grid * M * M * 8;
+        // small matrices live in shared memory: no scratch
+        o.fscr_bytes = M <= FULL_SMEM_M ? 0 : (size_t)o.full_grid * M * M * 8;
     }
     return o;
 }

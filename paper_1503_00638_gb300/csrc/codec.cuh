@@ -525,30 +525,59 @@ template <bool GEN>
 BSG_D void round_group(const VisParams &P, uint32_t (&a)[32], uint32_t rot, uint32_t f,
                        uint32_t t0, const float *ai, const float *aj, bool is_auto)
 {
+    if (GEN) {
+        // c per sample: the compensated table (two adjacent samples per
+        // 8-byte load) or the constant; the data type is one branch per group
+        const float *crow = P.cft ? P.cft + (size_t)f * P.T + t0 : nullptr;
+        const float mul = is_auto ? 2.0f : 1.0f;  // exact: c2 = 2 c
+        auto qs = [&](uint32_t c, float &q0, float &q1) {
+            const float2 Ai = __ldg(reinterpret_cast<const float2 *>(ai + 2 * c));
+            const float2 Aj = __ldg(reinterpret_cast<const float2 *>(aj + 2 * c));
+            const float2 cc = crow ? __ldg(reinterpret_cast<const float2 *>(crow + 2 * c))
+                                   : make_float2(P.c, P.c);
+            q0 = __fmul_rn(__fmul_rn(__fmul_rn(cc.x, mul), Ai.x), Aj.x);
+            q1 = __fmul_rn(__fmul_rn(__fmul_rn(cc.y, mul), Ai.y), Aj.y);
+        };
+        if (P.is_int) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                float q0, q1;
+                qs((k + rot) & 7u, q0, q1);
+                a[4 * k] = reduce_bits(a[4 * k], q0, true);
+                a[4 * k + 2] = reduce_bits(a[4 * k + 2], q1, true);
+                if (!is_auto) {
+                    a[4 * k + 1] = reduce_bits(a[4 * k + 1], q0, true);
+                    a[4 * k + 3] = reduce_bits(a[4 * k + 3], q1, true);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                float q0, q1;
+                qs((k + rot) & 7u, q0, q1);
+                a[4 * k] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k]), q0));
+                a[4 * k + 2] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 2]), q1));
+                if (!is_auto) {
+                    a[4 * k + 1] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 1]), q0));
+                    a[4 * k + 3] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 3]), q1));
+                }
+            }
+        }
+        return;
+    }
     const float cc = is_auto ? P.c2 : P.c;
 #pragma unroll
     for (int k = 0; k < 8; k++) {
         const uint32_t c = (k + rot) & 7u;  // chunk c: samples t0 + 2c, t0 + 2c + 1
         const float2 Ai = __ldg(reinterpret_cast<const float2 *>(ai + 2 * c));
         const float2 Aj = __ldg(reinterpret_cast<const float2 *>(aj + 2 * c));
-        if (GEN) {
-            const float q0 = __fmul_rn(__fmul_rn(vis_c(P, f, t0 + 2 * c, is_auto), Ai.x), Aj.x);
-            const float q1 = __fmul_rn(__fmul_rn(vis_c(P, f, t0 + 2 * c + 1, is_auto), Ai.y), Aj.y);
-            a[4 * k] = reduce_bits(a[4 * k], q0, P.is_int);
-            a[4 * k + 2] = reduce_bits(a[4 * k + 2], q1, P.is_int);
-            if (!is_auto) {
-                a[4 * k + 1] = reduce_bits(a[4 * k + 1], q0, P.is_int);
-                a[4 * k + 3] = reduce_bits(a[4 * k + 3], q1, P.is_int);
-            }
-        } else {
-            const float q0 = __fmul_rn(__fmul_rn(cc, Ai.x), Aj.x);
-            const float q1 = __fmul_rn(__fmul_rn(cc, Ai.y), Aj.y);
-            a[4 * k] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k]), q0));
-            a[4 * k + 2] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 2]), q1));
-            if (!is_auto) {
-                a[4 * k + 1] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 1]), q0));
-                a[4 * k + 3] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 3]), q1));
-            }
+        const float q0 = __fmul_rn(__fmul_rn(cc, Ai.x), Aj.x);
+        const float q1 = __fmul_rn(__fmul_rn(cc, Ai.y), Aj.y);
+        a[4 * k] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k]), q0));
+        a[4 * k + 2] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 2]), q1));
+        if (!is_auto) {
+            a[4 * k + 1] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 1]), q0));
+            a[4 * k + 3] = __float_as_uint(reduce_one(__uint_as_float(a[4 * k + 3]), q1));
         }
     }
 }

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) vis_compensation_kernel(const void *__res
 // the lower triangle of C in this CTA's global scratch (M^2 doubles, L2
 // resident), a right-looking Cholesky C = L L^T with the pivot column staged
 // in shared memory, then W = L^-1 row by row, thread k owning column k
-// (stored transposed in the free upper triangle) and summing
+// (row i of W overwriting row i of L once it is staged) and summing
 // (C^-1)_kk = sum_i W_ik^2.  A non-positive pivot leaves the sample
 // unrounded (q = 0).
 __global__ void __launch_bounds__(256) full_noise_kernel(const void *__restrict__ vis, VisParams P,
@@ -129,8 +129,10 @@ __global__ void __launch_bounds__(256) full_noise_kernel(const void *__restrict_
     __shared__ double Vre[FULL_MAX_INPUTS][FULL_MAX_INPUTS], Vim[FULL_MAX_INPUTS][FULL_MAX_INPUTS];
     __shared__ uint8_t ci[256], cj[256], ca[256];   // component -> (i, j, Re/Im)
     __shared__ double col[256];
+    extern __shared__ double smA[];   // the matrix itself when it fits (M <= 64)
     const uint32_t n = P.n_in, M = n * n, NP = P.P, tid = threadIdx.x, nt = blockDim.x;
-    double *A = scratch + (size_t)blockIdx.x * M * M;
+    double *A = M <= FULL_SMEM_M ? smA : scratch + (size_t)blockIdx.x * M * M;
+    const double inv2N = 1.0 / (2.0 * N);
     float *qtab = const_cast<float *>(P.qtab);
     for (uint32_t p = tid; p < NP; p += nt) {
         const uint32_t ij = P.pairs[p], i = ij & 0xffffu, j = ij >> 16;
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(256) full_noise_kernel(const void *__restrict_
             if (a == 0 && b == 0) v = xr + yr;
             else if (a == 1 && b == 1) v = xr - yr;
             else v = yi - xi;
-            A[(size_t)r * M + c] = v / (2.0 * N);
+            A[(size_t)r * M + c] = v * inv2N;
         }
         __syncthreads();
         bool ok = true;
@@ -186,37 +188,42 @@ __global__ void __launch_bounds__(256) full_noise_kernel(const void *__restrict_
                 ok = false;
                 break;
             }
-            const double ljj = sqrt(d);
+            const double ljj = sqrt(d), rl = 1.0 / ljj;  // one division per column
             for (uint32_t i = j + tid; i < M; i += nt) {
-                const double x = i == j ? ljj : A[(size_t)i * M + j] / ljj;
+                const double x = i == j ? ljj : A[(size_t)i * M + j] * rl;
                 A[(size_t)i * M + j] = x;
                 col[i] = x;
             }
             __syncthreads();
-            const uint32_t m = M - j - 1;
-            for (uint32_t e = tid; e < m * m; e += nt) {
-                const uint32_t ii = j + 1 + e / m, kk = j + 1 + e % m;
-                if (kk <= ii) A[(size_t)ii * M + kk] -= col[ii] * col[kk];
+            // trailing lower triangle, threads as a 16 x 16 grid (no index division)
+            for (uint32_t ii = j + 1 + (tid >> 4); ii < M; ii += nt >> 4) {
+                const double ci = col[ii];
+                for (uint32_t kk = j + 1 + (tid & 15u); kk <= ii; kk += 16)
+                    A[(size_t)ii * M + kk] -= ci * col[kk];
             }
             __syncthreads();
         }
-        double acc = 0.0, wkk = 0.0;
+        double acc = 0.0;
         const uint32_t k = tid;
         if (ok) {
+            // W = L^-1 row by row: row i of L is staged in `col`, then its
+            // storage takes row i of W (A[i][k] = W_ik), so thread k reads its
+            // column of W across rows at consecutive addresses (no bank
+            // conflicts between threads)
             for (uint32_t i = 0; i < M; i++) {
                 for (uint32_t m = tid; m <= i; m += nt) col[m] = A[(size_t)i * M + m];
                 __syncthreads();
                 if (k <= i && k < M) {
+                    const double rli = 1.0 / col[i];
                     double w;
                     if (k == i) {
-                        w = 1.0 / col[i];
-                        wkk = w;
+                        w = rli;
                     } else {
-                        double sum = col[k] * wkk;
-                        for (uint32_t m = k + 1; m < i; m++) sum += col[m] * A[(size_t)k * M + m];
-                        w = -sum / col[i];
-                        A[(size_t)k * M + i] = w;   // W_ik, transposed into the upper triangle
+                        double sum = 0.0;
+                        for (uint32_t m = k; m < i; m++) sum += col[m] * A[(size_t)m * M + k];
+                        w = -sum * rli;
                     }
+                    A[(size_t)i * M + k] = w;
                     acc += w * w;
                 }
                 __syncthreads();
@@ -792,6 +799,19 @@ cudaError_t launch_full_noise(const void *vis, const VisParams &P, uint32_t n_fr
                               double N, double *scratch, uint32_t grid, double *s2,
                               cudaStream_t s)
 {
+    const uint32_t M = P.n_in * P.n_in;
+    if (M <= FULL_SMEM_M) {
+        // the matrix in shared memory: no scratch, and as many CTAs as fit
+        const uint32_t smem = M * M * 8;
+        int dev = 0, sms = 148, per = 1;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, full_noise_kernel, 256, smem);
+        const uint64_t ft = (uint64_t)n_freq * P.T, want = (uint64_t)sms * (per > 0 ? per : 1);
+        grid = (uint32_t)(ft < want ? ft : want);
+        full_noise_kernel<<<grid ? grid : 1, 256, smem, s>>>(vis, P, n_freq, f, N, scratch, s2);
+        return cudaGetLastError();
+    }
     full_noise_kernel<<<grid ? grid : 1, 256, 0, s>>>(vis, P, n_freq, f, N, scratch, s2);
     return cudaGetLastError();
 }

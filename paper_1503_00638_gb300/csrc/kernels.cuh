@@ -92,6 +92,7 @@ cudaError_t launch_full_noise(const void *vis, const VisParams &P, uint32_t n_fr
                               double N, double *scratch, uint32_t grid, double *s2,
                               cudaStream_t s);
 constexpr uint32_t FULL_MAX_INPUTS = 16;   // M = n^2 <= 256: one column per thread
+constexpr uint32_t FULL_SMEM_M = 64;       // up to 8 inputs the matrix sits in shared memory
 // per (freq, time) compensated c of Sec. 3.2 into P.cft (needs the tables)
 cudaError_t launch_vis_compensation(const void *vis, const VisParams &P, uint32_t n_freq,
                                     double f, double N, cudaStream_t s);
