@@ -192,8 +192,8 @@ def run_reference(args, rank):
 # -- traffic recorded from an ncu capture of the current kernel source ----------
 
 # the sources the profiled compress kernel is compiled from
-KERNEL_SOURCES = ("kernels.cu", "kernels.cuh", "codec.cuh", "common.cuh", "lz4_warp.cuh",
-                  "shuffle.cuh")
+KERNEL_SOURCES = ("kernels.cu", "kernels.cuh", "compress_fast.cuh", "codec.cuh", "common.cuh",
+                  "lz4_warp.cuh", "shuffle.cuh")
 
 
 def kernel_source_hash():

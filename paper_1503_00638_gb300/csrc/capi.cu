@@ -104,25 +104,27 @@ VisOpts vis_opts(int flags, int64_t n_freq, int64_t n_in, int64_t n_time)
 }
 
 // Whether compress takes the fast kernel (full blocks of at most 8 KiB of 4-
-// or 8-byte elements; a cube of 4-byte components also needs n_time % 16 == 0).
-bool fast_shape(const Geometry &g, uint64_t n_time, bool tslow = false)
+// or 8-byte elements; a cube of 4-byte components also needs n_time % 16 == 0,
+// and a time-slowest cube, gathered in series of 16 time samples, needs
+// n_time % 16 == 0 and blocks of a multiple of 16 samples).  The full-
+// covariance rounding (`general`) only runs in the general kernel.
+bool fast_shape(const Geometry &g, uint64_t n_time, bool tslow = false, bool general = false)
 {
-    // a time-slowest cube is gathered block by block: the general kernel
-    return !tslow && shuffle_inplace_ok(g.es, g.B) &&
-           (n_time == 0 || g.es == 8 || n_time % 16 == 0);
+    if (general || !shuffle_inplace_ok(g.es, g.B)) return false;
+    if (tslow) return n_time % 16 == 0 && ((uint64_t)g.B * g.es) % 128 == 0;
+    return n_time == 0 || g.es == 8 || n_time % 16 == 0;
 }
 
 // n_ft: entries of the per-(freq, time) compensated-c table (0 = none)
 WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint64_t n_time = 0,
                    const VisOpts &opts = VisOpts())
 {
-    const bool tslow = opts.tslow || opts.full;  // both take the general compress kernel
     WsLayout L{};
     size_t o = WS_HEADER;
     if (op == BSGPU_OP_COMPRESS || op == BSGPU_OP_COMPRESS_VIS) {
         L.state = o;
         o += r256((size_t)g.nb * 8);
-        if (g.nb && fast_shape(g, n_time, tslow)) {
+        if (g.nb && fast_shape(g, n_time, opts.tslow, opts.full)) {
             L.slots = o;
             o += (size_t)FAST_MAX_WARPS * 2 * FAST_SLOT_BYTES;
         }
@@ -431,7 +433,9 @@ static int compress_common(const void *in, const Geometry &g, int level, void *o
         int dev = 0, sms = 148;
         if (cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        uint64_t grid = (uint64_t)sms * compress_fast_blocks_per_sm(level, g.es);
+        const bool ts = vis && vis->tslow;
+        uint64_t grid = (uint64_t)sms * (ts ? compress_fast_tslow_blocks_per_sm(level, g.es)
+                                            : compress_fast_blocks_per_sm(level, g.es));
         if (grid > nfull) grid = nfull;
         if (grid > FAST_MAX_WARPS) grid = FAST_MAX_WARPS;
         CodecArgs f = a;
@@ -440,7 +444,8 @@ static int compress_common(const void *in, const Geometry &g, int level, void *o
         f.slots = reinterpret_cast<uint8_t *>(ws) + L.slots;
         f.nslot_warps = FAST_MAX_WARPS;
         f.tile_counter = reinterpret_cast<uint32_t *>((uint8_t *)ws + 4);
-        cudaError_t e = launch_compress_fast(f, (uint32_t)grid, s);
+        cudaError_t e = ts ? launch_compress_fast_tslow(f, (uint32_t)grid, s)
+                           : launch_compress_fast(f, (uint32_t)grid, s);
         if (e != cudaSuccess) return BSGPU_ERR_CUDA;
         done = nfull;
     }

@@ -102,6 +102,37 @@ BSG_D bool load_block_any(const CodecArgs &a, uint8_t *dst, uint32_t tile, uint6
     return false;
 }
 
+// Full block `tile` of a time-slowest cube ([T][F P] complex samples, T a
+// multiple of 16) into shared `dst` in time-fastest order.  The block is
+// groups of 16 consecutive time samples of one (freq, product) series, 128
+// output bytes (eight 16-byte chunks of two samples) each; lane l takes
+// groups l, l + 32, ...  Lanes run through the chunks in an order rotated by
+// m = (l / 4) mod 8, so at every step the four lanes of one 32-byte sector
+// of neighbouring series read the same time row (full sectors), and the
+// chunks the 32 lanes store fall in eight different bank groups (no shared-
+// memory conflicts).
+BSG_D void gather_tslow_block(const CodecArgs &a, uint8_t *dst, uint32_t tile, uint32_t lane)
+{
+    const VisParams &P = a.vis;
+    const uint32_t n8 = (uint32_t)(((uint64_t)a.B * a.es) >> 3);   // samples per block
+    const uint32_t c0 = tile * n8;        // complex indices of a cube are below 2^32
+    const uint64_t row = P.FP;            // one time step, in samples
+    const uint2 *src = reinterpret_cast<const uint2 *>(a.in);
+    const uint32_t m = (lane >> 2) & 7u;
+    for (uint32_t q = lane; q < n8 / 16u; q += 32) {
+        const uint32_t c = c0 + 16u * q, s = fastdiv(c, P.dT), t0 = c - s * P.T;
+        const uint2 *p = src + (uint64_t)t0 * row + s;
+        uint4 *d = reinterpret_cast<uint4 *>(dst + (size_t)128 * q);
+#pragma unroll
+        for (uint32_t k = 0; k < 8; k++) {
+            const uint32_t x = (k + m) & 7u;   // chunk x: samples t0 + 2x, t0 + 2x + 1
+            const uint2 u = __ldg(p + (uint64_t)(2 * x) * row);
+            const uint2 v = __ldg(p + (uint64_t)(2 * x + 1) * row);
+            d[x] = make_uint4(u.x, u.y, v.x, v.y);
+        }
+    }
+}
+
 // Copy len bytes from 16-byte aligned shared `s` to global `g` (any alignment):
 // byte stores up to g's next 16-byte boundary, then 16-byte stores assembled
 // from two aligned shared vectors and a funnel shift, then the ragged end.

@@ -5,7 +5,7 @@
 // bulk-copy (TMA) engine with the next block prefetched.
 #include <cuda_runtime.h>
 
-#include "codec.cuh"
+#include "compress_fast.cuh"
 
 namespace bsg {
 
@@ -318,9 +318,6 @@ uint32_t compress_fast_smem_bytes(int level)
     return level >= 1 ? FastPlan<1>::BYTES : FastPlan<0>::BYTES;
 }
 
-template <int LEVEL, int ES, bool GEN = false>
-__global__ void compress_fast_kernel(const __grid_constant__ CodecArgs a);
-
 uint32_t compress_fast_blocks_per_sm(int level, uint32_t es)
 {
     int n = 0;
@@ -341,92 +338,6 @@ uint32_t compress_fast_blocks_per_sm(int level, uint32_t es)
     return e == cudaSuccess && n > 0 ? (uint32_t)n : 1u;
 }
 
-
-// One warp per CTA, persistent, one shared buffer: bulk-copy the block in,
-// round + bit-transpose it in place through registers, LZ4-encode it into
-// this warp's staging slot in global memory (it stays in L2), publish its
-// size, and place the PREVIOUS block: by then its predecessors have long
-// published theirs, so the look-back rarely waits.  GEN (4-byte elements of a
-// cube only): int32 components or a compensated c (see round_group).
-template <int LEVEL, int ES, bool GEN>
-__global__ void __launch_bounds__(32, 20) compress_fast_kernel(const __grid_constant__ CodecArgs a)
-{
-    using L = FastPlan<LEVEL>;
-    extern __shared__ __align__(128) uint8_t sm[];
-    uint8_t *tmp = sm;
-    void *scratch = sm + L::TMP;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::TMP + r16(L::SCR));
-    const uint32_t lane = threadIdx.x & 31u;
-    if (lane == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
-    uint8_t *slot0 = a.slots + (size_t)(2 * blockIdx.x) * FAST_SLOT_BYTES;
-    uint8_t *slot1 = slot0 + FAST_SLOT_BYTES;
-    uint32_t parity = 0;
-    uint32_t ptile = ~0u, pcs = 0;  // the block waiting to be placed, in slot1
-    uint32_t tile = grab_tile(a.tile_counter, lane);
-    while (tile < a.tile_end) {
-        const uint32_t Bb = a.B;  // the fast path takes full blocks only
-        if (load_block(tmp, a.in + (uint64_t)tile * a.B * a.es, Bb * a.es, bar, lane)) {
-            if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);
-            parity ^= 1u;
-        }
-        if (ES == 2) {
-            shuffle2_inplace(tmp, Bb, lane);
-        } else if (ES == 8) {
-            if (a.vis.enabled) {
-                // one complex sample per element: round them in place first
-                const uint32_t c0 = (uint32_t)((uint64_t)tile * a.B);
-                if ((a.vis.T & 1u) == 0) {
-                    uint4 *b4 = reinterpret_cast<uint4 *>(tmp);
-                    reduce_run2(b4, b4, c0, Bb, a.vis, lane);
-                } else {
-                    uint2 *b2 = reinterpret_cast<uint2 *>(tmp);
-                    reduce_run(b2, b2, c0, Bb, a.vis, lane);
-                }
-                __syncwarp();
-            }
-            shuffle8_inplace(tmp, Bb, lane);
-        } else if (a.vis.enabled) {
-            shuffle4_inplace(tmp, Bb, lane,
-                             VisGroupRound<GEN>{&a.vis, (uint32_t)(((uint64_t)tile * a.B) >> 1)});
-        } else {
-            shuffle4_inplace(tmp, Bb, lane, NoRound{});
-        }
-        __syncwarp();
-        uint32_t cs;
-        if (LEVEL == 0 && (Bb * ES) % 128u == 0) {
-            cs = lz4_encode_bitmap_fast(tmp, Bb * ES, Bb / 8, slot0 + 4,
-                                        static_cast<uint32_t *>(scratch));
-            if (lane == 0) put_be32(slot0, cs);
-            __syncwarp();
-        } else {
-            cs = compress_encode<LEVEL, L::HBITS>(a, Bb, tmp, slot0, scratch, lane);
-        }
-        lookback_publish(a.tile_state, tile, 4ull + cs, lane);
-        const uint32_t nxt = grab_tile(a.tile_counter, lane);
-        if (ptile != ~0u) {
-            const uint64_t excl = lookback_resolve(a.tile_state, ptile, 4ull + pcs, a.status, lane);
-            compress_place(a, ptile, slot1, pcs, 12 + excl, lane);
-        }
-        __syncwarp();
-        ptile = tile;
-        pcs = cs;
-        uint8_t *t = slot0;
-        slot0 = slot1;
-        slot1 = t;
-        tile = nxt;
-        // the next load overwrites `tmp`: the async proxy follows the generic reads
-        fence_proxy_async_smem();
-        __syncwarp();
-    }
-    if (ptile != ~0u) {
-        const uint64_t excl = lookback_resolve(a.tile_state, ptile, 4ull + pcs, a.status, lane);
-        compress_place(a, ptile, slot1, pcs, 12 + excl, lane);
-    }
-}
 
 // n_elem < 8: no block; header plus the elements verbatim (rounded for a cube).
 __global__ void compress_small_kernel(const __grid_constant__ CodecArgs a)

@@ -1,0 +1,47 @@
+// The fast compress kernel for time-slowest cubes ([T][F P] samples, the
+// instrument's order before the post-acquisition reorder of Sec. 2): each
+// full block is gathered into time-fastest order in shared memory and then
+// rounded, shuffled and coded exactly like a block of a time-fastest cube.
+// Kept in its own translation unit so the in-order kernels compile without
+// the gather and the build compiles both in parallel.
+#include <cuda_runtime.h>
+
+#include "compress_fast.cuh"
+
+namespace bsg {
+
+uint32_t compress_fast_tslow_blocks_per_sm(int level, uint32_t es)
+{
+    int n = 0;
+    const uint32_t smem = compress_fast_smem_bytes(level);
+    cudaError_t e;
+    if (es == 8)
+        e = level >= 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, compress_fast_kernel<1, 8, false, true>, 32, smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, compress_fast_kernel<0, 8, false, true>, 32, smem);
+    else
+        e = level >= 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, compress_fast_kernel<1, 4, false, true>, 32, smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, compress_fast_kernel<0, 4, false, true>, 32, smem);
+    return e == cudaSuccess && n > 0 ? (uint32_t)n : 1u;
+}
+
+cudaError_t launch_compress_fast_tslow(const CodecArgs &a, uint32_t grid, cudaStream_t s)
+{
+    const uint32_t smem = compress_fast_smem_bytes(a.level);
+    if (a.es == 8)
+        return a.level >= 1
+                   ? launch_warp_kernel(compress_fast_kernel<1, 8, false, true>, smem, grid, s, a)
+                   : launch_warp_kernel(compress_fast_kernel<0, 8, false, true>, smem, grid, s, a);
+    if (a.vis.is_int || a.vis.cft)
+        return a.level >= 1
+                   ? launch_warp_kernel(compress_fast_kernel<1, 4, true, true>, smem, grid, s, a)
+                   : launch_warp_kernel(compress_fast_kernel<0, 4, true, true>, smem, grid, s, a);
+    return a.level >= 1
+               ? launch_warp_kernel(compress_fast_kernel<1, 4, false, true>, smem, grid, s, a)
+               : launch_warp_kernel(compress_fast_kernel<0, 4, false, true>, smem, grid, s, a);
+}
+
+}  // namespace bsg

@@ -45,6 +45,10 @@ CASES = [
     ("T40", synth.VisConfig(2, 12, 40, 2 ** 16, 1e-3, seed=5), 1e3),
     ("one-input", synth.VisConfig(3, 1, 5, 2 ** 10, 0.05, seed=2), 300.0),
     ("chime-slab", synth.VisConfig(4, 128, 16, 2 ** 17, 0.01, seed=6, drift=True), 2.0 ** 22),
+    # series of 32 and 48 samples: a block holds whole series, or starts and
+    # ends inside one (1024 / 48 is not whole), and the cube ends in a short block
+    ("T32", synth.VisConfig(3, 10, 32, 2 ** 15, 0.02, seed=7), 2.0 ** 16),
+    ("T48", synth.VisConfig(2, 16, 48, 2 ** 16, 0.01, seed=8, drift=True), 2.0 ** 20),
 ]
 
 
@@ -73,6 +77,13 @@ def test_fused_reorder_rounding(bs, orc, name, cfg, scale, dtype, compensate):
     ("one-input", "i32", 8, 8, 0, False),
     ("chime-slab", "f32", 4, 2048, 0, True),
     ("chime-slab", "i32", 4, 0, 1, False),
+    ("small", "f32", 8, 1024, 1, False),
+    ("T32", "f32", 4, 2048, 0, False),
+    ("T32", "i32", 8, 1024, 1, False),
+    ("T48", "f32", 4, 2048, 1, True),
+    ("T48", "f32", 8, 1024, 0, False),
+    ("T48", "i32", 4, 2048, 0, True),
+    ("T48", "f32", 4, 512, 0, False),
 ])
 def test_fused_reorder_compression(bs, orc, name, dtype, es, B, level, comp):
     cfg, scale = {c[0]: (c[1], c[2]) for c in CASES}[name]
