@@ -550,8 +550,11 @@ VARIANTS = {
                           "what": "complex64 cube, compensated f of Sec. 3.2 per sample"},
     "chime-samples8": {"dtype": "f32", "es": 8, "tslow": False, "comp": False, "full": False,
                        "what": "complex64 cube bitshuffled as 8-byte samples"},
-    "fullcov8": {"dtype": "f32", "es": 4, "tslow": False, "comp": False, "full": True,
+    "fullcov8": {"dtype": "f32", "es": 4, "tslow": False, "comp": False, "full": True, "n_in": 8,
                  "what": "8-input array, 1024 freq x 36 products x 64 time, full covariance"},
+    "fullcov16": {"dtype": "f32", "es": 4, "tslow": False, "comp": False, "full": True,
+                  "n_in": 16,
+                  "what": "16-input array, 1024 freq x 136 products x 64 time, full covariance"},
 }
 
 
@@ -562,7 +565,7 @@ def run_variant(args, rank, world, gpu_index, barrier):
     from paper_1503_00638_gb300 import bsgpu, synth
     v = VARIANTS[args.workload]
     if v["full"]:
-        cfg = synth.VisConfig(1024, 8, 64, 2 ** 16, args.f, seed=rank, rho=0.5)
+        cfg = synth.VisConfig(1024, v["n_in"], 64, 2 ** 16, args.f, seed=rank, rho=0.5)
         host = synth.visibilities_physical(cfg)
     else:
         cfg = synth.VisConfig(1024, 128, 16, 2 ** 17, args.f, seed=rank, drift=True)

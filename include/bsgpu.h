@@ -146,11 +146,14 @@ int bsgpu_reduce_precision_c64(const void *in, void *out, int64_t n_freq, int64_
  *           rad_full1-3 instead of Eq. rad_simple: for every (freq, time)
  *           sample the n^2 components left after the redundancy removal of
  *           Sec. 3.1 (Re of every product, Im of every cross product) get
- *           s^2 = 1 / (C^-1)_kk, computed in fp64 (Cholesky factorisation,
- *           then the inverse factor); q = fl32(12 f s^2).  A sample whose C
- *           is not positive definite is left unrounded.  Sec. 3.1 keeps
- *           this to arrays of a few dozen inputs at most; the workspace
- *           grows as n^4.
+ *           s^2 = 1 / (C^-1)_kk in fp64, where C^-1 is the Fisher
+ *           information N tr(E_a W E_b W) of the components (W = V^-1):
+ *           (C^-1)_kk = N W_ii^2 for Re V_ii and 2 N (W_ii W_jj +- Re(W_ij^2))
+ *           for Re / Im V_ij, from an n x n complex Cholesky factorisation
+ *           per sample; q = fl32(12 f s^2).  A sample whose C is not
+ *           positive definite (V neither positive nor negative definite) is
+ *           left unrounded.  Sec. 3.1 keeps this to arrays of a few dozen
+ *           inputs at most; the workspace holds one float per component.
  * ws: bsgpu_vis_workspace_size_ex(BSGPU_OP_REDUCE_PRECISION, ..., flags). */
 int bsgpu_reduce_precision_ex(const void *in, void *out, int dtype, int64_t n_freq,
                               int64_t n_inputs, int64_t n_time, double N, double f, int flags,

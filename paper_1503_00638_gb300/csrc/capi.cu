@@ -76,15 +76,14 @@ uint32_t persistent_grid(uint32_t smem_per_cta, uint64_t work)
 }
 
 struct WsLayout {
-    size_t state, autos, pairs, cft, qtab, fscr, offsets, slots, total;
+    size_t state, autos, pairs, cft, qtab, offsets, slots, total;
 };
 
 // What the flags of the visibility entry points add to the workspace.
 struct VisOpts {
     bool tslow = false, full = false;
     size_t n_ft = 0;                    // compensated c per (freq, time)
-    size_t qtab_bytes = 0, fscr_bytes = 0;
-    uint32_t full_grid = 0;             // CTAs of the full-covariance kernel
+    size_t qtab_bytes = 0;
 };
 
 VisOpts vis_opts(int flags, int64_t n_freq, int64_t n_in, int64_t n_time)
@@ -95,10 +94,7 @@ VisOpts vis_opts(int flags, int64_t n_freq, int64_t n_in, int64_t n_time)
     if (flags & BSGPU_VIS_COMPENSATE) o.n_ft = (size_t)n_freq * n_time;
     if (o.full) {
         const uint64_t ft = (uint64_t)n_freq * n_time, M = (uint64_t)n_in * n_in;
-        o.full_grid = (uint32_t)(ft < 256 ? ft : 256);
         o.qtab_bytes = ft * M * 4;
-        // small matrices live in shared memory: no scratch
-        o.fscr_bytes = M <= FULL_SMEM_M ? 0 : (size_t)o.full_grid * M * M * 8;
     }
     return o;
 }
@@ -141,8 +137,6 @@ WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint
         if (opts.full) {
             L.qtab = o;
             o += r256(opts.qtab_bytes);
-            L.fscr = o;
-            o += r256(opts.fscr_bytes);
         }
     }
     if (op == BSGPU_OP_DECOMPRESS) {
@@ -208,15 +202,14 @@ int vis_dtype_ok(int dtype, int flags, int64_t n_inputs = 1)
 // The tables (autos, product indices) and, when asked, the compensated c
 // per (freq, time) or the full-covariance q table: everything the rounding
 // kernels read besides the cube.
-int vis_prepare(const void *vis, const VisParams &v, const WsLayout &L, const VisOpts &o,
-                void *ws, int64_t n_freq, double N, double f, cudaStream_t s, double *s2 = nullptr)
+int vis_prepare(const void *vis, const VisParams &v, int64_t n_freq, double N, double f,
+                cudaStream_t s, double *s2 = nullptr)
 {
     cudaError_t e = launch_vis_tables(reinterpret_cast<const float *>(vis), v, (uint32_t)n_freq, s);
     if (e != cudaSuccess) return BSGPU_ERR_CUDA;
     if (v.cft) e = launch_vis_compensation(vis, v, (uint32_t)n_freq, f, N, s);
     if (e == cudaSuccess && v.qtab)
-        e = launch_full_noise(vis, v, (uint32_t)n_freq, f, N,
-                              reinterpret_cast<double *>((uint8_t *)ws + L.fscr), o.full_grid, s2, s);
+        e = launch_full_noise(vis, v, (uint32_t)n_freq, f, N, s2, s);
     return e == cudaSuccess ? BSGPU_OK : BSGPU_ERR_CUDA;
 }
 
@@ -302,7 +295,7 @@ int bsgpu_reduce_precision_ex(const void *in, void *out, int dtype, int64_t n_fr
     if (cudaMemsetAsync(ws, 0, WS_HEADER, s) != cudaSuccess) return BSGPU_ERR_CUDA;
     VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32, o,
                              (uint64_t)n_freq);
-    rc = vis_prepare(in, v, L, o, ws, n_freq, N, f, s);
+    rc = vis_prepare(in, v, n_freq, N, f, s);
     if (rc) return rc;
     // 256-thread blocks, each warp rounding runs of 1024 samples
     uint64_t runs = (n_cplx + 1023) / 1024;
@@ -345,7 +338,7 @@ int bsgpu_full_noise_var(const void *vis, int dtype, int64_t n_freq, int64_t n_i
     if (cudaMemsetAsync(ws, 0, WS_HEADER, s) != cudaSuccess) return BSGPU_ERR_CUDA;
     VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, 0.0, dtype == BSGPU_VIS_I32, o,
                              (uint64_t)n_freq);
-    return vis_prepare(vis, v, L, o, ws, n_freq, N, 0.0, s, d_s2);
+    return vis_prepare(vis, v, n_freq, N, 0.0, s, d_s2);
 }
 
 int bsgpu_reorder_time(const void *in, void *out, uint64_t n_time, uint64_t n_series,
@@ -501,7 +494,7 @@ int bsgpu_compress_vis_ex(const void *vis, int dtype, int64_t n_freq, int64_t n_
     VisParams v = vis_params(L, ws, n_inputs, n_time, n_prod, N, f, dtype == BSGPU_VIS_I32, o,
                              (uint64_t)n_freq);
     cudaStream_t s = (cudaStream_t)stream;
-    rc = vis_prepare(vis, v, L, o, ws, n_freq, N, f, s);
+    rc = vis_prepare(vis, v, n_freq, N, f, s);
     if (rc) return rc;
     return compress_common(vis, g, level, out, out_cap, d_out_bytes, d_block_offsets, ws,
                            ws_bytes, stream, &v, L);

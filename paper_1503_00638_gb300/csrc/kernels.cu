@@ -114,130 +114,156 @@ __global__ void __launch_bounds__(256) vis_compensation_kernel(const void *__res
 
 // Sec. 3.1's full covariance for small arrays (Eq. rad_full1-3) and the noise
 // of Eq. noise, s^2 = 1 / (C^-1)_kk, for every component of every (freq,
-// time) sample; q = fl32(12 f s^2) goes to P.qtab.  One CTA of 256 threads
-// per sample at a time (persistent), fp64 throughout: V in shared memory,
-// the lower triangle of C in this CTA's global scratch (M^2 doubles, L2
-// resident), a right-looking Cholesky C = L L^T with the pivot column staged
-// in shared memory, then W = L^-1 row by row, thread k owning column k
-// (row i of W overwriting row i of L once it is staged) and summing
-// (C^-1)_kk = sum_i W_ik^2.  A non-positive pivot leaves the sample
-// unrounded (q = 0).
-__global__ void __launch_bounds__(256) full_noise_kernel(const void *__restrict__ vis, VisParams P,
-                                                         uint32_t n_freq, double f, double N,
-                                                         double *scratch, double *s2_out)
+// time) sample; q = fl32(12 f s^2) goes to P.qtab (0: not rounded).
+//
+// C is the covariance of the real components (Re V_ij for i <= j, Im V_ij
+// for i < j) of the correlation matrix of circular complex Gaussian signals:
+// C_ab = tr(D_a V D_b V) / N, with D_a the Hermitian matrix for which
+// tr(D_a X) is component a of X.  Let E_b be the dual basis (X = sum_b
+// x_b E_b, so tr(D_a E_b) = delta_ab and sum_b D_b tr(E_b Y) = Y for every
+// Hermitian Y) and W = V^-1.  Then H_bc = N tr(E_b W E_c W) gives
+// (C H)_ac = sum_b tr(D_a V D_b V) tr(E_b W E_c W) = tr(D_a V (W E_c W) V)
+// = tr(D_a E_c) = delta_ac: C^-1 = H, whose diagonal is
+//   N W_ii^2                        for Re V_ii,
+//   2 N (W_ii W_jj + Re(W_ij^2))    for Re V_ij (i < j),
+//   2 N (W_ii W_jj - Re(W_ij^2))    for Im V_ij (i < j).
+// So the n x n complex inverse (O(n^3) in fp64) replaces the n^2 x n^2 real
+// one (O(n^6)).  C is positive definite exactly when V is definite (V or -V
+// positive definite: H is quadratic in W); otherwise the sample stays
+// unrounded.
+//
+// One thread per sample, 32 samples per CTA (persistent): the sample's lower
+// triangles sit in shared memory as [element][lane] (the lanes of one
+// element in consecutive words: no bank conflicts), so every lane of every
+// fp64 instruction works (on GB300 fp64 issues at a small fraction of the
+// fp32 rate, and a warp instruction costs the same whatever its lanes).
+// Per sample: V's lower triangle; Cholesky V = L L^H in place (of -V when
+// V_00 < 0); X = L^-1 in place, column by column (for column j, every L
+// entry still needed lies right of it or below the current row); W = X^H X
+// for the diagonal and for each product.  The q table is [F][M][T], so the
+// lanes' writes (consecutive times) coalesce.
+__device__ __forceinline__ uint32_t tri_el(uint32_t r, uint32_t c) { return r * (r + 1) / 2 + c; }
+
+__global__ void __launch_bounds__(32) full_noise_kernel(const void *__restrict__ vis, VisParams P,
+                                                        uint32_t n_freq, double f, double N,
+                                                        double *s2_out)
 {
-    __shared__ double Vre[FULL_MAX_INPUTS][FULL_MAX_INPUTS], Vim[FULL_MAX_INPUTS][FULL_MAX_INPUTS];
-    __shared__ uint8_t ci[256], cj[256], ca[256];   // component -> (i, j, Re/Im)
-    __shared__ double col[256];
-    extern __shared__ double smA[];   // the matrix itself when it fits (M <= 64)
-    const uint32_t n = P.n_in, M = n * n, NP = P.P, tid = threadIdx.x, nt = blockDim.x;
-    double *A = M <= FULL_SMEM_M ? smA : scratch + (size_t)blockIdx.x * M * M;
-    const double inv2N = 1.0 / (2.0 * N);
+    extern __shared__ double fsm[];
+    const uint32_t lane = threadIdx.x;
+    const uint32_t n = P.n_in, NP = P.P, M = P.M;   // NP = n (n + 1) / 2 triangle elements
+    double *Ar = fsm + lane, *Ai = fsm + 32 * NP + lane, *D = fsm + 64 * NP + lane;
     float *qtab = const_cast<float *>(P.qtab);
-    for (uint32_t p = tid; p < NP; p += nt) {
-        const uint32_t ij = P.pairs[p], i = ij & 0xffffu, j = ij >> 16;
-        ci[p] = (uint8_t)i, cj[p] = (uint8_t)j, ca[p] = 0;
-        if (i < j) {
-            const uint32_t x = NP + p - i - 1;
-            ci[x] = (uint8_t)i, cj[x] = (uint8_t)j, ca[x] = 1;
-        }
-    }
-    for (uint64_t smp = blockIdx.x; smp < (uint64_t)n_freq * P.T; smp += gridDim.x) {
-        const uint32_t fr = (uint32_t)(smp / P.T), t = (uint32_t)(smp % P.T);
-        __syncthreads();
-        for (uint32_t p = tid; p < NP; p += nt) {
-            const uint32_t ij = P.pairs[p], i = ij & 0xffffu, j = ij >> 16;
-            const size_t at = vis_src(P, ((size_t)fr * NP + p) * P.T + t) * 2;
-            double re, im;
-            if (P.is_int) {
-                re = (double)(float)reinterpret_cast<const int32_t *>(vis)[at];
-                im = (double)(float)reinterpret_cast<const int32_t *>(vis)[at + 1];
-            } else {
-                re = reinterpret_cast<const float *>(vis)[at];
-                im = reinterpret_cast<const float *>(vis)[at + 1];
-            }
-            Vre[i][j] = re, Vim[i][j] = im, Vre[j][i] = re, Vim[j][i] = -im;
-        }
-        __syncthreads();
-        // C, lower triangle (r >= c).  With X = V_ig V_jh^*, Y = V_ih V_jg^*:
-        // Re,Re: Re(X + Y); Im,Im: Re(X - Y); Re ij,Im gh: Im(Y - X); all / 2N
-        for (uint32_t e = tid; e < M * M; e += nt) {
-            const uint32_t r = e / M, c = e - r * M;
-            if (c > r) continue;
-            uint32_t i = ci[r], j = cj[r], g = ci[c], h = cj[c];
-            const uint32_t a = ca[r], b = ca[c];
-            if (a == 1 && b == 0) {  // C_{Im ij, Re gh} = C_{Re gh, Im ij}
-                uint32_t x = i; i = g; g = x;
-                x = j; j = h; h = x;
-            }
-            const double xr = Vre[i][g] * Vre[j][h] + Vim[i][g] * Vim[j][h];
-            const double xi = Vim[i][g] * Vre[j][h] - Vre[i][g] * Vim[j][h];
-            const double yr = Vre[i][h] * Vre[j][g] + Vim[i][h] * Vim[j][g];
-            const double yi = Vim[i][h] * Vre[j][g] - Vre[i][h] * Vim[j][g];
-            double v;
-            if (a == 0 && b == 0) v = xr + yr;
-            else if (a == 1 && b == 1) v = xr - yr;
-            else v = yi - xi;
-            A[(size_t)r * M + c] = v * inv2N;
-        }
-        __syncthreads();
-        bool ok = true;
-        for (uint32_t j = 0; j < M; j++) {
-            const double d = A[(size_t)j * M + j];
-            if (!(d > 0.0) || !isfinite(d)) {  // every thread sees the same value
-                ok = false;
-                break;
-            }
-            const double ljj = sqrt(d), rl = 1.0 / ljj;  // one division per column
-            for (uint32_t i = j + tid; i < M; i += nt) {
-                const double x = i == j ? ljj : A[(size_t)i * M + j] * rl;
-                A[(size_t)i * M + j] = x;
-                col[i] = x;
-            }
-            __syncthreads();
-            // trailing lower triangle, threads as a 16 x 16 grid (no index division)
-            for (uint32_t ii = j + 1 + (tid >> 4); ii < M; ii += nt >> 4) {
-                const double ci = col[ii];
-                for (uint32_t kk = j + 1 + (tid & 15u); kk <= ii; kk += 16)
-                    A[(size_t)ii * M + kk] -= ci * col[kk];
-            }
-            __syncthreads();
-        }
-        double acc = 0.0;
-        const uint32_t k = tid;
-        if (ok) {
-            // W = L^-1 row by row: row i of L is staged in `col`, then its
-            // storage takes row i of W (A[i][k] = W_ik), so thread k reads its
-            // column of W across rows at consecutive addresses (no bank
-            // conflicts between threads)
-            for (uint32_t i = 0; i < M; i++) {
-                for (uint32_t m = tid; m <= i; m += nt) col[m] = A[(size_t)i * M + m];
-                __syncthreads();
-                if (k <= i && k < M) {
-                    const double rli = 1.0 / col[i];
-                    double w;
-                    if (k == i) {
-                        w = rli;
-                    } else {
-                        double sum = 0.0;
-                        for (uint32_t m = k; m < i; m++) sum += col[m] * A[(size_t)m * M + k];
-                        w = -sum * rli;
-                    }
-                    A[(size_t)i * M + k] = w;
-                    acc += w * w;
+    const uint64_t n_smp = (uint64_t)n_freq * P.T;
+    for (uint64_t base = (uint64_t)blockIdx.x * 32; base < n_smp; base += (uint64_t)gridDim.x * 32) {
+        const uint64_t smp = base + lane;
+        const bool live = smp < n_smp;
+        const uint32_t fr = live ? (uint32_t)(smp / P.T) : 0u, t = live ? (uint32_t)(smp % P.T) : 0u;
+        bool ok = live;
+        if (live) {
+            for (uint32_t p = 0; p < NP; p++) {
+                const uint32_t ij = __ldg(P.pairs + p), i = ij & 0xffffu, j = ij >> 16;
+                const size_t at = vis_src(P, ((size_t)fr * NP + p) * P.T + t) * 2;
+                double re, im;   // the stored values (int32 through float32)
+                if (P.is_int) {
+                    re = (double)(float)__ldg(reinterpret_cast<const int32_t *>(vis) + at);
+                    im = (double)(float)__ldg(reinterpret_cast<const int32_t *>(vis) + at + 1);
+                } else {
+                    re = __ldg(reinterpret_cast<const float *>(vis) + at);
+                    im = __ldg(reinterpret_cast<const float *>(vis) + at + 1);
                 }
-                __syncthreads();
+                Ar[32 * tri_el(j, i)] = re;   // V_ji = conj(V_ij)
+                Ai[32 * tri_el(j, i)] = -im;
+            }
+            const double sg = Ar[0] < 0.0 ? -1.0 : 1.0;
+            for (uint32_t j = 0; j < n; j++) {
+                double d = sg * Ar[32 * tri_el(j, j)];
+                for (uint32_t k = 0; k < j; k++) {
+                    const double lr = Ar[32 * tri_el(j, k)], li = Ai[32 * tri_el(j, k)];
+                    d -= lr * lr + li * li;
+                }
+                if (!(d > 0.0) || !isfinite(d)) {
+                    ok = false;
+                    break;
+                }
+                const double ljj = sqrt(d), rl = 1.0 / ljj;
+                Ar[32 * tri_el(j, j)] = ljj;
+                Ai[32 * tri_el(j, j)] = 0.0;
+                D[32 * j] = rl;
+                for (uint32_t i = j + 1; i < n; i++) {
+                    // (sg V_ij - sum_{k<j} L_ik conj(L_jk)) / L_jj
+                    double sr = sg * Ar[32 * tri_el(i, j)], si = sg * Ai[32 * tri_el(i, j)];
+                    for (uint32_t k = 0; k < j; k++) {
+                        const double ar = Ar[32 * tri_el(i, k)], ai = Ai[32 * tri_el(i, k)];
+                        const double br = Ar[32 * tri_el(j, k)], bi = Ai[32 * tri_el(j, k)];
+                        sr -= ar * br + ai * bi;
+                        si -= ai * br - ar * bi;
+                    }
+                    Ar[32 * tri_el(i, j)] = sr * rl;
+                    Ai[32 * tri_el(i, j)] = si * rl;
+                }
             }
         }
-        if (k < M) {
-            const double s2 = ok ? 1.0 / acc : 0.0;
-            qtab[smp * M + k] = ok ? (float)(12.0 * f * s2) : 0.0f;
-            if (s2_out) s2_out[smp * M + k] = s2;
+        if (ok) {
+            // X_jj = 1 / L_jj, X_ij = -(sum_{j<=k<i} L_ik X_kj) / L_ii
+            for (uint32_t j = 0; j < n; j++) {
+                Ar[32 * tri_el(j, j)] = D[32 * j];
+                for (uint32_t i = j + 1; i < n; i++) {
+                    double ur = 0.0, ui = 0.0;
+                    for (uint32_t k = j; k < i; k++) {
+                        const double ar = Ar[32 * tri_el(i, k)], ai = Ai[32 * tri_el(i, k)];
+                        const double xr = Ar[32 * tri_el(k, j)], xi = Ai[32 * tri_el(k, j)];
+                        ur += ar * xr - ai * xi;
+                        ui += ar * xi + ai * xr;
+                    }
+                    const double rli = D[32 * i];
+                    Ar[32 * tri_el(i, j)] = -ur * rli;
+                    Ai[32 * tri_el(i, j)] = -ui * rli;
+                }
+            }
+            // W_ii = sum_{k >= i} |X_ki|^2 (D is free again)
+            for (uint32_t i = 0; i < n; i++) {
+                double w = 0.0;
+                for (uint32_t k = i; k < n; k++) {
+                    const double xr = Ar[32 * tri_el(k, i)], xi = Ai[32 * tri_el(k, i)];
+                    w += xr * xr + xi * xi;
+                }
+                D[32 * i] = w;
+            }
+        }
+        if (live) {
+            for (uint32_t p = 0; p < NP; p++) {
+                const uint32_t ij = __ldg(P.pairs + p), i = ij & 0xffffu, j = ij >> 16;
+                double hre = 0.0, him = 0.0;   // (C^-1)_kk of the Re and Im components
+                if (ok) {
+                    const double wi = D[32 * i];
+                    if (i == j) {
+                        hre = N * (wi * wi);
+                    } else {
+                        double wr = 0.0, wm = 0.0;   // W_ij = sum_{k >= j} conj(X_ki) X_kj
+                        for (uint32_t k = j; k < n; k++) {
+                            const double ar = Ar[32 * tri_el(k, i)], ai = Ai[32 * tri_el(k, i)];
+                            const double br = Ar[32 * tri_el(k, j)], bi = Ai[32 * tri_el(k, j)];
+                            wr += ar * br + ai * bi;
+                            wm += ar * bi - ai * br;
+                        }
+                        const double ww = wi * D[32 * j], re2 = wr * wr - wm * wm;
+                        hre = 2.0 * N * (ww + re2);
+                        him = 2.0 * N * (ww - re2);
+                    }
+                }
+                for (int part = 0; part < 2; part++) {
+                    if (part == 1 && i == j) break;
+                    const uint32_t comp = part ? NP + p - i - 1 : p;
+                    const double s2 = ok ? 1.0 / (part ? him : hre) : 0.0;
+                    qtab[((size_t)fr * M + comp) * P.T + t] = ok ? (float)(12.0 * f * s2) : 0.0f;
+                    if (s2_out) s2_out[smp * M + comp] = s2;
+                }
+            }
         }
     }
 }
 
-// Standalone precision reduction: each warp rounds runs of 1024 samples.// Standalone precision reduction: each warp rounds runs of 1024 samples.
+// Standalone precision reduction: each warp rounds runs of 1024 samples.
 __global__ void __launch_bounds__(256) reduce_precision_kernel(const uint2 *__restrict__ in,
                                                                uint2 *__restrict__ out,
                                                                uint64_t n_cplx, VisParams P)
@@ -706,24 +732,26 @@ cudaError_t launch_vis_compensation(const void *vis, const VisParams &P, uint32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_full_noise(const void *vis, const VisParams &P, uint32_t n_freq, double f,
-                              double N, double *scratch, uint32_t grid, double *s2,
-                              cudaStream_t s)
+uint32_t full_noise_smem_bytes(uint32_t n_in)
 {
-    const uint32_t M = P.n_in * P.n_in;
-    if (M <= FULL_SMEM_M) {
-        // the matrix in shared memory: no scratch, and as many CTAs as fit
-        const uint32_t smem = M * M * 8;
-        int dev = 0, sms = 148, per = 1;
-        if (cudaGetDevice(&dev) == cudaSuccess)
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, full_noise_kernel, 256, smem);
-        const uint64_t ft = (uint64_t)n_freq * P.T, want = (uint64_t)sms * (per > 0 ? per : 1);
-        grid = (uint32_t)(ft < want ? ft : want);
-        full_noise_kernel<<<grid ? grid : 1, 256, smem, s>>>(vis, P, n_freq, f, N, scratch, s2);
-        return cudaGetLastError();
-    }
-    full_noise_kernel<<<grid ? grid : 1, 256, 0, s>>>(vis, P, n_freq, f, N, scratch, s2);
+    return (2u * (n_in * (n_in + 1) / 2) + n_in) * 32u * 8u;
+}
+
+cudaError_t launch_full_noise(const void *vis, const VisParams &P, uint32_t n_freq, double f,
+                              double N, double *s2, cudaStream_t s)
+{
+    const uint32_t smem = full_noise_smem_bytes(P.n_in);
+    cudaError_t e = cudaFuncSetAttribute(full_noise_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 148, per = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, full_noise_kernel, 32, smem);
+    const uint64_t ctas = ((uint64_t)n_freq * P.T + 31) / 32;
+    const uint64_t want = (uint64_t)sms * (per > 0 ? per : 1);
+    const uint32_t grid = (uint32_t)(ctas < want ? ctas : want);
+    full_noise_kernel<<<grid ? grid : 1, 32, smem, s>>>(vis, P, n_freq, f, N, s2);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ struct VisParams {
     int is_int;             // components are int32 (else float32)
     int tslow;              // the input is time-slowest: [T][n_freq n_prod] samples
     uint32_t FP;            // n_freq n_prod (series of T samples)
-    const float *qtab;      // full-covariance q per component [n_freq][T][M], or null
+    const float *qtab;      // full-covariance q per component [n_freq][M][T], or null
     uint32_t M;             // components per sample (n_in^2) when qtab is set
     FastDiv dT, dP;         // division by T and by P
     int enabled;
@@ -33,7 +33,7 @@ __device__ __forceinline__ float vis_q_full(const VisParams &P, uint32_t f, uint
                                             uint32_t p, uint32_t i, bool im)
 {
     const uint32_t comp = im ? P.P + p - i - 1 : p;
-    return __ldg(P.qtab + ((size_t)f * P.T + t) * P.M + comp);
+    return __ldg(P.qtab + ((size_t)f * P.M + comp) * P.T + t);
 }
 
 // Input sample holding time-fastest complex index c ((f, p) series c / T,
@@ -87,12 +87,10 @@ cudaError_t launch_reorder_time(const void *in, void *out, uint64_t T, uint64_t 
                                 cudaStream_t s);
 // full-covariance noise (Eq. rad_full1-3, Eq. noise) per (freq, time): q
 // table into P.qtab and, when s2 is not null, s^2 per component [F][T][M]
-// (fp64); scratch: grid x M^2 doubles
+// (fp64)
 cudaError_t launch_full_noise(const void *vis, const VisParams &P, uint32_t n_freq, double f,
-                              double N, double *scratch, uint32_t grid, double *s2,
-                              cudaStream_t s);
-constexpr uint32_t FULL_MAX_INPUTS = 16;   // M = n^2 <= 256: one column per thread
-constexpr uint32_t FULL_SMEM_M = 64;       // up to 8 inputs the matrix sits in shared memory
+                              double N, double *s2, cudaStream_t s);
+constexpr uint32_t FULL_MAX_INPUTS = 16;   // inputs of the full-covariance noise
 // per (freq, time) compensated c of Sec. 3.2 into P.cft (needs the tables)
 cudaError_t launch_vis_compensation(const void *vis, const VisParams &P, uint32_t n_freq,
                                     double f, double N, cudaStream_t s);

@@ -1,7 +1,8 @@
 """GPU parity of the full-covariance noise (Sec. 3.1, Eq. rad_full1-3 and Eq.
-noise) and its rounding.  s^2 comes from an fp64 matrix inverse whose
-operation order differs between the GPU (Cholesky) and the oracle
-(Gauss-Jordan), so s^2 is compared to a relative 1e-9; the rounding is
+noise) and its rounding.  s^2 comes from fp64 inverses along different
+routes (the GPU: the n x n inverse of V and the closed form of (C^-1)_kk;
+the oracle: Gauss-Jordan on the n^2 x n^2 C), so s^2 is compared to a
+relative 1e-9; the rounding is
 bit-exact wherever both sides' q = fl32(12 f s^2) agree, and elsewhere the
 GPU value must be the exact rounding for its own q (q straddles a float32
 step there, and both results are correct)."""
@@ -135,6 +136,28 @@ def test_singular_samples_stay_unrounded(bs, orc):
                               np.ascontiguousarray(v[:, :, 0]).view(np.uint32))
     s2 = bs.full_noise_var(torch.from_numpy(v.copy()).cuda(), cfg.n_samp).cpu().numpy()
     assert np.all(s2[0, 1] == 0) and np.all(s2[0, 0] > 0)
+
+
+def test_definiteness_like_the_oracle(bs, orc):
+    # t = 0: V negated (negative definite: C is still positive definite and
+    # s^2 the same); t = 1: one input's auto negative and its crosses zero
+    # (indefinite: C indefinite, unrounded); t = 2: as generated
+    cfg = synth.VisConfig(1, 5, 3, 2 ** 12, 0.3, seed=13, rho=0.6)
+    v = synth.visibilities_physical(cfg)
+    ii, jj = np.triu_indices(5)
+    v[0, :, 0] = -v[0, :, 0]
+    for p, (i, j) in enumerate(zip(ii, jj)):
+        if i == 3 or j == 3:
+            v[0, p, 1] = -1.0 if i == j else 0.0
+    s2 = bs.full_noise_var(torch.from_numpy(v.copy()).cuda(), cfg.n_samp).cpu().numpy()
+    for t in range(3):
+        rc, want = orc.full_noise_var(sample_matrix(v, 5, 0, t), cfg.n_samp)
+        assert rc == (-1 if t == 1 else 0), t
+        assert np.allclose(s2[0, t], want, rtol=1e-9, atol=0), t
+    got = bs.reduce_precision(torch.from_numpy(v.copy()).cuda(), cfg.n_samp, cfg.f,
+                              full_cov=True).cpu().numpy()
+    want = orc.reduce_precision_full(v, cfg.n_samp, cfg.f)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
 
 
 def test_argument_errors(bs):

@@ -43,6 +43,61 @@ def test_inverse_against_numpy(orc):
     assert rc == -1
 
 
+def fisher_s2(V, N):
+    """s^2 = 1/(C^-1)_kk from W = V^-1 alone: C is the covariance of the real
+    components of a circular complex Gaussian correlation matrix, whose
+    inverse is the Fisher information N tr(E_a W E_b W) of those components
+    (E_a: the Hermitian matrix with a one in component a).  Its diagonal is
+    N W_ii^2 for Re V_ii and 2 N (W_ii W_jj +- Re(W_ij^2)) for Re / Im V_ij."""
+    n = V.shape[0]
+    W = np.linalg.inv(V)
+    P = n * (n + 1) // 2
+    out = np.empty(n * n)
+    p = 0
+    for i in range(n):
+        for j in range(i, n):
+            if i == j:
+                out[p] = 1.0 / (N * W[i, i].real ** 2)
+            else:
+                ww, r2 = W[i, i].real * W[j, j].real, (W[i, j] ** 2).real
+                out[p] = 1.0 / (2 * N * (ww + r2))
+                out[P + p - i - 1] = 1.0 / (2 * N * (ww - r2))
+            p += 1
+    return out
+
+
+def wishart(n, rng, scale=1.0):
+    z = rng.standard_normal((n, 3 * n)) + 1j * rng.standard_normal((n, 3 * n))
+    return scale * (z @ z.conj().T) / (3 * n)
+
+
+def test_inverse_diagonal_matches_the_fisher_closed_form(orc):
+    # the oracle inverts the n^2 x n^2 matrix of Eq. rad_full1-3; the Fisher
+    # information gives the same diagonal from the n x n inverse of V
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 3, 5, 8):
+        V = wishart(n, rng, 50.0) + np.diag(rng.uniform(1, 5, n))
+        rc, s2 = orc.full_noise_var(V, 1000.0)
+        assert rc == 0
+        assert np.allclose(s2, fisher_s2(V, 1000.0), rtol=1e-10, atol=0), n
+
+
+def test_definiteness_of_c_follows_v(orc):
+    # C is quadratic in V: -V gives the same C (positive definite), an
+    # indefinite V an indefinite C
+    rng = np.random.default_rng(12)
+    V = wishart(4, rng, 10.0) + np.eye(4)
+    rc, s2 = orc.full_noise_var(V, 500.0)
+    rcn, s2n = orc.full_noise_var(-V, 500.0)
+    assert rc == 0 and rcn == 0 and np.allclose(s2, s2n, rtol=1e-12)
+    U = V.copy()
+    U[2, :] = 0
+    U[:, 2] = 0
+    U[2, 2] = -3.0      # one negative eigenvalue
+    rcu, s2u = orc.full_noise_var(U, 500.0)
+    assert rcu == -1 and np.all(s2u == 0)
+
+
 def simulate_components(R, N, trials, rng):
     """Visibility components of `trials` integrations of N samples of
     complex Gaussian voltages with covariance R, in the oracle's order."""
