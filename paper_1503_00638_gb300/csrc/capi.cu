@@ -102,11 +102,10 @@ VisOpts vis_opts(int flags, int64_t n_freq, int64_t n_in, int64_t n_time)
 // Whether compress takes the fast kernel (full blocks of at most 8 KiB of 4-
 // or 8-byte elements; a cube of 4-byte components also needs n_time % 16 == 0,
 // and a time-slowest cube, gathered in series of 16 time samples, needs
-// n_time % 16 == 0 and blocks of a multiple of 16 samples).  The full-
-// covariance rounding (`general`) only runs in the general kernel.
-bool fast_shape(const Geometry &g, uint64_t n_time, bool tslow = false, bool general = false)
+// n_time % 16 == 0 and blocks of a multiple of 16 samples).
+bool fast_shape(const Geometry &g, uint64_t n_time, bool tslow = false)
 {
-    if (general || !shuffle_inplace_ok(g.es, g.B)) return false;
+    if (!shuffle_inplace_ok(g.es, g.B)) return false;
     if (tslow) return n_time % 16 == 0 && ((uint64_t)g.B * g.es) % 128 == 0;
     return n_time == 0 || g.es == 8 || n_time % 16 == 0;
 }
@@ -120,7 +119,7 @@ WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint
     if (op == BSGPU_OP_COMPRESS || op == BSGPU_OP_COMPRESS_VIS) {
         L.state = o;
         o += r256((size_t)g.nb * 8);
-        if (g.nb && fast_shape(g, n_time, opts.tslow, opts.full)) {
+        if (g.nb && fast_shape(g, n_time, opts.tslow)) {
             L.slots = o;
             o += (size_t)FAST_MAX_WARPS * 2 * FAST_SLOT_BYTES;
         }

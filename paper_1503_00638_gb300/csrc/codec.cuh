@@ -616,6 +616,25 @@ BSG_D void round_group(const VisParams &P, uint32_t (&a)[32], uint32_t rot, uint
 // Precision reduction of one group of 32 components (16 consecutive time
 // samples of one product, the time axis being a multiple of 16) held in
 // registers in lane-rotated chunk order: a[m] is component (m + 4 (g & 7)) mod 32.
+// With the full-covariance table, each component has its own q (the Re and
+// Im rows of the product at the group's 16 times).
+BSG_D void round_group_full(const VisParams &P, uint32_t (&a)[32], uint32_t rot, const float *qre,
+                            const float *qim, bool is_auto)
+{
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const uint32_t c = (k + rot) & 7u;   // chunk c: samples t0 + 2c, t0 + 2c + 1
+        const float2 qr = __ldg(reinterpret_cast<const float2 *>(qre + 2 * c));
+        const float2 qi = __ldg(reinterpret_cast<const float2 *>(qim + 2 * c));
+        a[4 * k] = reduce_bits(a[4 * k], qr.x, P.is_int);
+        a[4 * k + 2] = reduce_bits(a[4 * k + 2], qr.y, P.is_int);
+        if (!is_auto) {   // the imaginary part of an auto stays
+            a[4 * k + 1] = reduce_bits(a[4 * k + 1], qi.x, P.is_int);
+            a[4 * k + 3] = reduce_bits(a[4 * k + 3], qi.y, P.is_int);
+        }
+    }
+}
+
 template <bool GEN>
 struct VisGroupRound {
     const VisParams *P;
@@ -631,6 +650,13 @@ struct VisGroupRound {
         const uint32_t ij = __ldg(P->pairs + p);
         const uint32_t i = ij & 0xffffu, j = ij >> 16;
         const bool is_auto = i == j;
+        if (GEN && P->qtab) {
+            // full covariance: the q rows of the Re and Im components ([F][M][T])
+            const float *qre = P->qtab + ((size_t)f * P->M + p) * P->T + t0;
+            const float *qim = P->qtab + ((size_t)f * P->M + P->P + p - i - 1) * P->T + t0;
+            round_group_full(*P, a, rot, qre, is_auto ? qre : qim, is_auto);
+            return;
+        }
         const float *ai = P->autos + (size_t)(f * P->n_in + i) * P->T + t0;
         const float *aj = P->autos + (size_t)(f * P->n_in + j) * P->T + t0;
         round_group<GEN>(*P, a, rot, f, t0, ai, aj, is_auto);

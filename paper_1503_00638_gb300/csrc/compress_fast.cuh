@@ -12,8 +12,9 @@ namespace bsg {
 // through registers, LZ4-encode it into this warp's staging slot in global
 // memory (it stays in L2), publish its size, and place the PREVIOUS block: by
 // then its predecessors have long published theirs, so the look-back rarely
-// waits.  GEN (4-byte elements of a cube only): int32 components or a
-// compensated c (see round_group).
+// waits.  GEN (4-byte elements of a cube only): int32 components, a
+// compensated c or the full-covariance q table (see round_group and
+// round_group_full).
 template <int LEVEL, int ES, bool GEN = false, bool TS = false>
 __global__ void __launch_bounds__(32, 20) compress_fast_kernel(const __grid_constant__ CodecArgs a)
 {

@@ -852,7 +852,7 @@ cudaError_t launch_compress_fast(const CodecArgs &a, uint32_t grid, cudaStream_t
     if (a.es == 2)
         return a.level >= 1 ? launch_warp_kernel(compress_fast_kernel<1, 2>, smem, grid, s, a)
                             : launch_warp_kernel(compress_fast_kernel<0, 2>, smem, grid, s, a);
-    if (a.vis.enabled && (a.vis.is_int || a.vis.cft))
+    if (a.vis.enabled && (a.vis.is_int || a.vis.cft || a.vis.qtab))
         return a.level >= 1 ? launch_warp_kernel(compress_fast_kernel<1, 4, true>, smem, grid, s, a)
                             : launch_warp_kernel(compress_fast_kernel<0, 4, true>, smem, grid, s, a);
     return a.level >= 1 ? launch_warp_kernel(compress_fast_kernel<1, 4>, smem, grid, s, a)

@@ -35,7 +35,7 @@ cudaError_t launch_compress_fast_tslow(const CodecArgs &a, uint32_t grid, cudaSt
         return a.level >= 1
                    ? launch_warp_kernel(compress_fast_kernel<1, 8, false, true>, smem, grid, s, a)
                    : launch_warp_kernel(compress_fast_kernel<0, 8, false, true>, smem, grid, s, a);
-    if (a.vis.is_int || a.vis.cft)
+    if (a.vis.is_int || a.vis.cft || a.vis.qtab)
         return a.level >= 1
                    ? launch_warp_kernel(compress_fast_kernel<1, 4, true, true>, smem, grid, s, a)
                    : launch_warp_kernel(compress_fast_kernel<0, 4, true, true>, smem, grid, s, a);

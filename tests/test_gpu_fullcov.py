@@ -106,10 +106,15 @@ def test_rounding(bs, orc, name, cfg, scale):
     check_rounding(orc, v, got, s2, cfg)
 
 
-@pytest.mark.parametrize("es,B,tslow", [(4, 2048, False), (8, 1024, True), (4, 96, False)])
-def test_compression(bs, orc, es, B, tslow):
+@pytest.mark.parametrize("es,B,tslow,scale", [(4, 2048, False, 0), (8, 1024, True, 0),
+                                              (4, 96, False, 0), (4, 2048, False, 2.0 ** 16),
+                                              (4, 1024, True, 2.0 ** 12), (8, 1024, False, 0)])
+def test_compression(bs, orc, es, B, tslow, scale):
+    # full blocks of 4-byte components take the fast kernel's per-component
+    # q rows (float and int32, in order and time-slowest), 8-byte samples its
+    # per-sample path, B = 96 the general kernel
     cfg = synth.VisConfig(2, 8, 16, 2 ** 14, 0.02, seed=9, rho=0.4)
-    v = synth.visibilities_physical(cfg)
+    v = cube(cfg, scale)
     d = torch.from_numpy(v.copy()).cuda()
     rounded = bs.reduce_precision(d, cfg.n_samp, cfg.f, full_cov=True).cpu().numpy()
     src = torch.from_numpy(np.ascontiguousarray(np.moveaxis(v, 2, 0))).cuda() if tslow else d
