@@ -25,8 +25,16 @@ BSG_HD uint32_t lz4_bound(uint32_t n) { return n + n / 255u + 16u; }
 // bytes): skips quickly through incompressible bit rows.
 constexpr uint32_t LZ4_ACCEL_WINDOWS = 4;
 
-// Shortest match the GPU encoder emits (the format allows 4).
+// Shortest match the GPU encoders emit (the format allows 4): two words at
+// level 1, three at level 0.  A short match saves a few bytes but costs a
+// whole sequence, and the number of sequences bounds both the level-0 parse
+// and the decoder; matches of two words are a third of the level-0 sequences
+// of bitshuffled visibilities but carry about 2 % of the matched bytes.
 constexpr uint32_t LZ4_GPU_MINMATCH = 8;
+constexpr uint32_t LZ4_L0_MINWORDS = 3;
+constexpr uint32_t LZ4_L0_MINMATCH = 4 * LZ4_L0_MINWORDS;
+template <int LEVEL>
+constexpr uint32_t LZ4_MINMATCH_OF = LEVEL >= 1 ? LZ4_GPU_MINMATCH : LZ4_L0_MINMATCH;
 
 #if defined(__CUDACC__) || defined(BSG_WARP_EMU)
 
@@ -232,9 +240,8 @@ BSG_D uint32_t lz4_emit_last(uint8_t *dst, uint32_t o, const uint8_t *src, uint3
 }
 
 // Encode src[0, S) (word aligned, readable up to S + 8) into dst (capacity
-// lz4_bound(S)), taking only matches of at least LZ4_GPU_MINMATCH bytes:
-// short matches save a byte or two each but cost a whole sequence, and the
-// sequence count is what bounds the decoder's speed.
+// lz4_bound(S)), taking only matches of at least LZ4_MINMATCH_OF<LEVEL>
+// bytes.
 //
 // Each step probes 32 word-aligned positions p at once.  Candidates:
 //  * the same column of the previous bit-row, p - rowlen (a bit-row repeating
@@ -246,8 +253,8 @@ BSG_D uint32_t lz4_emit_last(uint8_t *dst, uint32_t o, const uint8_t *src, uint3
 //    the highest lane of each hash group, so nothing depends on scheduling);
 //    after LZ4_ACCEL_WINDOWS fruitless steps the probe stride doubles (to 16
 //    bytes at most).
-// The first position whose candidate agrees on 8 bytes is taken, extended
-// back by up to 3 bytes and forward warp-wide.  Returns the compressed size,
+// The first position whose candidate agrees on the minimum match is taken,
+// extended back by up to 3 bytes and forward warp-wide.  Returns the compressed size,
 // or 0xffffffff if the progress guard tripped (cannot happen for valid sizes).
 template <int LEVEL, int HBITS>
 BSG_D uint32_t lz4_encode_warp(const uint8_t *src, uint32_t S, uint32_t rowlen, uint8_t *dst,
@@ -264,10 +271,11 @@ BSG_D uint32_t lz4_encode_warp(const uint8_t *src, uint32_t S, uint32_t rowlen, 
     }
     if (rowlen & 3u) rowlen = 0;
     uint32_t anchor = 0, o = 0;
-    if (S >= LZ4_MFLIMIT + 1) {
-        // a probe at p verifies 8 bytes, so it must end by the match-end bound
-        // (p + 8 <= S - 5), which is also below the last allowed match start
-        const uint32_t mflimit = S - LZ4_LASTLITERALS - LZ4_GPU_MINMATCH;
+    if (S >= LZ4_MFLIMIT + 1 && S >= LZ4_LASTLITERALS + LZ4_MINMATCH_OF<LEVEL>) {
+        // a probe at p verifies MM bytes, so it must end by the match-end
+        // bound (p + MM <= S - 5), which is also below the last allowed match start
+        constexpr uint32_t MM = LZ4_MINMATCH_OF<LEVEL>;
+        const uint32_t mflimit = S - LZ4_LASTLITERALS - MM;
         const uint32_t matchlimit = S - LZ4_LASTLITERALS;  // match end bound
         uint32_t pos = 0, fails = 0;
         const uint32_t guard = S / 4 + 8;
@@ -284,12 +292,17 @@ BSG_D uint32_t lz4_encode_warp(const uint8_t *src, uint32_t S, uint32_t rowlen, 
             const uint32_t wi = p >> 2;
             const uint32_t w0 = valid ? s32[wi] : 0u;
             const uint32_t w1 = valid ? s32[wi + 1] : 0u;
+            static_assert(MM == 8 || MM == 12, "probes verify two or three words");
+            const uint32_t w2 = (MM > 8 && valid) ? s32[wi + 2] : 0u;
             uint32_t off = 0;
             if (valid && rowlen && p >= rowlen) {
                 const uint32_t ri = (p - rowlen) >> 2;
-                if (s32[ri] == w0 && s32[ri + 1] == w1) off = rowlen;
+                if (s32[ri] == w0 && s32[ri + 1] == w1 && (MM <= 8 || s32[ri + 2] == w2))
+                    off = rowlen;
             }
-            if (valid && off == 0 && p >= 4 && w1 == w0 && s32[wi - 1] == w0) off = 4;
+            if (valid && off == 0 && p >= 4 && w1 == w0 && (MM <= 8 || w2 == w0) &&
+                s32[wi - 1] == w0)
+                off = 4;
             if (LEVEL >= 1) {
                 const uint32_t h = (w0 * 2654435761u) >> (32 - HBITS);
                 const uint32_t grp = __match_any_sync(FULL, valid ? h : 0x80000000u);
@@ -324,7 +337,7 @@ BSG_D uint32_t lz4_encode_warp(const uint8_t *src, uint32_t S, uint32_t rowlen, 
                 if (mp > anchor && mp > moff && src[mp - 1] == src[mp - 1 - moff]) mp--;
             }
             const uint32_t mc = mp - moff;
-            uint32_t len = p0 + 8 - mp;
+            uint32_t len = p0 + MM - mp;   // the verified bytes, and the backed-up ones
             // extend forward, 128 bytes per step
             for (uint32_t g2 = 0; g2 < S; g2 += 128) {
                 const uint32_t q = mp + len + 4 * lane;
@@ -378,12 +391,12 @@ BSG_D uint32_t bitmap_first_zero(const uint32_t *E, uint32_t start, uint32_t cap
     return cap;
 }
 
-// Level-0 encoder (same parse rule as lz4_encode_warp<0>: 8-byte matches at
-// word-aligned positions against the previous bit-row or the previous word,
-// extended back up to 3 bytes and forward), driven by two word-equality
-// bitmaps built in one parallel pass:
+// Level-0 encoder (same parse rule as lz4_encode_warp<0>: matches of at least
+// LZ4_L0_MINMATCH bytes at word-aligned positions against the previous bit-row
+// or the previous word, extended back up to 3 bytes and forward), driven by
+// two word-equality bitmaps built in one parallel pass:
 //   Erow bit w: word w equals word w - rowlen/4;  Erun bit w: word w equals w - 1.
-// A candidate at word w needs bits w and w+1 (8 bytes); a match then covers
+// A candidate at word w needs bits w .. w + LZ4_L0_MINWORDS - 1; a match then covers
 // every following word whose bit is set, plus the equal leading bytes of the
 // first word that differs.  The serial part of the parse is a handful of
 // bitmap scans per sequence instead of a probe loop.  S must be a multiple of
@@ -417,8 +430,8 @@ BSG_D uint32_t lz4_encode_bitmap(const uint8_t *src, uint32_t S, uint32_t rowlen
     }
     __syncwarp();
     uint32_t anchor = 0, o = 0;
-    if (S >= LZ4_MFLIMIT + 1) {
-        const uint32_t wlim = (S - LZ4_LASTLITERALS - LZ4_GPU_MINMATCH) / 4;  // last probe word
+    if (S >= LZ4_MFLIMIT + 1 && S >= LZ4_LASTLITERALS + LZ4_L0_MINMATCH) {
+        const uint32_t wlim = (S - LZ4_LASTLITERALS - LZ4_L0_MINMATCH) / 4;  // last probe word
         const uint32_t matchlimit = S - LZ4_LASTLITERALS;                    // match end bound
         uint32_t pos = 0;
         for (uint32_t guard = 0; guard <= NW; guard++) {
@@ -431,8 +444,14 @@ BSG_D uint32_t lz4_encode_bitmap(const uint8_t *src, uint32_t S, uint32_t rowlen
                 uint32_t crow = 0, crun = 0;
                 if (q <= (wlim >> 5)) {
                     const uint32_t r0 = Erow[q], r1 = Erow[q + 1], u0 = Erun[q], u1 = Erun[q + 1];
-                    crow = r0 & ((r0 >> 1) | (r1 << 31));
-                    crun = u0 & ((u0 >> 1) | (u1 << 31));
+                    // bits w .. w + LZ4_L0_MINWORDS - 1 all set
+                    crow = r0;
+                    crun = u0;
+#pragma unroll
+                    for (uint32_t k = 1; k < LZ4_L0_MINWORDS; k++) {
+                        crow &= (r0 >> k) | (r1 << (32 - k));
+                        crun &= (u0 >> k) | (u1 << (32 - k));
+                    }
                     uint32_t keep = ~0u;
                     if (q == (w0 >> 5)) keep &= ~0u << (w0 & 31u);
                     if (q == (wlim >> 5)) keep &= (wlim & 31u) == 31u ? ~0u : ((2u << (wlim & 31u)) - 1u);
@@ -455,7 +474,8 @@ BSG_D uint32_t lz4_encode_bitmap(const uint8_t *src, uint32_t S, uint32_t rowlen
             const uint32_t p0 = 4 * w;
             // whole words that still agree, then the agreeing bytes of the next
             const uint32_t cap = matchlimit / 4;
-            const uint32_t wz = bitmap_first_zero(isrow ? Erow : Erun, w + 2, cap, lane);
+            const uint32_t wz =
+                bitmap_first_zero(isrow ? Erow : Erun, w + LZ4_L0_MINWORDS, cap, lane);
             uint32_t len = 4 * (wz - w);
             if (4 * wz < matchlimit) {
                 const uint32_t x = s32[wz] ^ s32[wz - off / 4];
@@ -566,7 +586,8 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
             }
         }
     }
-    // candidate bitmaps: bits w and w + 1 both set (8 equal bytes)
+    // candidate bitmaps: bits w .. w + LZ4_L0_MINWORDS - 1 all set (LZ4_L0_MINMATCH
+    // equal bytes)
     uint32_t Crow[2], Crun[2];
 #pragma unroll
     for (int j = 0; j < 2; j++) {
@@ -577,8 +598,13 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
             nr = nr1;
             nu = nu1;
         }
-        Crow[j] = Erow[j] & ((Erow[j] >> 1) | (nr << 31));
-        Crun[j] = Erun[j] & ((Erun[j] >> 1) | (nu << 31));
+        Crow[j] = Erow[j];
+        Crun[j] = Erun[j];
+#pragma unroll
+        for (uint32_t k = 1; k < LZ4_L0_MINWORDS; k++) {
+            Crow[j] &= (Erow[j] >> k) | (nr << (32 - k));
+            Crun[j] &= (Erun[j] >> k) | (nu << (32 - k));
+        }
     }
     const uint32_t Cany[2] = {Crow[0] | Crun[0], Crow[1] | Crun[1]};
     const uint32_t Zrow[2] = {~Erow[0], ~Erow[1]}, Zrun[2] = {~Erun[0], ~Erun[1]};
@@ -592,8 +618,8 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
     __syncwarp();
 
     uint32_t anchor = 0, o = 0;
-    if (S >= LZ4_MFLIMIT + 1) {
-        const uint32_t wlim = (S - LZ4_LASTLITERALS - LZ4_GPU_MINMATCH) / 4;
+    if (S >= LZ4_MFLIMIT + 1 && S >= LZ4_LASTLITERALS + LZ4_L0_MINMATCH) {
+        const uint32_t wlim = (S - LZ4_LASTLITERALS - LZ4_L0_MINMATCH) / 4;
         const uint32_t matchlimit = S - LZ4_LASTLITERALS;
         const uint32_t cap = matchlimit / 4;
         uint32_t pos = 0;
@@ -611,8 +637,8 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
                 // the previous bit-row wins a tie
                 const uint32_t isrow = (sCrow[w >> 5] >> (w & 31u)) & 1u;
                 const uint32_t off = isrow ? rowlen : 4u;
-                uint32_t wz = smap_first_set(isrow ? sZrow : sZrun, isrow ? nZrow : nZrun, w + 2,
-                                             cap - 1);
+                uint32_t wz = smap_first_set(isrow ? sZrow : sZrun, isrow ? nZrow : nZrun,
+                                             w + LZ4_L0_MINWORDS, cap - 1);
                 if (wz == ~0u) wz = cap;
                 uint32_t len = 4 * (wz - w);
                 if (4 * wz < matchlimit) {
