@@ -99,6 +99,21 @@ BSG_D void compress_tiny(const CodecArgs &a, uint32_t lane)
 // Bit-transpose block `tile` of chunk `ch` into `tmp`: in place through
 // registers after a bulk copy when the shape allows, else straight from
 // global memory by the byte-wise path (a chunk's shortened last block).
+// The in-place transposes as calls of their own, so that each is
+// register-allocated alone rather than all three inside one kernel.
+__device__ __noinline__ void batch_shuffle2(uint8_t *tmp, uint32_t Bb, uint32_t lane)
+{
+    shuffle2_inplace(tmp, Bb, lane);
+}
+__device__ __noinline__ void batch_shuffle4(uint8_t *tmp, uint32_t Bb, uint32_t lane)
+{
+    shuffle4_inplace(tmp, Bb, lane, NoRound{});
+}
+__device__ __noinline__ void batch_shuffle8(uint8_t *tmp, uint32_t Bb, uint32_t lane)
+{
+    shuffle8_inplace(tmp, Bb, lane);
+}
+
 BSG_D void batch_prepare(const BatchChunk &ch, uint32_t tile, uint32_t Bb, uint8_t *tmp,
                          uint64_t *bar, uint32_t &parity, int *status, uint32_t lane)
 {
@@ -116,11 +131,11 @@ BSG_D void batch_prepare(const BatchChunk &ch, uint32_t tile, uint32_t Bb, uint8
         parity ^= 1u;
     }
     if (es == 2)
-        shuffle2_inplace(tmp, Bb, lane);
+        batch_shuffle2(tmp, Bb, lane);
     else if (es == 4)
-        shuffle4_inplace(tmp, Bb, lane, NoRound{});
+        batch_shuffle4(tmp, Bb, lane);
     else
-        shuffle8_inplace(tmp, Bb, lane);
+        batch_shuffle8(tmp, Bb, lane);
     __syncwarp();
 }
 
@@ -262,6 +277,21 @@ BSG_D bool batch_decode(const BatchArgs &b, uint32_t c, uint32_t tile, const Dec
     return good;
 }
 
+// The in-place un-transposes as calls of their own, so that each is
+// register-allocated alone rather than all three inside one kernel.
+__device__ __noinline__ void batch_unshuffle2(uint8_t *buf, uint32_t Bb, uint32_t lane)
+{
+    unshuffle2_inplace(buf, Bb, lane);
+}
+__device__ __noinline__ void batch_unshuffle4(uint8_t *buf, uint32_t Bb, uint32_t lane)
+{
+    unshuffle4_inplace(buf, Bb, lane);
+}
+__device__ __noinline__ void batch_unshuffle8(uint8_t *buf, uint32_t Bb, uint32_t lane)
+{
+    unshuffle8_inplace(buf, Bb, lane);
+}
+
 // One warp per CTA, persistent, one shared buffer decoded in place (as
 // decompress_inplace_kernel): per item, wait for its stream bytes, LZ4-decode,
 // un-transpose and store, then fetch the next item's bytes (of whichever chunk
@@ -307,11 +337,11 @@ __global__ void __launch_bounds__(32, 20) decompress_batch_kernel(const __grid_c
             uint8_t *dst = ch.out + (uint64_t)tile * ch.B * es;
             if (good && unshuffle_inplace_ok(es, Bb)) {
                 if (es == 2)
-                    unshuffle2_inplace(buf, Bb, lane);
+                    batch_unshuffle2(buf, Bb, lane);
                 else if (es == 4)
-                    unshuffle4_inplace(buf, Bb, lane);
+                    batch_unshuffle4(buf, Bb, lane);
                 else
-                    unshuffle8_inplace(buf, Bb, lane);
+                    batch_unshuffle8(buf, Bb, lane);
                 __syncwarp();
                 if ((S & 15u) == 0 && ((uintptr_t)dst & 15u) == 0) {
                     fence_proxy_async_smem();
