@@ -65,7 +65,7 @@ def parse():
                    help="frequencies of the cube (1024 = the full workload; fewer only for "
                         "profiling runs)")
     p.add_argument("--workload", default="chime",
-                   choices=["chime", "batch", "serve"] + sorted(VARIANTS))
+                   choices=["chime", "batch", "serve", "shuffle"] + sorted(VARIANTS))
     p.add_argument("--requests", type=int, default=3000,
                    help="serve workload: requests per arrival-rate point")
     p.add_argument("--chunks", type=int, default=4096,
@@ -761,6 +761,89 @@ def run_variant(args, rank, world, gpu_index, barrier):
         print(json.dumps(line), flush=True)
 
 
+def run_shuffle(args, rank, world, gpu_index, barrier):
+    """Bitshuffle and un-Bitshuffle alone (Sec. 4.2), timed separately on
+    random walks of 1-, 2-, 4- and 8-byte elements (1 GiB each, 8 KiB
+    blocks): every byte is read once and written once, so these kernels
+    are HBM-bound."""
+    import torch
+    import torch.distributed as dist
+    from paper_1503_00638_gb300 import bsgpu, synth
+    nbytes = 1 << 30
+    stream = torch.cuda.current_stream()
+    hbm, peak_kind = peaks()
+    per_es, fwd_ms, inv_ms = {}, [], []
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+    t_soak0 = time.time()
+    ok_all = True
+    for es in (1, 2, 4, 8):
+        x = synth.random_walk_torch(nbytes // es, es, seed=rank * 16 + es)
+        if x.element_size() != es:
+            x = x.view({1: torch.uint8, 2: torch.int16, 4: torch.int32, 8: torch.int64}[es])
+        B = 8192 // es
+        y, z = torch.empty_like(x), torch.empty_like(x)
+        for _ in range(args.warmup):
+            bsgpu.bitshuffle(x, B, out=y)
+            bsgpu.bitunshuffle(y, B, out=z)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            evs[k][0].record(stream)
+            bsgpu.bitshuffle(x, B, out=y)
+            evs[k][1].record(stream)
+            bsgpu.bitunshuffle(y, B, out=z)
+            evs[k][2].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        f_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+        i_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+        ok = bool(torch.equal(x, z))
+        ok_all &= ok
+        fwd_ms.append(f_ms)
+        inv_ms.append(i_ms)
+        per_es[str(es)] = {"shuffle_gbs": nbytes / (f_ms / 1e3) / 1e9,
+                           "unshuffle_gbs": nbytes / (i_ms / 1e3) / 1e9,
+                           "shuffle_frac": 2 * nbytes / (f_ms / 1e3) / 1e9 / hbm,
+                           "unshuffle_frac": 2 * nbytes / (i_ms / 1e3) / 1e9 / hbm,
+                           "round_trip_ok": ok}
+        del x, y, z
+        torch.cuda.empty_cache()
+    t_wall1 = time.time()
+    clk = clocks.summary(t_soak0, t_wall1)
+    clocks.stop()
+    step_ms = sum(fwd_ms) + sum(inv_ms)
+    t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms = float(t.item())
+    f4 = fwd_ms[2]
+    line = {
+        "metric": "bitshuffle + unshuffle GB/s (uncompressed bytes) & % HBM roofline",
+        "value": 4 * nbytes * world / (step_ms / 1e3) / 1e9,
+        "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "shuffle: random walks x_{t+1} = x_t +- 2^k, k ~ U{0..6}, of 1-, "
+                               "2-, 4- and 8-byte integers, 1 GiB each, 8 KiB blocks",
+                   "l2": "inputs (1.07 GB) larger than L2; no flush",
+                   "step": "Bitshuffle + un-Bitshuffle of each of the four arrays",
+                   "parallelism": f"replicas x{world}"},
+        "per_elem_size": per_es, "round_trip_ok": ok_all,
+        "roofline": {"bound": "hbm", "kernel": "shuffle_kernel (4-byte elements)",
+                     "achieved": 2 * nbytes / (f4 / 1e3) / 1e9, "peak": hbm,
+                     "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": 2 * nbytes / (f4 / 1e3) / 1e9 / hbm, "traffic": None,
+                     "algorithmic_bytes": 2 * nbytes},
+        "gpu_launches": args.steps * 8,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # -- the GPU arm ----------------------------------------------------------------
 
 def main():
@@ -800,6 +883,11 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args, rank, world, gpu_index)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if args.workload == "shuffle":
+        run_shuffle(args, rank, world, gpu_index, barrier)
         if world > 1:
             dist.destroy_process_group()
         return

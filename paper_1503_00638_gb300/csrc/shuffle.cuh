@@ -7,7 +7,9 @@
 // of 32 consecutive elements, reads them from shared memory in 16-byte chunks
 // in a lane-rotated order (conflict-free banks), transposes 32 x 32 bits in
 // registers and undoes the rotation with one funnel shift per output word.
-// Other element sizes and shapes take the byte-by-byte generic path.
+// es = 2 (B a multiple of 64) pairs words by byte permutes into the same
+// 32 x 32 transpose; es = 1 (B a multiple of 32) transposes 8 x 8 bit
+// matrices in 64-bit words.  Other shapes take the byte-by-byte generic path.
 #pragma once
 
 #include "common.cuh"
@@ -146,29 +148,6 @@ BSG_HD void unshuffle_generic(const uint8_t *src, uint8_t *dst, uint32_t Bb, uin
             v |= ((uint32_t)(src[(8 * byte + bit) * rowb + e / 8] >> (e & 7u)) & 1u) << bit;
         dst[o] = (uint8_t)v;
     }
-}
-
-// One lane's share of a block transpose; a warp calls it with lanes 0..31.
-BSG_HD void shuffle_block(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t es,
-                          uint32_t lane)
-{
-    if (es == 4 && Bb % 32u == 0)
-        shuffle4_fast(src, dst, Bb, lane);
-    else if (es == 8 && Bb % 32u == 0)
-        shuffle8_fast(src, dst, Bb, lane);
-    else
-        shuffle_generic(src, dst, Bb, es, lane);
-}
-
-BSG_HD void unshuffle_block(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t es,
-                            uint32_t lane)
-{
-    if (es == 4 && Bb % 32u == 0)
-        unshuffle4_fast(src, dst, Bb, lane);
-    else if (es == 8 && Bb % 32u == 0)
-        unshuffle8_fast(src, dst, Bb, lane);
-    else
-        unshuffle_generic(src, dst, Bb, es, lane);
 }
 
 #if defined(__CUDACC__) || defined(BSG_WARP_EMU)
@@ -346,54 +325,106 @@ BSG_HD Shuf2Sel shuf2_sel(uint32_t c)
     return c < 4 ? Shuf2Sel{0x5410u, 0x7632u} : Shuf2Sel{0x1054u, 0x3276u};
 }
 
+// Group g of 64 2-byte elements (128 bytes at grp, rot = g & 7) into a[],
+// transposed: a[r] and a[16 + r] hold bit-row r of the group's first and
+// second 32 elements, rotated left by 8 (g & 3) bits.
+BSG_D void shuf2_read_group(const uint8_t *grp, uint32_t rot, uint32_t (&a)[32])
+{
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint32_t c = (k + rot) & 7u;
+        const uint4 v = *reinterpret_cast<const uint4 *>(grp + 16u * c);
+        const uint4 w = *reinterpret_cast<const uint4 *>(grp + 16u * (c ^ 4u));
+        const Shuf2Sel sel = shuf2_sel(c);
+        const uint32_t x[4] = {v.x, v.y, v.z, v.w}, y[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            a[8 * k + 2 * i] = bperm(x[i], y[i], sel.lo);
+            a[8 * k + 2 * i + 1] = bperm(x[i], y[i], sel.hi);
+        }
+    }
+    // a[n] = P_((n + 8 rot) mod 32)
+    transpose32(a);
+}
+
+// Bit-rows r0 .. r1-1 of group g into `out` (16 bit-rows of 2 G words).
+BSG_D void shuf2_put_rows(uint8_t *out, uint32_t G, uint32_t g, const uint32_t (&a)[32], int r0,
+                          int r1)
+{
+    const uint32_t s = 8u * (g & 3u);
+#pragma unroll
+    for (int r = r0; r < r1; r++)
+        *reinterpret_cast<uint2 *>(out + 4u * (2u * G * r + 2u * g)) =
+            make_uint2(rotl(a[r], s), rotl(a[16 + r], s));
+}
+
 // Bb <= 2048 (G <= 32 groups of 64, one per lane) or Bb == 4096 (G == 64:
 // rows 0..7 of the first 32 groups fall in the first half of the buffer and
 // are written before the second groups are read; at most 48 live values).
 BSG_D void shuffle2_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
 {
     const uint32_t G = Bb / 64;
-    auto read_group = [&](uint32_t g, uint32_t (&a)[32]) {
-        const uint8_t *grp = buf + 128u * g;
-        const uint32_t rot = g & 7u;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const uint32_t c = (k + rot) & 7u;
-            const uint4 v = *reinterpret_cast<const uint4 *>(grp + 16u * c);
-            const uint4 w = *reinterpret_cast<const uint4 *>(grp + 16u * (c ^ 4u));
-            const Shuf2Sel sel = shuf2_sel(c);
-            const uint32_t x[4] = {v.x, v.y, v.z, v.w}, y[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                a[8 * k + 2 * i] = bperm(x[i], y[i], sel.lo);
-                a[8 * k + 2 * i + 1] = bperm(x[i], y[i], sel.hi);
-            }
-        }
-        // a[n] = P_((n + 8 rot) mod 32)
-        transpose32(a);
-    };
-    auto put_rows = [&](uint32_t g, const uint32_t (&a)[32], int r0, int r1) {
-        const uint32_t s = 8u * (g & 3u);
-#pragma unroll
-        for (int r = r0; r < r1; r++)
-            *reinterpret_cast<uint2 *>(buf + 4u * (2u * G * r + 2u * g)) =
-                make_uint2(rotl(a[r], s), rotl(a[16 + r], s));
-    };
     const uint32_t g0 = lane;
     uint32_t a[32];
-    if (g0 < G) read_group(g0, a);
+    if (g0 < G) shuf2_read_group(buf + 128u * g0, g0 & 7u, a);
     __syncwarp();
     if (G <= 32) {
-        if (g0 < G) put_rows(g0, a, 0, 16);
+        if (g0 < G) shuf2_put_rows(buf, G, g0, a, 0, 16);
         return;
     }
     // G == 64
-    put_rows(g0, a, 0, 8);
+    shuf2_put_rows(buf, G, g0, a, 0, 8);
     const uint32_t g1 = lane + 32u;
     uint32_t b[32];
-    read_group(g1, b);
+    shuf2_read_group(buf + 128u * g1, g1 & 7u, b);
     __syncwarp();
-    put_rows(g0, a, 8, 16);
-    put_rows(g1, b, 0, 16);
+    shuf2_put_rows(buf, G, g0, a, 8, 16);
+    shuf2_put_rows(buf, G, g1, b, 0, 16);
+}
+
+// From src to dst (Bb a multiple of 64, any number of groups).
+BSG_D void shuffle2_fast(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t G = Bb / 64;
+    for (uint32_t g = lane; g < G; g += 32) {
+        uint32_t a[32];
+        shuf2_read_group(src + 128u * g, g & 7u, a);
+        shuf2_put_rows(dst, G, g, a, 0, 16);
+    }
+}
+
+// Bit-rows r0 .. r1-1 of group g from `in` (16 bit-rows of 2 G words).
+BSG_D void unshuf2_get_rows(const uint8_t *in, uint32_t G, uint32_t g, uint32_t (&a)[32], int r0,
+                            int r1)
+{
+    const uint32_t s = 8u * (g & 3u);
+#pragma unroll
+    for (int r = r0; r < r1; r++) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(in + 4u * (2u * G * r + 2u * g));
+        a[r] = rotr(v.x, s);
+        a[16 + r] = rotr(v.y, s);
+    }
+}
+
+// The group's 64 elements from its 16 bit-rows in a[] to grp (rot = g & 7).
+BSG_D void unshuf2_store_group(uint8_t *grp, uint32_t rot, uint32_t (&a)[32])
+{
+    transpose32(a);  // a[n] = P_((n + 8 rot) mod 32)
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint32_t c = (k + rot) & 7u;
+        // P_2j = lo(w_j) | lo(w_(j+16)) << 16, P_2j+1 = hi(w_j) | hi(w_(j+16)) << 16
+        uint32_t x[4], y[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const uint32_t wj = bperm(a[8 * k + 2 * i], a[8 * k + 2 * i + 1], 0x5410u);
+            const uint32_t wj16 = bperm(a[8 * k + 2 * i], a[8 * k + 2 * i + 1], 0x7632u);
+            x[i] = c < 4 ? wj : wj16;
+            y[i] = c < 4 ? wj16 : wj;
+        }
+        *reinterpret_cast<uint4 *>(grp + 16u * c) = make_uint4(x[0], x[1], x[2], x[3]);
+        *reinterpret_cast<uint4 *>(grp + 16u * (c ^ 4u)) = make_uint4(y[0], y[1], y[2], y[3]);
+    }
 }
 
 // Inverse of shuffle2_inplace (same shapes).  With G == 64 a lane reads all
@@ -402,53 +433,136 @@ BSG_D void shuffle2_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
 BSG_D void unshuffle2_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
 {
     const uint32_t G = Bb / 64;
-    auto get_rows = [&](uint32_t g, uint32_t (&a)[32], int r0, int r1) {
-        const uint32_t s = 8u * (g & 3u);
-#pragma unroll
-        for (int r = r0; r < r1; r++) {
-            const uint2 v = *reinterpret_cast<const uint2 *>(buf + 4u * (2u * G * r + 2u * g));
-            a[r] = rotr(v.x, s);
-            a[16 + r] = rotr(v.y, s);
-        }
-    };
-    auto store_group = [&](uint32_t g, uint32_t (&a)[32]) {
-        transpose32(a);  // a[n] = P_((n + 8 rot) mod 32)
-        uint8_t *grp = buf + 128u * g;
-        const uint32_t rot = g & 7u;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const uint32_t c = (k + rot) & 7u;
-            // P_2j = lo(w_j) | lo(w_(j+16)) << 16, P_2j+1 = hi(w_j) | hi(w_(j+16)) << 16
-            uint32_t x[4], y[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const uint32_t wj = bperm(a[8 * k + 2 * i], a[8 * k + 2 * i + 1], 0x5410u);
-                const uint32_t wj16 = bperm(a[8 * k + 2 * i], a[8 * k + 2 * i + 1], 0x7632u);
-                x[i] = c < 4 ? wj : wj16;
-                y[i] = c < 4 ? wj16 : wj;
-            }
-            *reinterpret_cast<uint4 *>(grp + 16u * c) = make_uint4(x[0], x[1], x[2], x[3]);
-            *reinterpret_cast<uint4 *>(grp + 16u * (c ^ 4u)) = make_uint4(y[0], y[1], y[2], y[3]);
-        }
-    };
     const uint32_t g0 = lane;
     uint32_t a[32];
     if (G <= 32) {
-        if (g0 < G) get_rows(g0, a, 0, 16);
+        if (g0 < G) unshuf2_get_rows(buf, G, g0, a, 0, 16);
         __syncwarp();
-        if (g0 < G) store_group(g0, a);
+        if (g0 < G) unshuf2_store_group(buf + 128u * g0, g0 & 7u, a);
         return;
     }
     // G == 64
     const uint32_t g1 = lane + 32u;
     uint32_t b[32];
-    get_rows(g0, a, 0, 16);
-    get_rows(g1, b, 0, 8);
+    unshuf2_get_rows(buf, G, g0, a, 0, 16);
+    unshuf2_get_rows(buf, G, g1, b, 0, 8);
     __syncwarp();
-    store_group(g0, a);
-    get_rows(g1, b, 8, 16);
+    unshuf2_store_group(buf + 128u * g0, g0 & 7u, a);
+    unshuf2_get_rows(buf, G, g1, b, 8, 16);
     __syncwarp();
-    store_group(g1, b);
+    unshuf2_store_group(buf + 128u * g1, g1 & 7u, b);
+}
+
+// From src to dst (Bb a multiple of 64, any number of groups).
+BSG_D void unshuffle2_fast(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t G = Bb / 64;
+    for (uint32_t g = lane; g < G; g += 32) {
+        uint32_t a[32];
+        unshuf2_get_rows(src, G, g, a, 0, 16);
+        unshuf2_store_group(dst + 128u * g, g & 7u, a);
+    }
+}
+
+// 1-byte elements: 8 consecutive bytes form an 8 x 8 bit matrix (byte i =
+// element i, bit j = bit-row j); its transpose (three delta swaps, the
+// classic method for an 8 x 8 bit transpose in a 64-bit word) has in byte j
+// the output byte of bit-row j for those 8 elements.  A lane takes 32
+// elements (four such matrices, read as two 16-byte chunks in a
+// lane-alternated order) and writes one word to each of the 8 bit-rows.
+BSG_D uint64_t transpose8x8(uint64_t x)
+{
+    uint64_t t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+    x ^= t ^ (t << 7);
+    t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+    x ^= t ^ (t << 14);
+    t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+    x ^= t ^ (t << 28);
+    return x;
+}
+
+// src: Bb bytes (16-byte aligned), dst: 8 bit-rows of Bb/8 bytes; Bb % 32 == 0
+BSG_D void shuffle1_fast(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t Q = Bb / 32;  // groups of 32 elements; also words per bit-row
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t q = lane; q < Q; q += 32) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src + 32u * q);
+        const uint32_t o = q & 1u;
+        const uint4 u = s4[o], v = s4[o ^ 1u];
+        const uint4 c0 = o ? v : u, c1 = o ? u : v;
+        const uint64_t m[4] = {transpose8x8(((uint64_t)c0.y << 32) | c0.x),
+                               transpose8x8(((uint64_t)c0.w << 32) | c0.z),
+                               transpose8x8(((uint64_t)c1.y << 32) | c1.x),
+                               transpose8x8(((uint64_t)c1.w << 32) | c1.z)};
+#pragma unroll
+        for (uint32_t r = 0; r < 8; r++) {
+            uint32_t w = 0;
+#pragma unroll
+            for (uint32_t k = 0; k < 4; k++) w |= (uint32_t)((m[k] >> (8 * r)) & 0xffu) << (8 * k);
+            d32[r * Q + q] = w;
+        }
+    }
+}
+
+BSG_D void unshuffle1_fast(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t lane)
+{
+    const uint32_t Q = Bb / 32;
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
+    for (uint32_t q = lane; q < Q; q += 32) {
+        uint64_t m[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (uint32_t r = 0; r < 8; r++) {
+            const uint32_t w = s32[r * Q + q];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; k++) m[k] |= (uint64_t)((w >> (8 * k)) & 0xffu) << (8 * r);
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4; k++) m[k] = transpose8x8(m[k]);
+        const uint4 c0 = make_uint4((uint32_t)m[0], (uint32_t)(m[0] >> 32), (uint32_t)m[1],
+                                    (uint32_t)(m[1] >> 32));
+        const uint4 c1 = make_uint4((uint32_t)m[2], (uint32_t)(m[2] >> 32), (uint32_t)m[3],
+                                    (uint32_t)(m[3] >> 32));
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + 32u * q);
+        if (q & 1u) {
+            d4[1] = c1;
+            d4[0] = c0;
+        } else {
+            d4[0] = c0;
+            d4[1] = c1;
+        }
+    }
+}
+
+// One lane's share of a block transpose; a warp calls it with lanes 0..31.
+BSG_D void shuffle_block(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t es,
+                         uint32_t lane)
+{
+    if (es == 4 && Bb % 32u == 0)
+        shuffle4_fast(src, dst, Bb, lane);
+    else if (es == 8 && Bb % 32u == 0)
+        shuffle8_fast(src, dst, Bb, lane);
+    else if (es == 2 && Bb % 64u == 0)
+        shuffle2_fast(src, dst, Bb, lane);
+    else if (es == 1 && Bb % 32u == 0)
+        shuffle1_fast(src, dst, Bb, lane);
+    else
+        shuffle_generic(src, dst, Bb, es, lane);
+}
+
+BSG_D void unshuffle_block(const uint8_t *src, uint8_t *dst, uint32_t Bb, uint32_t es,
+                           uint32_t lane)
+{
+    if (es == 4 && Bb % 32u == 0)
+        unshuffle4_fast(src, dst, Bb, lane);
+    else if (es == 8 && Bb % 32u == 0)
+        unshuffle8_fast(src, dst, Bb, lane);
+    else if (es == 2 && Bb % 64u == 0)
+        unshuffle2_fast(src, dst, Bb, lane);
+    else if (es == 1 && Bb % 32u == 0)
+        unshuffle1_fast(src, dst, Bb, lane);
+    else
+        unshuffle_generic(src, dst, Bb, es, lane);
 }
 
 // Whether a block can be bit-transposed in place by the register paths above.
