@@ -765,7 +765,8 @@ def run_shuffle(args, rank, world, gpu_index, barrier):
     """Bitshuffle and un-Bitshuffle alone (Sec. 4.2), timed separately on
     random walks of 1-, 2-, 4- and 8-byte elements (1 GiB each, 8 KiB
     blocks): every byte is read once and written once, so these kernels
-    are HBM-bound."""
+    are HBM-bound.  The same arrays then go through the whole codec
+    (Bitshuffle + LZ4, Sec. 4.2.1), compress and decompress timed apart."""
     import torch
     import torch.distributed as dist
     from paper_1503_00638_gb300 import bsgpu, synth
@@ -801,15 +802,55 @@ def run_shuffle(args, rank, world, gpu_index, barrier):
         f_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
         i_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
         ok = bool(torch.equal(x, z))
-        ok_all &= ok
+        # the whole codec on the same array (Bitshuffle + LZ4 level 0 and back)
+        n = nbytes // es
+        cap, nblk = bsgpu.compress_bound(n, es, B), bsgpu.num_blocks(n, es, B)
+        cbuf = torch.empty(cap, dtype=torch.uint8, device="cuda")
+        offs = torch.empty(max(nblk, 1), dtype=torch.int64, device="cuda")
+        nbd = torch.zeros(1, dtype=torch.int64, device="cuda")
+        wsc = bsgpu.new_workspace(bsgpu.workspace_size(bsgpu.OP_COMPRESS, n, es, B))
+        wsd = bsgpu.new_workspace(bsgpu.workspace_size(bsgpu.OP_DECOMPRESS, n, es, B))
+        lib = bsgpu._lib
+
+        def comp():
+            bsgpu._check(lib.bsgpu_compress(x.data_ptr(), n, es, B, LEVEL, cbuf.data_ptr(), cap,
+                                            nbd.data_ptr(), offs.data_ptr(), wsc.data_ptr(),
+                                            wsc.numel(), stream.cuda_stream), "bsgpu_compress")
+
+        def dec(L):
+            bsgpu._check(lib.bsgpu_decompress(cbuf.data_ptr(), L, z.data_ptr(), n, es, B,
+                                              offs.data_ptr(), wsd.data_ptr(), wsd.numel(),
+                                              stream.cuda_stream), "bsgpu_decompress")
+
+        comp()
+        L = int(nbd.item())
+        for _ in range(args.warmup):
+            comp()
+            dec(L)
+        z.zero_()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            evs[k][0].record(stream)
+            comp()
+            evs[k][1].record(stream)
+            dec(L)
+            evs[k][2].record(stream)
+        torch.cuda.synchronize()
+        c_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+        d_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+        ok_c = bool(torch.equal(x, z)) and bsgpu.status(wsc) == 0 and bsgpu.status(wsd) == 0
+        ok_all &= ok and ok_c
         fwd_ms.append(f_ms)
         inv_ms.append(i_ms)
         per_es[str(es)] = {"shuffle_gbs": nbytes / (f_ms / 1e3) / 1e9,
                            "unshuffle_gbs": nbytes / (i_ms / 1e3) / 1e9,
                            "shuffle_frac": 2 * nbytes / (f_ms / 1e3) / 1e9 / hbm,
                            "unshuffle_frac": 2 * nbytes / (i_ms / 1e3) / 1e9 / hbm,
-                           "round_trip_ok": ok}
-        del x, y, z
+                           "round_trip_ok": ok,
+                           "codec_compress_gbs": nbytes / (c_ms / 1e3) / 1e9,
+                           "codec_decompress_gbs": nbytes / (d_ms / 1e3) / 1e9,
+                           "codec_ratio": L / nbytes, "codec_round_trip_ok": ok_c}
+        del x, y, z, cbuf, offs, wsc, wsd
         torch.cuda.empty_cache()
     t_wall1 = time.time()
     clk = clocks.summary(t_soak0, t_wall1)
