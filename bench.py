@@ -1109,6 +1109,10 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "compress_gbs": nbytes / (comp_avg_ms / 1e3) / 1e9,
         "decompress_gbs": nbytes / (dec_avg_ms / 1e3) / 1e9,
+        "kernel_ms": {"compress": {"mean": comp_avg_ms, "median": statistics.median(comp_ms),
+                                   "best": min(comp_ms)},
+                      "decompress": {"mean": dec_avg_ms, "median": statistics.median(dec_ms),
+                                     "best": min(dec_ms)}},
         "ratio": slen / nbytes,
         "roofline": {"bound": "hbm", "kernel": "compress_fast_kernel (fused round+shuffle+LZ4)",
                      "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
