@@ -68,7 +68,8 @@ __global__ void vis_tables_kernel(const float *__restrict__ vis, VisParams V, ui
 // float32 (each operation rounded to nearest; a negative or NaN value counts
 // as 0; no cross product gives 1), c = fl32(6 (f m) / N) in fp64.  One CTA per
 // (frequency, chunk of up to 1024 time samples); the minimum of non-negative
-// floats is taken on their bit patterns.
+// floats is taken on their bit patterns (order-free, so per-thread minima
+// merged by one atomic each give the same result as any other order).
 __global__ void __launch_bounds__(256) vis_compensation_kernel(const void *__restrict__ vis,
                                                                VisParams P, float *cft,
                                                                uint32_t n_freq, double f,
@@ -81,6 +82,42 @@ __global__ void __launch_bounds__(256) vis_compensation_kernel(const void *__res
         const uint32_t tn = P.T - t0 < 1024 ? P.T - t0 : 1024;
         for (uint32_t t = threadIdx.x; t < tn; t += blockDim.x) mins[t] = __float_as_uint(1.0f);
         __syncthreads();
+        if (!P.tslow && tn <= blockDim.x) {
+            // time-fastest cube: thread (p0, tl) takes time t0 + tl of products
+            // p0, p0 + per, ... (the lanes of a product read consecutive
+            // samples), keeps its minimum in a register and merges it once
+            const uint32_t per = blockDim.x / tn, tl = threadIdx.x % tn, p0 = threadIdx.x / tn;
+            if (p0 < per) {
+                const uint32_t t = t0 + tl;
+                const float *arow = P.autos + (size_t)fr * P.n_in * P.T + t;
+                uint32_t m = __float_as_uint(1.0f);
+#pragma unroll 4
+                for (uint32_t p = p0; p < P.P; p += per) {
+                    const uint32_t ij = __ldg(P.pairs + p);
+                    const uint32_t i = ij & 0xffffu, j = ij >> 16;
+                    if (i == j) continue;
+                    const float Ai = __ldg(arow + (size_t)i * P.T);
+                    const float Aj = __ldg(arow + (size_t)j * P.T);
+                    const size_t at = (((size_t)fr * P.P + p) * P.T + t) * 2;
+                    float re, im;
+                    if (P.is_int) {
+                        const int2 v = __ldg(reinterpret_cast<const int2 *>(vis) + at / 2);
+                        re = __int2float_rn(v.x);
+                        im = __int2float_rn(v.y);
+                    } else {
+                        const float2 v = __ldg(reinterpret_cast<const float2 *>(vis) + at / 2);
+                        re = v.x;
+                        im = v.y;
+                    }
+                    const float num = __fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im));
+                    const float den = __fmul_rn(Ai, Aj);
+                    float om = __fsub_rn(1.0f, __fdiv_rn(num, den));
+                    if (!(om >= 0.0f)) om = 0.0f;
+                    m = min(m, __float_as_uint(om));
+                }
+                atomicMin(&mins[tl], m);
+            }
+        } else
         for (uint64_t e = threadIdx.x; e < (uint64_t)P.P * tn; e += blockDim.x) {
             const uint32_t p = (uint32_t)(e / tn), t = t0 + (uint32_t)(e % tn);
             const uint32_t ij = __ldg(P.pairs + p);
