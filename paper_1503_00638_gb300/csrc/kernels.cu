@@ -91,29 +91,40 @@ __global__ void __launch_bounds__(256) vis_compensation_kernel(const void *__res
                 const uint32_t t = t0 + tl;
                 const float *arow = P.autos + (size_t)fr * P.n_in * P.T + t;
                 uint32_t m = __float_as_uint(1.0f);
-#pragma unroll 4
-                for (uint32_t p = p0; p < P.P; p += per) {
-                    const uint32_t ij = __ldg(P.pairs + p);
-                    const uint32_t i = ij & 0xffffu, j = ij >> 16;
-                    if (i == j) continue;
-                    const float Ai = __ldg(arow + (size_t)i * P.T);
-                    const float Aj = __ldg(arow + (size_t)j * P.T);
-                    const size_t at = (((size_t)fr * P.P + p) * P.T + t) * 2;
-                    float re, im;
-                    if (P.is_int) {
-                        const int2 v = __ldg(reinterpret_cast<const int2 *>(vis) + at / 2);
-                        re = __int2float_rn(v.x);
-                        im = __int2float_rn(v.y);
-                    } else {
-                        const float2 v = __ldg(reinterpret_cast<const float2 *>(vis) + at / 2);
-                        re = v.x;
-                        im = v.y;
+                // eight samples (and their product entries) are loaded before
+                // any is used, with no branch between the loads, so that they
+                // are in flight together
+                const uint2 *vrow = reinterpret_cast<const uint2 *>(vis) + (size_t)fr * P.P * P.T + t;
+                for (uint32_t pb = p0; pb < P.P; pb += 8 * per) {
+                    uint2 v[8];
+                    uint32_t ijs[8];
+#pragma unroll
+                    for (uint32_t k = 0; k < 8; k++) {
+                        const uint32_t p = pb + k * per;
+                        const bool in = p < P.P;
+                        v[k] = in ? __ldg(vrow + (size_t)p * P.T) : make_uint2(0u, 0u);
+                        ijs[k] = in ? __ldg(P.pairs + p) : 0u;   // 0: the auto (0, 0), skipped
                     }
-                    const float num = __fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im));
-                    const float den = __fmul_rn(Ai, Aj);
-                    float om = __fsub_rn(1.0f, __fdiv_rn(num, den));
-                    if (!(om >= 0.0f)) om = 0.0f;
-                    m = min(m, __float_as_uint(om));
+#pragma unroll
+                    for (uint32_t k = 0; k < 8; k++) {
+                        const uint32_t i = ijs[k] & 0xffffu, j = ijs[k] >> 16;
+                        if (i == j) continue;
+                        const float Ai = __ldg(arow + (size_t)i * P.T);
+                        const float Aj = __ldg(arow + (size_t)j * P.T);
+                        float re, im;
+                        if (P.is_int) {
+                            re = __int2float_rn((int32_t)v[k].x);
+                            im = __int2float_rn((int32_t)v[k].y);
+                        } else {
+                            re = __uint_as_float(v[k].x);
+                            im = __uint_as_float(v[k].y);
+                        }
+                        const float num = __fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im));
+                        const float den = __fmul_rn(Ai, Aj);
+                        float om = __fsub_rn(1.0f, __fdiv_rn(num, den));
+                        if (!(om >= 0.0f)) om = 0.0f;
+                        m = min(m, __float_as_uint(om));
+                    }
                 }
                 atomicMin(&mins[tl], m);
             }
