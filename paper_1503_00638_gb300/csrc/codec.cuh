@@ -254,6 +254,31 @@ BSG_D void reduce_run(const uint2 *src, uint2 *dst, uint32_t c0, uint32_t ncplx,
 // product per 16-byte access, so the product lookup and the two autos loads
 // serve both, and the auto / cross choice is a select (for an auto A_j = A_i,
 // the constant is 2c and the imaginary part is kept).
+// Round samples (t, t + 1) of product p = (i, j) (ij as in P.pairs) at
+// frequency f, held as one 16-byte value.
+BSG_D uint4 reduce_pair(uint4 v, uint32_t ij, uint32_t f, uint32_t t, const VisParams &P)
+{
+    if (P.qtab) {  // full covariance: per-component q from the table
+        const uint2 a = reduce_sample(make_uint2(v.x, v.y), ij, f, t, P);
+        const uint2 b = reduce_sample(make_uint2(v.z, v.w), ij, f, t + 1, P);
+        return make_uint4(a.x, a.y, b.x, b.y);
+    }
+    const uint32_t i = ij & 0xffffu, j = ij >> 16;
+    const uint32_t row = f * P.n_in;
+    const float2 Ai = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + i) * P.T + t));
+    const float2 Aj = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + j) * P.T + t));
+    const bool is_auto = i == j;
+    const float qa = __fmul_rn(__fmul_rn(vis_c(P, f, t, is_auto), Ai.x), Aj.x);
+    const float qb = __fmul_rn(__fmul_rn(vis_c(P, f, t + 1, is_auto), Ai.y), Aj.y);
+    v.x = reduce_bits(v.x, qa, P.is_int);
+    v.z = reduce_bits(v.z, qb, P.is_int);
+    if (!is_auto) {
+        v.y = reduce_bits(v.y, qa, P.is_int);
+        v.w = reduce_bits(v.w, qb, P.is_int);
+    }
+    return v;
+}
+
 BSG_D void reduce_run2(const uint4 *src, uint4 *dst, uint32_t c0, uint32_t ncplx,
                        const VisParams &P, uint32_t lane)
 {
@@ -264,28 +289,7 @@ BSG_D void reduce_run2(const uint4 *src, uint4 *dst, uint32_t c0, uint32_t ncplx
     uint32_t p = fp - f * P.P;
     const uint32_t q64 = 64 / P.T, r64 = 64 % P.T;
     for (uint32_t k = lane; k < ncplx / 2; k += 32) {
-        const uint32_t ij = __ldg(P.pairs + p);
-        uint4 v = src[k];
-        if (P.qtab) {  // full covariance: per-component q from the table
-            const uint2 a = reduce_sample(make_uint2(v.x, v.y), ij, f, t, P);
-            const uint2 b = reduce_sample(make_uint2(v.z, v.w), ij, f, t + 1, P);
-            v = make_uint4(a.x, a.y, b.x, b.y);
-        } else {
-            const uint32_t i = ij & 0xffffu, j = ij >> 16;
-            const uint32_t row = f * P.n_in;
-            const float2 Ai = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + i) * P.T + t));
-            const float2 Aj = __ldg(reinterpret_cast<const float2 *>(P.autos + (size_t)(row + j) * P.T + t));
-            const bool is_auto = i == j;
-            const float qa = __fmul_rn(__fmul_rn(vis_c(P, f, t, is_auto), Ai.x), Aj.x);
-            const float qb = __fmul_rn(__fmul_rn(vis_c(P, f, t + 1, is_auto), Ai.y), Aj.y);
-            v.x = reduce_bits(v.x, qa, P.is_int);
-            v.z = reduce_bits(v.z, qb, P.is_int);
-            if (!is_auto) {
-                v.y = reduce_bits(v.y, qa, P.is_int);
-                v.w = reduce_bits(v.w, qb, P.is_int);
-            }
-        }
-        dst[k] = v;
+        dst[k] = reduce_pair(src[k], __ldg(P.pairs + p), f, t, P);
         t += r64;
         p += q64;
         if (t >= P.T) {

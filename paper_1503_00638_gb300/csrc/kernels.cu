@@ -333,11 +333,34 @@ __global__ void __launch_bounds__(256) reduce_precision_kernel(const uint2 *__re
     }
     for (uint64_t r = warp * RUN; r < n_cplx; r += nwarps * RUN) {
         uint32_t cnt = (uint32_t)(n_cplx - r < RUN ? n_cplx - r : RUN);
-        if ((P.T & 1u) == 0)  // r is even and so is cnt (n_cplx = F P T is even)
-            reduce_run2(reinterpret_cast<const uint4 *>(in + r), reinterpret_cast<uint4 *>(out + r),
-                        (uint32_t)r, cnt, P, lane);
-        else
+        if ((P.T & 1u) == 0) {
+            // r is even and so is cnt (n_cplx = F P T is even): pairs of
+            // samples (t, t + 1) of one product, four per lane loaded before
+            // any is stored (out does not alias in), each placed in the cube
+            // by division through precomputed multiply-high
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(in + r);
+            uint4 *d4 = reinterpret_cast<uint4 *>(out + r);
+            const uint32_t np = cnt / 2;
+            for (uint32_t k0 = 0; k0 < np; k0 += 4 * 32) {
+                uint4 v[4];
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) {
+                    const uint32_t k = k0 + 32 * q + lane;
+                    v[q] = k < np ? __ldg(s4 + k) : make_uint4(0u, 0u, 0u, 0u);
+                }
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) {
+                    const uint32_t k = k0 + 32 * q + lane;
+                    if (k >= np) break;
+                    const uint32_t c = (uint32_t)r + 2 * k;
+                    const uint32_t fp = fastdiv(c, P.dT), t = c - fp * P.T;
+                    const uint32_t f = fastdiv(fp, P.dP), p = fp - f * P.P;
+                    d4[k] = reduce_pair(v[q], __ldg(P.pairs + p), f, t, P);
+                }
+            }
+        } else {
             reduce_run(in + r, out + r, (uint32_t)r, cnt, P, lane);
+        }
     }
 }
 
