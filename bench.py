@@ -819,6 +819,23 @@ def run_round(args, rank, world, gpu_index, barrier):
             want = oracle.reduce_precision_c64(host[fr:fr + 1], cfg.n_samp, cfg.f)
             ok &= bool(np.array_equal(out[fr:fr + 1].cpu().numpy().view(np.uint32),
                                       want.view(np.uint32)))
+    # the post-acquisition reorder alone (bsgpu_reorder_time) on the same
+    # cube in the instrument's [T][F P] order: 16 bytes per sample moved
+    ts = torch.empty((T, F, P), dtype=torch.complex64, device="cuda")
+    ts.copy_(d.permute(2, 0, 1))
+    back = torch.empty_like(d)
+    for _ in range(args.warmup):
+        bsgpu.reorder_time(ts, out=back)
+    evr = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        evr[k][0].record(stream)
+        bsgpu.reorder_time(ts, out=back)
+        evr[k][1].record(stream)
+    torch.cuda.synchronize()
+    r_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evr)
+    reorder_ok = bool(torch.equal(back, d))
+    del ts, back
     line = {
         "metric": "precision reduction GB/s (uncompressed bytes) & % HBM roofline",
         "value": nbytes * world / (mean_ms / 1e3) / 1e9, "unit": "GB/s", "n_gpus": world,
@@ -832,6 +849,9 @@ def run_round(args, rank, world, gpu_index, barrier):
         "kernel_ms": {"mean": statistics.mean(ms), "median": statistics.median(ms),
                       "best": min(ms)},
         "matches_oracle_sampled": ok,
+        "reorder": {"gbs": nbytes / (r_ms / 1e3) / 1e9, "frac": 2 * nbytes / (r_ms / 1e3) / 1e9 / hbm,
+                    "ms": r_ms, "round_trip_ok": reorder_ok,
+                    "what": "bsgpu_reorder_time, [T][F P] -> [F P][T], complex64"},
         "roofline": {"bound": "hbm", "kernel": "reduce_precision_kernel",
                      "achieved": alg / (mean_ms / 1e3) / 1e9, "peak": hbm,
                      "peak_kind": peak_kind, "unit": "GB/s",

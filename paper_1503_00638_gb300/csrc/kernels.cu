@@ -864,9 +864,60 @@ __global__ void __launch_bounds__(256) reorder_time_kernel(const E *__restrict__
     }
 }
 
+// The same for a short time axis (T <= 32): a tile is all T time rows of 64
+// series, read row by row (64 consecutive elements each) and written as the
+// tile's one contiguous stretch of output (64 series of T samples), element
+// o of the stretch from tile[o mod T][o / T]; the row pitch of 65 elements
+// keeps those transposed reads free of bank conflicts.
+template <typename E>
+__global__ void __launch_bounds__(256) reorder_time_short_kernel(const E *__restrict__ in,
+                                                                 E *__restrict__ out, uint32_t T,
+                                                                 uint64_t S)
+{
+    constexpr uint32_t W = 64;
+    __shared__ E tile[32][W + 1];
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint64_t ntiles = (S + W - 1) / W;
+    for (uint64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
+        const uint64_t s0 = b * W;
+        const uint32_t w = S - s0 < W ? (uint32_t)(S - s0) : W;   // series in this tile
+        __syncthreads();
+        for (uint32_t e = tid; e < T * W; e += nt) {
+            const uint32_t t = e / W, x = e % W;
+            if (x < w) tile[t][x] = in[(uint64_t)t * S + s0 + x];
+        }
+        __syncthreads();
+        E *o = out + s0 * T;
+        // element e = x T + t of the stretch; (t, x) advance by nt per step
+        const uint32_t qn = nt / T, rn = nt % T;
+        uint32_t t = tid % T, x = tid / T;
+        for (uint32_t e = tid; e < w * T; e += nt) {
+            o[e] = tile[t][x];
+            t += rn;
+            x += qn;
+            if (t >= T) {
+                t -= T;
+                x++;
+            }
+        }
+    }
+}
+
 cudaError_t launch_reorder_time(const void *in, void *out, uint64_t T, uint64_t S, uint32_t es,
                                 cudaStream_t s)
 {
+    if (T >= 1 && T <= 32) {
+        const uint64_t tiles = (S + 63) / 64;
+        const uint32_t grid = (uint32_t)(tiles < 65536 ? (tiles ? tiles : 1) : 65536);
+        const uint32_t t32 = (uint32_t)T;
+        switch (es) {
+        case 1: reorder_time_short_kernel<<<grid, 256, 0, s>>>((const uint8_t *)in, (uint8_t *)out, t32, S); break;
+        case 2: reorder_time_short_kernel<<<grid, 256, 0, s>>>((const uint16_t *)in, (uint16_t *)out, t32, S); break;
+        case 4: reorder_time_short_kernel<<<grid, 256, 0, s>>>((const uint32_t *)in, (uint32_t *)out, t32, S); break;
+        default: reorder_time_short_kernel<<<grid, 256, 0, s>>>((const uint2 *)in, (uint2 *)out, t32, S); break;
+        }
+        return cudaGetLastError();
+    }
     const uint64_t tiles = ((S + 31) / 32) * ((T + 31) / 32);
     const uint32_t grid = (uint32_t)(tiles < 65536 ? (tiles ? tiles : 1) : 65536);
     const dim3 blk(32, 8);
