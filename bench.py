@@ -586,6 +586,10 @@ VARIANTS = {
                           "what": "complex64 cube, compensated f of Sec. 3.2 per sample"},
     "chime-samples8": {"dtype": "f32", "es": 8, "tslow": False, "comp": False, "full": False,
                        "what": "complex64 cube bitshuffled as 8-byte samples"},
+    "chime-t40": {"dtype": "f32", "es": 4, "tslow": False, "comp": False, "full": False,
+                  "F": 512, "T": 40,
+                  "what": "complex64 cube of 512 freq x 8256 products x 40 time (a time axis "
+                          "that is not a multiple of 16)"},
     "fullcov8": {"dtype": "f32", "es": 4, "tslow": False, "comp": False, "full": True, "n_in": 8,
                  "what": "8-input array, 1024 freq x 36 products x 64 time, full covariance"},
     "fullcov16": {"dtype": "f32", "es": 4, "tslow": False, "comp": False, "full": True,
@@ -604,7 +608,8 @@ def run_variant(args, rank, world, gpu_index, barrier):
         cfg = synth.VisConfig(1024, v["n_in"], 64, 2 ** 16, args.f, seed=rank, rho=0.5)
         host = synth.visibilities_physical(cfg)
     else:
-        cfg = synth.VisConfig(1024, 128, 16, 2 ** 17, args.f, seed=rank, drift=True)
+        cfg = synth.VisConfig(v.get("F", 1024), 128, v.get("T", 16), 2 ** 17, args.f, seed=rank,
+                              drift=True)
         host = synth.visibilities_int(cfg, 4096.0) if v["dtype"] == "i32" else synth.visibilities(cfg)
     F, n_in, T = cfg.n_freq, cfg.n_inputs, cfg.n_time
     host_in = _np.ascontiguousarray(_np.moveaxis(host, 2, 0)) if v["tslow"] else host

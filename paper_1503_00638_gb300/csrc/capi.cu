@@ -99,15 +99,14 @@ VisOpts vis_opts(int flags, int64_t n_freq, int64_t n_in, int64_t n_time)
     return o;
 }
 
-// Whether compress takes the fast kernel (full blocks of at most 8 KiB of 4-
-// or 8-byte elements; a cube of 4-byte components also needs n_time % 16 == 0,
-// and a time-slowest cube, gathered in series of 16 time samples, needs
-// n_time % 16 == 0 and blocks of a multiple of 16 samples).
+// Whether compress takes the fast kernel (full blocks of at most 8 KiB of 2-,
+// 4- or 8-byte elements; a time-slowest cube, gathered in series of 16 time
+// samples, needs n_time % 16 == 0 and blocks of a multiple of 16 samples).
 bool fast_shape(const Geometry &g, uint64_t n_time, bool tslow = false)
 {
     if (!shuffle_inplace_ok(g.es, g.B)) return false;
     if (tslow) return n_time % 16 == 0 && ((uint64_t)g.B * g.es) % 128 == 0;
-    return n_time == 0 || g.es == 8 || n_time % 16 == 0;
+    return true;
 }
 
 // n_ft: entries of the per-(freq, time) compensated-c table (0 = none)
@@ -426,8 +425,11 @@ static int compress_common(const void *in, const Geometry &g, int level, void *o
         if (cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const bool ts = vis && vis->tslow;
+        // 4-byte components of a cube whose time axis is not a multiple of 16
+        const bool ps = vis && !vis->tslow && g.es == 4 && (vis->T % 16u) != 0;
         uint64_t grid = (uint64_t)sms * (ts ? compress_fast_tslow_blocks_per_sm(level, g.es)
-                                            : compress_fast_blocks_per_sm(level, g.es));
+                                            : ps ? compress_fast_ps_blocks_per_sm(level)
+                                                 : compress_fast_blocks_per_sm(level, g.es));
         if (grid > nfull) grid = nfull;
         if (grid > FAST_MAX_WARPS) grid = FAST_MAX_WARPS;
         CodecArgs f = a;
@@ -436,8 +438,9 @@ static int compress_common(const void *in, const Geometry &g, int level, void *o
         f.slots = reinterpret_cast<uint8_t *>(ws) + L.slots;
         f.nslot_warps = FAST_MAX_WARPS;
         f.tile_counter = reinterpret_cast<uint32_t *>((uint8_t *)ws + 4);
-        cudaError_t e = ts ? launch_compress_fast_tslow(f, (uint32_t)grid, s)
-                           : launch_compress_fast(f, (uint32_t)grid, s);
+        cudaError_t e = ts   ? launch_compress_fast_tslow(f, (uint32_t)grid, s)
+                        : ps ? launch_compress_fast_ps(f, (uint32_t)grid, s)
+                             : launch_compress_fast(f, (uint32_t)grid, s);
         if (e != cudaSuccess) return BSGPU_ERR_CUDA;
         done = nfull;
     }

@@ -1,6 +1,7 @@
 // The fast compress kernel (full blocks of at most 8 KiB, Sec. 4.2.1), shared
 // by the translation units that instantiate it: kernels.cu for cubes and
-// streams stored in order, tslow.cu for time-slowest cubes.
+// streams stored in order, tslow.cu for time-slowest cubes and for cubes
+// whose time axis is not a multiple of 16.
 #pragma once
 
 #include "codec.cuh"
@@ -14,8 +15,10 @@ namespace bsg {
 // then its predecessors have long published theirs, so the look-back rarely
 // waits.  GEN (4-byte elements of a cube only): int32 components, a
 // compensated c or the full-covariance q table (see round_group and
-// round_group_full).
-template <int LEVEL, int ES, bool GEN = false, bool TS = false>
+// round_group_full).  PS (4-byte elements of a cube whose time axis is not a
+// multiple of 16, so 16-sample groups would straddle products): the samples
+// are rounded one by one before the plain transpose.
+template <int LEVEL, int ES, bool GEN = false, bool TS = false, bool PS = false>
 __global__ void __launch_bounds__(32, 20) compress_fast_kernel(const __grid_constant__ CodecArgs a)
 {
     using L = FastPlan<LEVEL>;
@@ -59,6 +62,19 @@ __global__ void __launch_bounds__(32, 20) compress_fast_kernel(const __grid_cons
                 __syncwarp();
             }
             shuffle8_inplace(tmp, Bb, lane);
+        } else if (PS && a.vis.enabled) {
+            // a time axis that is not a multiple of 16: the components are
+            // rounded sample by sample in place, then transposed
+            const uint32_t c0 = (uint32_t)(((uint64_t)tile * a.B) >> 1);
+            if ((a.vis.T & 1u) == 0) {
+                uint4 *b4 = reinterpret_cast<uint4 *>(tmp);
+                reduce_run2(b4, b4, c0, Bb / 2, a.vis, lane);
+            } else {
+                uint2 *b2 = reinterpret_cast<uint2 *>(tmp);
+                reduce_run(b2, b2, c0, Bb / 2, a.vis, lane);
+            }
+            __syncwarp();
+            shuffle4_inplace(tmp, Bb, lane, NoRound{});
         } else if (a.vis.enabled) {
             shuffle4_inplace(tmp, Bb, lane,
                              VisGroupRound<GEN>{&a.vis, (uint32_t)(((uint64_t)tile * a.B) >> 1)});

@@ -108,6 +108,9 @@ uint32_t compress_fast_blocks_per_sm(int level, uint32_t es);
 // the same for a time-slowest cube (n_time % 16 == 0), in tslow.cu
 cudaError_t launch_compress_fast_tslow(const CodecArgs &a, uint32_t grid, cudaStream_t s);
 uint32_t compress_fast_tslow_blocks_per_sm(int level, uint32_t es);
+// the same for a time-fastest cube of 4-byte components with n_time % 16 != 0
+cudaError_t launch_compress_fast_ps(const CodecArgs &a, uint32_t grid, cudaStream_t s);
+uint32_t compress_fast_ps_blocks_per_sm(int level);
 // staging slot size of the fast path and the warp count its slots cover
 constexpr uint32_t FAST_SLOT_BYTES = 8304;
 constexpr uint32_t FAST_MAX_WARPS = 3072;

@@ -1,9 +1,11 @@
 // The fast compress kernel for time-slowest cubes ([T][F P] samples, the
 // instrument's order before the post-acquisition reorder of Sec. 2): each
 // full block is gathered into time-fastest order in shared memory and then
-// rounded, shuffled and coded exactly like a block of a time-fastest cube.
-// Kept in its own translation unit so the in-order kernels compile without
-// the gather and the build compiles both in parallel.
+// rounded, shuffled and coded exactly like a block of a time-fastest cube;
+// and for time-fastest cubes of 4-byte components whose time axis is not a
+// multiple of 16 (rounded sample by sample, then shuffled).  Kept in their
+// own translation unit so the in-order kernels compile without these paths
+// and the build compiles both in parallel.
 #include <cuda_runtime.h>
 
 #include "compress_fast.cuh"
@@ -42,6 +44,28 @@ cudaError_t launch_compress_fast_tslow(const CodecArgs &a, uint32_t grid, cudaSt
     return a.level >= 1
                ? launch_warp_kernel(compress_fast_kernel<1, 4, false, true>, smem, grid, s, a)
                : launch_warp_kernel(compress_fast_kernel<0, 4, false, true>, smem, grid, s, a);
+}
+
+// Cubes of 4-byte components whose time axis is not a multiple of 16: the
+// fast kernel rounding each sample before the transpose (PS).
+uint32_t compress_fast_ps_blocks_per_sm(int level)
+{
+    int n = 0;
+    const uint32_t smem = compress_fast_smem_bytes(level);
+    const cudaError_t e =
+        level >= 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                         &n, compress_fast_kernel<1, 4, false, false, true>, 32, smem)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                         &n, compress_fast_kernel<0, 4, false, false, true>, 32, smem);
+    return e == cudaSuccess && n > 0 ? (uint32_t)n : 1u;
+}
+
+cudaError_t launch_compress_fast_ps(const CodecArgs &a, uint32_t grid, cudaStream_t s)
+{
+    const uint32_t smem = compress_fast_smem_bytes(a.level);
+    return a.level >= 1
+               ? launch_warp_kernel(compress_fast_kernel<1, 4, false, false, true>, smem, grid, s, a)
+               : launch_warp_kernel(compress_fast_kernel<0, 4, false, false, true>, smem, grid, s, a);
 }
 
 }  // namespace bsg
