@@ -586,6 +586,10 @@ VARIANTS = {
                           "what": "complex64 cube, compensated f of Sec. 3.2 per sample"},
     "chime-samples8": {"dtype": "f32", "es": 8, "tslow": False, "comp": False, "full": False,
                        "what": "complex64 cube bitshuffled as 8-byte samples"},
+    "chime-tslow-t40": {"dtype": "f32", "es": 4, "tslow": True, "comp": False, "full": False,
+                        "F": 512, "T": 40,
+                        "what": "complex64 cube of 512 freq x 8256 products x 40 time in the "
+                                "instrument's [T][F][P] order, reorder fused"},
     "chime-t40": {"dtype": "f32", "es": 4, "tslow": False, "comp": False, "full": False,
                   "F": 512, "T": 40,
                   "what": "complex64 cube of 512 freq x 8256 products x 40 time (a time axis "

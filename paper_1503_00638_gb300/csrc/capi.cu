@@ -99,14 +99,11 @@ VisOpts vis_opts(int flags, int64_t n_freq, int64_t n_in, int64_t n_time)
     return o;
 }
 
-// Whether compress takes the fast kernel (full blocks of at most 8 KiB of 2-,
-// 4- or 8-byte elements; a time-slowest cube, gathered in series of 16 time
-// samples, needs n_time % 16 == 0 and blocks of a multiple of 16 samples).
-bool fast_shape(const Geometry &g, uint64_t n_time, bool tslow = false)
+// Whether compress takes the fast kernel: full blocks of at most 8 KiB of 2-,
+// 4- or 8-byte elements (a cube in any order, any time axis).
+bool fast_shape(const Geometry &g)
 {
-    if (!shuffle_inplace_ok(g.es, g.B)) return false;
-    if (tslow) return n_time % 16 == 0 && ((uint64_t)g.B * g.es) % 128 == 0;
-    return true;
+    return shuffle_inplace_ok(g.es, g.B);
 }
 
 // n_ft: entries of the per-(freq, time) compensated-c table (0 = none)
@@ -118,7 +115,7 @@ WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint
     if (op == BSGPU_OP_COMPRESS || op == BSGPU_OP_COMPRESS_VIS) {
         L.state = o;
         o += r256((size_t)g.nb * 8);
-        if (g.nb && fast_shape(g, n_time, opts.tslow)) {
+        if (g.nb && fast_shape(g)) {
             L.slots = o;
             o += (size_t)FAST_MAX_WARPS * 2 * FAST_SLOT_BYTES;
         }

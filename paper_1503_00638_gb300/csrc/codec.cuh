@@ -133,6 +133,24 @@ BSG_D void gather_tslow_block(const CodecArgs &a, uint8_t *dst, uint32_t tile, u
     }
 }
 
+// Full block `tile` of a time-slowest cube whose time axis is not a multiple
+// of 16 (series of 16 samples would straddle products) into shared `dst` in
+// time-fastest order, one complex sample per lane and step: output sample
+// c0 + k comes from time (c0 + k) mod T of series (c0 + k) / T, the division
+// through the precomputed multiply-high.
+BSG_D void gather_tslow_samples(const CodecArgs &a, uint8_t *dst, uint32_t tile, uint32_t lane)
+{
+    const VisParams &P = a.vis;
+    const uint32_t n8 = (uint32_t)(((uint64_t)a.B * a.es) >> 3);   // samples per block
+    const uint32_t c0 = tile * n8;        // complex indices of a cube are below 2^32
+    const uint2 *src = reinterpret_cast<const uint2 *>(a.in);
+    uint2 *d = reinterpret_cast<uint2 *>(dst);
+    for (uint32_t k = lane; k < n8; k += 32) {
+        const uint32_t c = c0 + k, s = fastdiv(c, P.dT), t = c - s * P.T;
+        d[k] = __ldg(src + (uint64_t)t * P.FP + s);
+    }
+}
+
 // Copy len bytes from 16-byte aligned shared `s` to global `g` (any alignment):
 // byte stores up to g's next 16-byte boundary, then 16-byte stores assembled
 // from two aligned shared vectors and a funnel shift, then the ragged end.

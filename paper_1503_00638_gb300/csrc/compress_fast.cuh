@@ -15,9 +15,9 @@ namespace bsg {
 // then its predecessors have long published theirs, so the look-back rarely
 // waits.  GEN (4-byte elements of a cube only): int32 components, a
 // compensated c or the full-covariance q table (see round_group and
-// round_group_full).  PS (4-byte elements of a cube whose time axis is not a
-// multiple of 16, so 16-sample groups would straddle products): the samples
-// are rounded one by one before the plain transpose.
+// round_group_full).  PS (a cube whose time axis is not a multiple of 16, so
+// 16-sample groups would straddle products): the samples are rounded one by
+// one before the plain transpose, and with TS gathered one by one.
 template <int LEVEL, int ES, bool GEN = false, bool TS = false, bool PS = false>
 __global__ void __launch_bounds__(32, 20) compress_fast_kernel(const __grid_constant__ CodecArgs a)
 {
@@ -40,7 +40,10 @@ __global__ void __launch_bounds__(32, 20) compress_fast_kernel(const __grid_cons
     while (tile < a.tile_end) {
         const uint32_t Bb = a.B;  // the fast path takes full blocks only
         if (TS) {
-            gather_tslow_block(a, tmp, tile, lane);
+            if (PS)
+                gather_tslow_samples(a, tmp, tile, lane);
+            else
+                gather_tslow_block(a, tmp, tile, lane);
             __syncwarp();
         } else if (load_block(tmp, a.in + (uint64_t)tile * a.B * a.es, Bb * a.es, bar, lane)) {
             if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);

@@ -49,6 +49,9 @@ CASES = [
     # ends inside one (1024 / 48 is not whole), and the cube ends in a short block
     ("T32", synth.VisConfig(3, 10, 32, 2 ** 15, 0.02, seed=7), 2.0 ** 16),
     ("T48", synth.VisConfig(2, 16, 48, 2 ** 16, 0.01, seed=8, drift=True), 2.0 ** 20),
+    # an odd time axis with several full blocks (samples gathered and rounded
+    # one by one in the fast kernel)
+    ("T7", synth.VisConfig(4, 20, 7, 2 ** 14, 0.03, seed=9), 2.0 ** 18),
 ]
 
 
@@ -84,6 +87,11 @@ def test_fused_reorder_rounding(bs, orc, name, cfg, scale, dtype, compensate):
     ("T48", "f32", 8, 1024, 0, False),
     ("T48", "i32", 4, 2048, 0, True),
     ("T48", "f32", 4, 512, 0, False),
+    ("T40", "f32", 4, 2048, 0, False),
+    ("T40", "i32", 8, 1024, 0, True),
+    ("T40", "i32", 4, 1024, 1, True),
+    ("T7", "f32", 4, 2048, 0, True),
+    ("T7", "i32", 8, 1024, 1, False),
 ])
 def test_fused_reorder_compression(bs, orc, name, dtype, es, B, level, comp):
     cfg, scale = {c[0]: (c[1], c[2]) for c in CASES}[name]
