@@ -3,7 +3,6 @@ re/im pairs) and for the compensated f of Sec. 3.2."""
 from fractions import Fraction
 
 import numpy as np
-import pytest
 
 from paper_1503_00638_gb300 import synth
 

@@ -5,7 +5,6 @@ keeps its scratch in a fixed array inside the library instead of a
 caller-provided workspace.  Its output must equal bsgpu_compress's, byte for
 byte (the encoder is deterministic), on consecutive calls that reuse the
 array.  This file is collected last."""
-import ctypes
 
 import numpy as np
 import pytest
