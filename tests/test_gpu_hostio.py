@@ -41,3 +41,26 @@ def test_round_trip_through_host(mods, orc, slab, depth, lag):
         assert rc == 0 and np.array_equal(back.view(np.uint32), flat.view(np.uint32))
     h2d, d2h = codec.bytes_moved(chunks)
     assert h2d > v.nbytes and d2h > v.nbytes
+
+
+@pytest.mark.parametrize("cfg", [synth.VisConfig(6, 16, 40, 2 ** 16, 0.01, seed=3),
+                                 synth.VisConfig(5, 12, 7, 2 ** 14, 0.03, seed=4)],
+                         ids=["T40", "T7"])
+def test_round_trip_with_other_time_axes(mods, orc, cfg):
+    # time axes that are not a multiple of 16: slabs go through the fast
+    # kernel's per-sample rounding; the result is still the oracle's cube
+    bs, hostio = mods
+    v = synth.visibilities(cfg)
+    want = orc.reduce_precision_c64(v, cfg.n_samp, cfg.f)
+    h_vis = torch.from_numpy(v.copy()).pin_memory()
+    h_out = torch.empty_like(h_vis).pin_memory()
+    codec = hostio.HostVisCodec(cfg.n_freq, cfg.n_inputs, cfg.n_time, cfg.n_samp, cfg.f,
+                                block_elems=2048, slab_freq=2, depth=2)
+    chunks = codec.round_trip(h_vis, h_out, lag=1)
+    assert all(c == (0, 0) for c in codec.statuses())
+    assert np.array_equal(h_out.numpy().view(np.uint32), want.view(np.uint32))
+    for c in chunks:
+        f0, f1 = c.freq
+        flat = want[f0:f1].view(np.float32).reshape(-1)
+        rc, back = orc.decompress(c.stream.numpy().tobytes(), flat.size, np.float32, 2048)
+        assert rc == 0 and np.array_equal(back.view(np.uint32), flat.view(np.uint32))
