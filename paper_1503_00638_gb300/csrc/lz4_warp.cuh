@@ -743,7 +743,8 @@ BSG_D void lz4_match_copy(uint8_t *dst, uint32_t op, uint32_t off, uint32_t ML, 
         // period dividing 4: every aligned output word holds the same value
         warp_fill_pattern(dst, op, off, ML, lane);
     } else if (off >= 32) {
-        const uint32_t W = off < 128u ? off : 128u;
+        // steps of at most `off` bytes never read what the same step writes
+        const uint32_t W = off < 512u ? off : 512u;
         for (uint32_t base = 0; base < ML; base += W) {
             warp_copy(dst, op + base, dst, op + base - off, ML - base < W ? ML - base : W, lane);
             __syncwarp();
