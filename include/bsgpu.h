@@ -262,17 +262,25 @@ int bsgpu_compress_vis_ex(const void *vis, int dtype, int64_t n_freq, int64_t n_
  *   Arguments and output as for bsgpu_compress, without the workspace.  The
  *   scratch (status word, tile counter, 8 bytes of look-back state per block)
  *   lives in a fixed array inside the library of 256 + 8 * 131072 bytes
- *   (about 1 MiB), held by every device that loads the library until the
- *   process exits; inputs of more than 131072 blocks (1 GiB at 8 KiB blocks)
+ *   (about 1 MiB), held in every context the library's module is loaded
+ *   into (each device the process uses it on) until the process exits; inputs of more than 131072 blocks (1 GiB at 8 KiB blocks)
  *   are rejected with BSGPU_ERR_SPACE before anything is enqueued.
- *   The first call on a device looks up the array's device address (once per
- *   device, with that device current); make that first call before any
- *   stream capture.  No call allocates or frees memory.
+ *   The first call in each context (the device's primary context, or any
+ *   other context the caller makes current) looks up the array's device
+ *   address with that context current and caches it for that context.  With
+ *   lazy module loading (the CUDA default) that first call also loads the
+ *   library's module into the context, which places the array and may
+ *   synchronize the device: make it at start-up, as a warm-up, before any
+ *   stream capture (or set CUDA_MODULE_LOADING=EAGER to do it when the
+ *   library is loaded).  Later calls allocate and free nothing and call no
+ *   allocating routine.
  *   Every call shares the one array: calls that overlap on the GPU (on
  *   different streams, or from different threads) race and corrupt each
  *   other's output; serialize them.
- *   A device-side failure (a bounded wait that ran out) is reported by
- *   writing 0 to *d_out_bytes (a valid stream is at least 12 bytes long). */
+ *   Any device-side failure (a bounded wait that ran out, or any other
+ *   error the kernels record) is reported by writing 0 to *d_out_bytes (a
+ *   valid stream is at least 12 bytes long); the call's own return value
+ *   covers argument and launch errors only. */
 int bsgpu_compress_noalloc(const void *in, size_t n_elem, size_t elem_size, size_t block_elems,
                            int level, void *out, size_t out_cap, uint64_t *d_out_bytes,
                            uint64_t *d_block_offsets, void *stream);

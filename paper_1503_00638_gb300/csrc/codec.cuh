@@ -420,6 +420,11 @@ BSG_D uint64_t lookback_resolve(uint64_t *state, uint32_t tile, uint64_t agg, in
     for (;;) {
         int64_t idx = base - (int64_t)lane;
         uint64_t v = idx >= 0 ? ld_relaxed_u64(state + idx) : FP;
+#ifdef BSG_TEST_LOOKBACK_STALL
+        // test builds only: predecessors never look ready, so the bounded
+        // wait below runs out and reports BSGPU_ERR_TIMEOUT
+        if (idx >= 0) v = 0;
+#endif
         uint32_t flag = (uint32_t)(v >> 62);
         uint32_t pm = __ballot_sync(FULL, flag == 2);
         uint32_t im = __ballot_sync(FULL, flag == 0);

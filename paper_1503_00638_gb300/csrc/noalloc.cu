@@ -8,6 +8,7 @@
 // For them this entry point keeps its scratch (the status word, the tile
 // counter and the per-block look-back state of the compress kernel) in a
 // fixed array in device memory that belongs to the library.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -24,34 +25,94 @@ constexpr uint32_t NOALLOC_MAX_BLOCKS = 131072;   // 1 GiB of input at 8 KiB blo
 constexpr size_t NOALLOC_HEADER = 256;            // status word, tile counter
 constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + 8ull * NOALLOC_MAX_BLOCKS;
 
-// Held by every device that loads the library, for the life of the process.
+// One copy in every context the module is loaded into, for the life of the
+// process (with lazy module loading, from the first call in that context).
 static __device__ __align__(256) uint8_t g_compress_scratch[NOALLOC_BYTES];
 
-// A device-side failure (a bounded wait that ran out) turns the reported
-// stream length into 0; a valid stream is at least 12 bytes long.
+// Any device-side failure recorded in the status word (a bounded wait that
+// ran out, or any other error code) turns the reported stream length into
+// 0; a valid stream is at least 12 bytes long.
 __global__ void noalloc_report_kernel(const int *status, uint64_t *out_bytes)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0 && *status != 0) *out_bytes = 0;
 }
 
-constexpr int MAX_DEVICES = 64;
-std::once_flag g_once[MAX_DEVICES];
-void *g_scratch_ptr[MAX_DEVICES];
-cudaError_t g_scratch_err[MAX_DEVICES];
+// Device address of the scratch array in the calling thread's current
+// context.  In host code the array's name is only a host-side stand-in; its
+// device address belongs to a context (the module is loaded per context), so
+// the lookup is cached per context, keyed by the driver's context id (ids
+// are never reused, so a context created after cudaDeviceReset, or a second
+// context on the same device, gets its own lookup).  Failures are not
+// cached.  The driver's context queries are reached through the runtime's
+// entry-point lookup, so the library does not link the driver library.
+typedef int (*CtxGetCurrentFn)(CUcontext *);
+typedef int (*CtxGetIdFn)(CUcontext, unsigned long long *);
 
-// Device address of the scratch array on the current device.  In host code
-// the array's name is only a host-side stand-in, so the address is looked up
-// once per device, with that device current.
-int scratch_on_current_device(void **ptr)
+constexpr int CACHE_SLOTS = 64;
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void *ptr;
+};
+std::mutex g_mu;
+ScratchSlot g_slots[CACHE_SLOTS];
+int g_nslots = 0;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_fns_tried = false;
+
+// Id of the current context, or false when it cannot be had (no driver
+// entry points, or no context current yet).
+bool current_context_id(unsigned long long *id)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return BSGPU_ERR_CUDA;
-    if (dev < 0 || dev >= MAX_DEVICES) return BSGPU_ERR_ARG;
-    std::call_once(g_once[dev], [dev] {
-        g_scratch_err[dev] = cudaGetSymbolAddress(&g_scratch_ptr[dev], g_compress_scratch);
-    });
-    if (g_scratch_err[dev] != cudaSuccess) return BSGPU_ERR_CUDA;
-    *ptr = g_scratch_ptr[dev];
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_fns_tried) {
+            g_fns_tried = true;
+            void *f1 = nullptr, *f2 = nullptr;
+            cudaDriverEntryPointQueryResult q1, q2;
+            if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                                 &q1) == cudaSuccess &&
+                q1 == cudaDriverEntryPointSuccess &&
+                cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault,
+                                                 &q2) == cudaSuccess &&
+                q2 == cudaDriverEntryPointSuccess) {
+                g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+                g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+            }
+        }
+    }
+    if (!g_ctx_current || !g_ctx_id) return false;
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != 0 || ctx == nullptr) return false;
+    return g_ctx_id(ctx, id) == 0;
+}
+
+int scratch_in_current_context(void **ptr)
+{
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);
+    if (have_id) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        for (int k = 0; k < g_nslots; k++)
+            if (g_slots[k].ctx_id == id) {
+                *ptr = g_slots[k].ptr;
+                return BSGPU_OK;
+            }
+    }
+    // first call in this context: the lookup loads the library's module into
+    // the context (and, with no context current yet, makes the device's
+    // primary context current)
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_compress_scratch) != cudaSuccess || p == nullptr)
+        return BSGPU_ERR_CUDA;
+    if (!have_id) have_id = current_context_id(&id);
+    if (have_id) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        bool known = false;
+        for (int k = 0; k < g_nslots; k++) known = known || g_slots[k].ctx_id == id;
+        if (!known && g_nslots < CACHE_SLOTS) g_slots[g_nslots++] = ScratchSlot{id, p};
+    }
+    *ptr = p;
     return BSGPU_OK;
 }
 
@@ -73,7 +134,7 @@ extern "C" int bsgpu_compress_noalloc(const void *in, size_t n_elem, size_t elem
     if (nb > NOALLOC_MAX_BLOCKS) return BSGPU_ERR_SPACE;  // beyond the fixed scratch
 
     void *scratch = nullptr;
-    int rc = scratch_on_current_device(&scratch);
+    int rc = scratch_in_current_context(&scratch);
     if (rc != BSGPU_OK) return rc;
 
     const uint32_t B = (uint32_t)(block_elems ? block_elems : 4096 / elem_size);
@@ -117,6 +178,11 @@ extern "C" int bsgpu_compress_noalloc(const void *in, size_t n_elem, size_t elem
         e = launch_compress(a, maxb, (uint32_t)grid, s);
     }
     if (e != cudaSuccess) return BSGPU_ERR_CUDA;
-    noalloc_report_kernel<<<1, 32, 0, s>>>(a.status, d_out_bytes);
-    return cudaGetLastError() == cudaSuccess ? BSGPU_OK : BSGPU_ERR_CUDA;
+    // launched through cudaLaunchKernel, whose return value is this launch's
+    // own error (an error left by an unrelated earlier launch is not taken
+    // for it)
+    const int *st = a.status;
+    void *args[] = {(void *)&st, (void *)&d_out_bytes};
+    e = cudaLaunchKernel((const void *)noalloc_report_kernel, dim3(1), dim3(32), args, 0, s);
+    return e == cudaSuccess ? BSGPU_OK : BSGPU_ERR_CUDA;
 }
