@@ -70,6 +70,14 @@ def parse():
                    help="serve workload: requests per arrival-rate point")
     p.add_argument("--chunks", type=int, default=4096,
                    help="batch workload: number of chunks (4096 = the full workload)")
+    p.add_argument("--sub-chunks", type=int, default=1024,
+                   help="chunks of the batch record in the default run's line")
+    p.add_argument("--sub-requests", type=int, default=800,
+                   help="requests per point of the serving record in the default run's line")
+    p.add_argument("--no-sweep", action="store_true",
+                   help="shuffle workload: leave out the codec-only size x block grid")
+    p.add_argument("--no-sub", action="store_true",
+                   help="leave the batch and serving records out of the default run's line")
     return p.parse_args()
 
 
@@ -271,25 +279,28 @@ def issue_peak_ginst(sm_mhz):
 
 BATCH_WORKLOAD = ("batch of 4096 chunks, log-uniform 64 KiB..64 MiB (~40 GB), elem 2/4/8 B, "
                   "half rounded visibilities (16 inputs x 64 time), half random walks")
-BATCH_BLOCK_BYTES = 8192
+BATCH_BLOCK_BYTES = 8192                     # the serving workload's block size
+BATCH_BLOCK_CANDIDATES = (2048, 4096, 8192)  # the batch autotuner's block sizes (bytes)
 
 
 def batch_specs(n_chunks, seed):
     """(bytes, elem size, kind) per chunk; sizes log-uniform on [64 KiB, 64 MiB]."""
-    rng = np.random.default_rng([seed, 4])
-    sizes = np.exp(rng.uniform(np.log(64 << 10), np.log(64 << 20), n_chunks)).astype(np.int64)
-    es = rng.choice([2, 4, 8], n_chunks)
-    kind = rng.random(n_chunks) < 0.5
-    return [(int(b) // int(e) * int(e), int(e), "vis" if k else "walk")
-            for b, e, k in zip(sizes, es, kind)]
+    from paper_1503_00638_gb300 import synth
+    return synth.batch_specs(n_chunks, seed)
 
 
-def batch_inputs(specs, seed, device="cuda"):
+def batch_inputs(specs, seed, device="cuda", keep_raw=False):
     """Device buffers of the chunks: rounded visibility cubes (16 inputs x 64
-    time, as many frequencies as the size needs, cut to size) or random walks."""
+    time, as many frequencies as the size needs, cut to size) or random walks.
+    With keep_raw, also {chunk: (host cube, config)} for the smallest
+    visibility chunk of each element size (for the oracle's check of the
+    rounding)."""
     import torch
     from paper_1503_00638_gb300 import bsgpu, synth
-    xs = []
+    xs, raw, keep = [], {}, {}
+    for k, (nb, es, kind) in enumerate(specs):
+        if kind == "vis" and (es not in keep or nb < specs[keep[es]][0]):
+            keep[es] = k
     per_freq = synth.n_products(16) * 64 * 8
     for k, (nb, es, kind) in enumerate(specs):
         if kind == "vis":
@@ -298,14 +309,43 @@ def batch_inputs(specs, seed, device="cuda"):
             cube = synth.visibilities_torch(cfg, device)
             r = bsgpu.reduce_precision_c64(cube, cfg.n_samp, cfg.f)
             x = r.view(torch.uint8).reshape(-1)[:nb].clone()
+            if keep_raw and keep.get(es) == k:
+                raw[k] = (cube.cpu().numpy(), cfg)
             del cube, r
         else:
             x = synth.random_walk_torch(nb // es, es, seed=seed * 100003 + k, device=device)
         xs.append(x)
-    return xs
+    return (xs, raw) if keep_raw else xs
 
 
-def oracle_batch_sample(xs, specs, seconds=15.0):
+def oracle_batch_checks(eng, xs, specs, raw, block_bytes):
+    """The oracle against the batch run: the GPU rounding of the smallest
+    visibility chunk of each element size against the oracle's rounding of
+    its raw cube, and the oracle's strict decoder on the GPU stream of the
+    smallest chunk of every (element size, kind) pair."""
+    import oracle
+    rounding_ok = True
+    for k, (cube, cfg) in raw.items():
+        want = oracle.reduce_precision_c64(cube, cfg.n_samp, cfg.f).view(np.uint8).reshape(-1)
+        rounding_ok &= bool(np.array_equal(xs[k].cpu().numpy(), want[:specs[k][0]]))
+    pick = {}
+    for k, (nb, es, kind) in enumerate(specs):
+        if (es, kind) not in pick or nb < specs[pick[(es, kind)]][0]:
+            pick[(es, kind)] = k
+    udt = {2: np.uint16, 4: np.uint32, 8: np.uint64}
+    decode_ok = True
+    for (es, kind), k in pick.items():
+        a = xs[k].cpu().numpy().view(udt[es])
+        rc, back = oracle.decompress(eng.stream(k).cpu().numpy().tobytes(), a.size, a.dtype,
+                                     block_bytes // es)
+        decode_ok &= rc == 0 and bool(np.array_equal(back, a))
+    return {"rounding_vs_oracle": {"chunks": len(raw), "bit_exact": rounding_ok},
+            "oracle_decodes": {"chunks": len(pick),
+                               "pairs": sorted(f"{es}B-{kind}" for es, kind in pick),
+                               "exact": decode_ok}}
+
+
+def oracle_batch_sample(xs, specs, block_bytes=BATCH_BLOCK_BYTES, seconds=15.0):
     """The oracle compressing and decompressing whole chunks, in order, until
     about `seconds` have passed; returns (bytes, seconds, chunks)."""
     import oracle
@@ -313,8 +353,8 @@ def oracle_batch_sample(xs, specs, seconds=15.0):
     for x, (nb, es, _) in zip(xs, specs):
         a = x.cpu().numpy().view({2: np.uint16, 4: np.uint32, 8: np.uint64}[es])
         t0 = time.perf_counter()
-        s = oracle.compress(a, BATCH_BLOCK_BYTES // es)
-        rc, back = oracle.decompress(s, a.size, a.dtype, BATCH_BLOCK_BYTES // es)
+        s = oracle.compress(a, block_bytes // es)
+        rc, back = oracle.decompress(s, a.size, a.dtype, block_bytes // es)
         t_used += time.perf_counter() - t0
         if rc != 0 or not np.array_equal(back, a):
             raise RuntimeError("oracle round trip failed")
@@ -325,18 +365,36 @@ def oracle_batch_sample(xs, specs, seconds=15.0):
     return done, t_used, n
 
 
-def run_batch(args, rank, world, local, barrier, gpu_index):
+def run_batch(args, rank, world, local, barrier, gpu_index, chunks=None, steps=None,
+              warmup=None, cpu=True):
+    """The batched engine on `chunks` chunks of the batch generator: the
+    autotuner picks the block size and each launch's shape, then compress +
+    decompress of the whole batch is timed as one CUDA-graph replay per step.
+    Returns the record (rank 0 prints it for --workload batch)."""
     import torch
     import torch.distributed as dist
     from paper_1503_00638_gb300 import bsgpu, engine
 
-    specs = batch_specs(args.chunks, rank)
-    xs = batch_inputs(specs, rank)
+    chunks = chunks or args.chunks
+    steps = steps or args.steps
+    warmup = args.warmup if warmup is None else warmup
+    specs = batch_specs(chunks, rank)
+    xs, raw = batch_inputs(specs, rank, keep_raw=True)
     es_l = [es for _, es, _ in specs]
-    bl = [BATCH_BLOCK_BYTES // es for es in es_l]
     nbytes = sum(nb for nb, _, _ in specs)
+    # the autotuner: block size x warps per CTA x CTAs per SM, each launch
+    # tuned on its own (one codec at a time, so that a 40 GB batch fits)
+    block_bytes, tune_table, _ = engine.tune(xs, es_l, BATCH_BLOCK_CANDIDATES, level=LEVEL,
+                                             reps=2, keep=False)
+    torch.cuda.empty_cache()
+    bl = [block_bytes // es for es in es_l]
     eng = engine.BatchCodec(xs, es_l, bl, level=LEVEL)
-    tune_c, tune_d = eng.autotune(candidates=(0, 8, 12, 16), reps=2)
+    chosen = tune_table[block_bytes]
+    eng.warps_c, eng.ctas_c = chosen["compress"]["warps_per_cta"], chosen["compress"]["ctas_per_sm"]
+    eng.warps_d, eng.ctas_d = (chosen["decompress"]["warps_per_cta"],
+                               chosen["decompress"]["ctas_per_sm"])
+    eng.compress()
+    eng.decompress()
     sc, sd = eng.statuses()
     if any(sc) or any(sd):
         raise RuntimeError("batch status after tuning")
@@ -351,7 +409,7 @@ def run_batch(args, rank, world, local, barrier, gpu_index):
     clocks = ClockSampler(gpu_index)
     clocks.start()
     time.sleep(0.3)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         graph.replay()
     t_soak0 = time.time()
     torch.cuda.synchronize()
@@ -372,7 +430,7 @@ def run_batch(args, rank, world, local, barrier, gpu_index):
     t_wall0 = time.time()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         graph.replay()
     end.record(stream)
     torch.cuda.synchronize()
@@ -388,7 +446,7 @@ def run_batch(args, rank, world, local, barrier, gpu_index):
     if world > 1:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms_max = float(ms_t.item())
-    value = nbytes * world * args.steps / (ms_max / 1e3) / 1e9
+    value = nbytes * world * steps / (ms_max / 1e3) / 1e9
 
     # end to end through the engine with host buffers, on the leading chunks
     # up to 4 GB (pinned host copies of the whole 40 GB are not kept)
@@ -400,6 +458,7 @@ def run_batch(args, rank, world, local, barrier, gpu_index):
     xs_sub = xs[:sub]
     e_sub = engine.BatchCodec(xs_sub, es_l[:sub], bl[:sub], level=LEVEL)
     e_sub.ctas_c, e_sub.ctas_d = eng.ctas_c, eng.ctas_d
+    e_sub.warps_c, e_sub.warps_d = eng.warps_c, eng.warps_d
     host_in = [x.cpu().pin_memory() for x in xs_sub]
     e_sub.compress()
     torch.cuda.synchronize()
@@ -431,15 +490,24 @@ def run_batch(args, rank, world, local, barrier, gpu_index):
     alg_c = nbytes + slen + 8 * eng.n_items + 8 * eng.n
     alg_d = slen + 8 * eng.n_items + nbytes
     line = {
-        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD if args.chunks == 4096
-                   else f"{BATCH_WORKLOAD} (first {args.chunks} chunks)",
+        "config": {"workload": BATCH_WORKLOAD if chunks == 4096
+                   else f"{BATCH_WORKLOAD} (first {chunks} chunks, {nbytes / 1e9:.1f} GB)",
                    "chunks": eng.n, "items": eng.n_items, "bytes": nbytes,
-                   "block_bytes": BATCH_BLOCK_BYTES, "level": LEVEL,
-                   "ctas_per_sm": {"compress": eng.ctas_c, "decompress": eng.ctas_d},
-                   "tuning_ms": {"compress": tune_c.table, "decompress": tune_d.table},
+                   "block_bytes": block_bytes, "level": LEVEL,
+                   "launch": {"compress": {"warps_per_cta": eng.warps_c,
+                                           "ctas_per_sm": eng.ctas_c},
+                              "decompress": {"warps_per_cta": eng.warps_d,
+                                             "ctas_per_sm": eng.ctas_d}},
+                   "autotuner": {"block_bytes_candidates": list(BATCH_BLOCK_CANDIDATES),
+                                 "shapes": [f"{w}x{k}" for w, k in engine.SHAPES],
+                                 "shape_note": "WxC = W warps per CTA, C CTAs per SM (0 = as "
+                                               "many as fit)",
+                                 "rule": "fastest round trip among block sizes within 2% of "
+                                         "the smallest compressed size",
+                                 "per_block_bytes": tune_table},
                    "l2": f"inputs ({nbytes / 1e9:.1f} GB) larger than L2; no flush",
                    "step": "compress + decompress batch, one CUDA-graph replay",
                    "parallelism": f"replicas x{world}"},
@@ -456,18 +524,19 @@ def run_batch(args, rank, world, local, barrier, gpu_index):
         "e2e": {"value": e2e_value, "unit": "GB/s",
                 "h2d_bytes_per_step": sub_bytes + end_b, "d2h_bytes_per_step": end_b + 8 * sub
                 + e_sub.dec_arena.numel(), "chunks": sub, "round_trip_ok": ok_e2e},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 2 * steps,
         "clocks": clk,
         "wall_s_timed": t_wall1 - t_wall0,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        nb_cpu, dt, n_cpu = oracle_batch_sample(xs, specs)
+    if rank == 0:
+        line["parity"] = oracle_batch_checks(eng, xs, specs, raw, block_bytes)
+    if rank == 0 and world == 1 and cpu and not args.no_cpu_baseline:
+        nb_cpu, dt, n_cpu = oracle_batch_sample(xs, specs, block_bytes)
         line["cpu_baseline"] = {"value": nb_cpu / dt / 1e9, "unit": "GB/s", "cores": 1,
                                 "kind": "oracle",
                                 "sample": f"first {n_cpu} chunks ({nb_cpu / 1e6:.1f} MB): "
                                           "compress+decompress"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 # -- the serving workload --------------------------------------------------------
@@ -515,10 +584,15 @@ def serve_requests(xs, comp, n, rate, seed):
     return reqs
 
 
-def run_serve(args, rank, world, gpu_index):
+def run_serve(args, rank, world, gpu_index, requests=None, payloads=256):
+    """Serving: the continuous-batching server and the one-at-a-time
+    pipeline on the same request lists (every request present at t = 0, then
+    Poisson arrivals at 0.1 .. 0.9 of the batching server's saturation).
+    Returns the record."""
     import torch
     from paper_1503_00638_gb300 import serve
-    xs, comp = serve_pool(256, rank)
+    n_req = requests or args.requests
+    xs, comp = serve_pool(payloads, rank)
     mean_bytes = statistics.mean(x.numel() for x in xs)   # payloads are drawn uniformly
     cap = 40 << 30
     bsrv = serve.BatchingServer(cap_bytes=cap, depth=2)
@@ -530,20 +604,19 @@ def run_serve(args, rank, world, gpu_index):
     time.sleep(0.3)
     t_0 = time.time()
     # saturation: every request present at t = 0
-    sat_b = serve.latency_summary(bsrv.run(serve_requests(xs, comp, args.requests, 0.0, 1)))
-    sat_s = serve.latency_summary(ssrv.run(serve_requests(xs, comp, args.requests // 4, 0.0, 1)))
+    # both servers run the identical request list at every point
+    sat_b = serve.latency_summary(bsrv.run(serve_requests(xs, comp, n_req, 0.0, 1)))
+    sat_s = serve.latency_summary(ssrv.run(serve_requests(xs, comp, n_req, 0.0, 1)))
     lam_sat = sat_b["gbs"] * 1e9 / mean_bytes
     sweep = []
     for frac in (0.1, 0.3, 0.5, 0.7, 0.9):
         lam = frac * lam_sat
         point = {"rate_per_s": lam, "offered_gbs": lam * mean_bytes / 1e9, "frac_of_sat": frac}
-        rb = bsrv.run(serve_requests(xs, comp, args.requests, lam, 2))
+        rb = bsrv.run(serve_requests(xs, comp, n_req, lam, 2))
         point["batching"] = serve.latency_summary(rb)
         point["batching"]["batches"] = len(bsrv.batches)
         bsrv.batches.clear()
-        # the one-at-a-time server falls behind early: fewer requests per point
-        nser = max(200, args.requests // 4)
-        rs = ssrv.run(serve_requests(xs, comp, nser, lam, 2))
+        rs = ssrv.run(serve_requests(xs, comp, n_req, lam, 2))
         point["serial"] = serve.latency_summary(rs)
         for r in rb + rs:
             if r.status != 0:
@@ -555,9 +628,10 @@ def run_serve(args, rank, world, gpu_index):
     half = [p for p in sweep if p["frac_of_sat"] == 0.5][0]
     line = {
         "metric": METRIC, "value": sat_b["gbs"], "unit": "GB/s", "n_gpus": world,
-        "steps": args.requests, "warmup": 64, "ms_per_step": None, "higher_is_better": True,
+        "steps": n_req, "warmup": 64, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": SERVE_WORKLOAD, "payloads": len(xs), "requests": args.requests,
+        "config": {"workload": SERVE_WORKLOAD, "payloads": len(xs), "requests": n_req,
+                   "same_requests": "both servers run the identical request list at every point",
                    "mean_request_bytes": mean_bytes, "block_bytes": BATCH_BLOCK_BYTES,
                    "admission_cap_bytes": cap, "batch_depth": 2,
                    "value": "batching server GB/s with every request present at t = 0",
@@ -570,8 +644,7 @@ def run_serve(args, rank, world, gpu_index):
                     "sweep": sweep},
         "clocks": clk,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 # -- variants of the visibility path (the int32 path, the fused reorder, the
@@ -669,18 +742,28 @@ def run_variant(args, rank, world, gpu_index, barrier):
         compress()
         decompress(slen)
         torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    # inputs that fit in L2 (the full-covariance cubes) are timed cold: a
+    # write of 2 x L2 before each launch, outside the launch's events
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    small = nbytes + cap < 2 * l2
+    flush = torch.empty(2 * l2 if small else 0, dtype=torch.uint8, device="cuda")
     barrier()
     torch.cuda.synchronize()
     t_wall0 = time.time()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(stream)
     for k in range(args.steps):
+        if small:
+            flush.zero_()
         evs[k][0].record(stream)
         compress()
         evs[k][1].record(stream)
-        decompress(slen)
+        if small:
+            flush.zero_()
         evs[k][2].record(stream)
+        decompress(slen)
+        evs[k][3].record(stream)
     end.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -689,13 +772,14 @@ def run_variant(args, rank, world, gpu_index, barrier):
     clocks.stop()
     if bsgpu.status(ws_c) or bsgpu.status(ws_d):
         raise RuntimeError("variant status after timed steps")
-    ms = start.elapsed_time(end)
+    cm = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    dm = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    # with flushes, the step is the two launches' own time
+    ms = start.elapsed_time(end) if not small else args.steps * (cm + dm)
     ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms_max = float(ms_t.item())
-    cm = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
-    dm = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
     # the output is the time-fastest rounded cube
     ref = bsgpu.reduce_precision(d_in, cfg.n_samp, cfg.f, compensate=v["comp"],
                                  time_slowest=v["tslow"], full_cov=v["full"])
@@ -731,7 +815,10 @@ def run_variant(args, rank, world, gpu_index, barrier):
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {v['what']}", "f": cfg.f, "N": cfg.n_samp,
                    "elem_bytes": es, "block_bytes": 8192, "cube_bytes": nbytes,
-                   "l2": f"inputs ({nbytes / 1e9:.2f} GB) larger than L2; no flush",
+                   "l2": (f"inputs ({nbytes / 1e9:.3f} GB) fit in L2: L2 flushed (a "
+                          f"{2 * l2 / 1e6:.0f} MB write) before every timed launch"
+                          if small else
+                          f"inputs ({nbytes / 1e9:.2f} GB) larger than L2; no flush"),
                    "parallelism": f"replicas x{world}"},
         "compress_gbs": nbytes / (cm / 1e3) / 1e9, "decompress_gbs": nbytes / (dm / 1e3) / 1e9,
         "ratio": slen / nbytes, "round_trip_ok": ok,
@@ -993,8 +1080,103 @@ def run_shuffle(args, rank, world, gpu_index, barrier):
         "gpu_launches": args.steps * 8,
         "clocks": clk,
     }
+    if not args.no_sweep:
+        line["sweep"] = codec_sweep(args, hbm)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+SWEEP_SIZES = tuple((1 << 20) * 4 ** k for k in range(6)) + (4 * 10 ** 9,)   # 1 MiB .. 1 GiB, 4 GB
+SWEEP_BLOCKS = (1024, 2048, 4096, 8192)
+
+
+def codec_sweep(args, hbm):
+    """The codec-only grid: uint8 / uint16 / int32 / float64 random walks of
+    1 MiB to 4 GB (x4 steps) in blocks of 1024 .. 8192 elements; Bitshuffle,
+    un-Bitshuffle, compress (Bitshuffle + LZ4) and decompress each timed on
+    its own with CUDA events (median of the repetitions).  Sizes that fit in
+    L2 are timed cold: a write of 2 x L2 precedes every timed launch.  Each
+    smaller array is the start of the 4 GB one.  Every point checks both
+    round trips."""
+    import torch
+    from paper_1503_00638_gb300 import bsgpu, synth
+    stream = torch.cuda.current_stream()
+    lib = bsgpu._lib
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    flush = torch.empty(2 * l2, dtype=torch.uint8, device="cuda")
+    grid = []
+    for es in (1, 2, 4, 8):
+        nmax = max(SWEEP_SIZES) // es
+        x = synth.random_walk_device(nmax, es, seed=40 + es, floating=(es == 8))
+        y, z = torch.empty_like(x), torch.empty_like(x)
+        cap = bsgpu.compress_bound(nmax, es, min(SWEEP_BLOCKS))
+        cbuf = torch.empty(cap, dtype=torch.uint8, device="cuda")
+        offs = torch.empty(bsgpu.num_blocks(nmax, es, min(SWEEP_BLOCKS)), dtype=torch.int64,
+                           device="cuda")
+        nbd = torch.zeros(1, dtype=torch.int64, device="cuda")
+        wsc = bsgpu.new_workspace(bsgpu.workspace_size(bsgpu.OP_COMPRESS, nmax, es,
+                                                       min(SWEEP_BLOCKS)))
+        wsd = bsgpu.new_workspace(bsgpu.workspace_size(bsgpu.OP_DECOMPRESS, nmax, es,
+                                                       min(SWEEP_BLOCKS)))
+        for size in SWEEP_SIZES:
+            n = size // es
+            cold = size < 2 * l2
+            reps = 3 if size >= (1 << 30) else 5
+            for B in SWEEP_BLOCKS:
+                ops = {
+                    "shuffle": lambda: lib.bsgpu_bitshuffle(x.data_ptr(), y.data_ptr(), n, es, B,
+                                                            stream.cuda_stream),
+                    "unshuffle": lambda: lib.bsgpu_bitunshuffle(y.data_ptr(), z.data_ptr(), n, es,
+                                                                B, stream.cuda_stream),
+                    "compress": lambda: lib.bsgpu_compress(
+                        x.data_ptr(), n, es, B, LEVEL, cbuf.data_ptr(), cap, nbd.data_ptr(),
+                        offs.data_ptr(), wsc.data_ptr(), wsc.numel(), stream.cuda_stream),
+                }
+                times = {}
+                for name in ("shuffle", "unshuffle", "compress", "decompress"):
+                    if name == "decompress":
+                        L = int(nbd.item())
+                        fn = (lambda L=L: lib.bsgpu_decompress(
+                            cbuf.data_ptr(), L, z.data_ptr(), n, es, B, offs.data_ptr(),
+                            wsd.data_ptr(), wsd.numel(), stream.cuda_stream))
+                    else:
+                        fn = ops[name]
+                    bsgpu._check(fn(), name)            # warm-up
+                    if name == "unshuffle":
+                        ok_sh = bool(torch.equal(z[:n * es], x[:n * es]))
+                    ts = []
+                    for _ in range(reps):
+                        if cold:
+                            flush.zero_()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        bsgpu._check(fn(), name)
+                        e1.record(stream)
+                        e1.synchronize()
+                        ts.append(e0.elapsed_time(e1))
+                    times[name] = statistics.median(ts)
+                L = int(nbd.item())
+                ok_c = (bool(torch.equal(z[:n * es], x[:n * es])) and bsgpu.status(wsc) == 0
+                        and bsgpu.status(wsd) == 0)
+                nb = n * es
+                grid.append({
+                    "elem_bytes": es, "bytes": nb, "block_elems": B, "l2_cold": cold,
+                    "shuffle_gbs": nb / times["shuffle"] / 1e6,
+                    "shuffle_frac": 2 * nb / times["shuffle"] / 1e6 / hbm,
+                    "unshuffle_gbs": nb / times["unshuffle"] / 1e6,
+                    "unshuffle_frac": 2 * nb / times["unshuffle"] / 1e6 / hbm,
+                    "compress_gbs": nb / times["compress"] / 1e6,
+                    "compress_frac": (nb + L) / times["compress"] / 1e6 / hbm,
+                    "decompress_gbs": nb / times["decompress"] / 1e6,
+                    "decompress_frac": (nb + L) / times["decompress"] / 1e6 / hbm,
+                    "ratio": L / nb, "round_trips_ok": ok_sh and ok_c})
+        del x, y, z, cbuf, offs, wsc, wsd
+        torch.cuda.empty_cache()
+    return {"sizes": list(SWEEP_SIZES), "blocks": list(SWEEP_BLOCKS), "elem_bytes": [1, 2, 4, 8],
+            "values": "uint8 / uint16 / int32 random walks (wrapping), float64 random walk",
+            "timing": "CUDA events per launch, median of 5 (3 at 1 GiB and up); L2 flushed "
+                      "before each launch when the array is under 2 x L2",
+            "grid": grid}
 
 
 # -- the GPU arm ----------------------------------------------------------------
@@ -1035,7 +1217,9 @@ def main():
             dist.destroy_process_group()
         return
     if args.workload == "serve":
-        run_serve(args, rank, world, gpu_index)
+        line = run_serve(args, rank, world, gpu_index)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -1050,7 +1234,9 @@ def main():
             dist.destroy_process_group()
         return
     if args.workload == "batch":
-        run_batch(args, rank, world, local, barrier, gpu_index)
+        line = run_batch(args, rank, world, local, barrier, gpu_index)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -1222,7 +1408,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if F == 1024 else f"{WORKLOAD} (first {F} freq)",
                    "f": cfg.f, "N": 2 ** 17, "block_bytes": BLOCK_ELEMS * 4,
-                   "cube_bytes": nbytes, "l2": "inputs (1.08 GB) larger than L2; no flush",
+                   "cube_bytes": nbytes,
+                   "l2": f"inputs ({nbytes / 1e9:.2f} GB) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "compress_gbs": nbytes / (comp_avg_ms / 1e3) / 1e9,
         "decompress_gbs": nbytes / (dec_avg_ms / 1e3) / 1e9,
@@ -1264,10 +1451,91 @@ def main():
             "value": nb_all / dt_all / 1e9, "unit": "GB/s", "cores": nc, "kind": "oracle",
             "sample": f"first {nf_all} of 1024 frequencies ({nb_all / 1e6:.1f} MB) in {nc} "
                       f"frequency slabs, one thread each: round+compress+decompress"}
+    if rank == 0 and world == 1:
+        line["ratio_vs_oracle"], orc_stream = ratio_side_by_side(cfg, vis_h, args)
+        line["decompress_no_index"] = time_no_index(
+            bsgpu, [("gpu stream", comp[:slen]), ("oracle stream", orc_stream)], dec, n_fl,
+            nbytes, dec_avg_ms)
+    if world == 1 and not args.no_sub:
+        # the batched engine and the server, at stated sizes, in the same line
+        del comp, dec, ws_c, ws_d, offs
+        torch.cuda.empty_cache()
+        b = run_batch(args, rank, world, local, barrier, gpu_index, chunks=args.sub_chunks,
+                      steps=5, warmup=3, cpu=False)
+        line["batch"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "compress_gbs",
+                                           "decompress_gbs", "ratio", "roofline",
+                                           "decompress_roofline", "config", "parity", "e2e",
+                                           "clocks", "gpu_launches") if k in b}
+        torch.cuda.empty_cache()
+        sv = run_serve(args, rank, world, gpu_index, requests=args.sub_requests, payloads=128)
+        line["serving"] = {"value_gbs_at_saturation": sv["value"], "unit": "GB/s",
+                           "config": sv["config"], "clocks": sv["clocks"], **sv["serving"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def ratio_side_by_side(cfg, vis, args):
+    """Compression ratio of the GPU encoder and of the oracle's greedy encoder
+    on the whole CHIME-shaped cube at f = 1e-3, 1e-2 and 0.1 (the oracle over
+    all host cores, one frequency slab each; blocks never straddle slabs, so
+    the per-slab streams add up to the whole stream less their headers).
+    Also returns the oracle's whole-cube stream at f = args.f (the slabs'
+    blocks after one header)."""
+    import concurrent.futures as cf
+    import torch
+    import oracle
+    from paper_1503_00638_gb300 import bsgpu
+    F = vis.shape[0]
+    d = torch.from_numpy(vis).cuda()
+    out, whole = {}, None
+    for f in sorted({1e-3, 1e-2, 0.1, args.f}):
+        c = bsgpu.compress_vis(d, cfg.n_samp, f, BLOCK_ELEMS)
+        g = c.nbytes
+
+        def slab(fr):
+            r = oracle.reduce_precision_c64(vis[fr:fr + 1], cfg.n_samp, f)
+            return oracle.compress(r.view(np.float32).reshape(-1), BLOCK_ELEMS)[12:]
+
+        with cf.ThreadPoolExecutor(max_workers=host_cores()) as ex:
+            parts = list(ex.map(slab, range(F)))
+        o = 12 + sum(len(p) for p in parts)
+        out[str(f)] = {"gpu": g / vis.nbytes, "oracle": o / vis.nbytes}
+        if f == args.f:
+            whole = (vis.nbytes.to_bytes(8, "big") + (BLOCK_ELEMS * 4).to_bytes(4, "big")
+                     + b"".join(parts))
+        del c, parts
+    del d
+    return out, whole
+
+
+def time_no_index(bsgpu, streams, want, n_fl, nbytes, indexed_ms, reps=5):
+    """Decompression of whole-cube streams WITHOUT their block index (the
+    device first walks the chain of length fields, chain_walk_kernel), next
+    to the indexed figure; each output is checked against `want`."""
+    import torch
+    out = {"indexed_decompress_gbs": nbytes / (indexed_ms / 1e3) / 1e9}
+    dec = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    for name, st in streams:
+        d = st if isinstance(st, torch.Tensor) else torch.frombuffer(bytearray(st),
+                                                                      dtype=torch.uint8).cuda()
+        ws = bsgpu.new_workspace(bsgpu.workspace_size(bsgpu.OP_DECOMPRESS, n_fl, 4, BLOCK_ELEMS))
+        bsgpu.decompress(d, d.numel(), n_fl, 4, BLOCK_ELEMS, offsets=None, out=dec, ws=ws)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bsgpu.decompress(d, d.numel(), n_fl, 4, BLOCK_ELEMS, offsets=None, out=dec, ws=ws)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ok = bool(torch.equal(dec, want)) and bsgpu.status(ws) == 0
+        ms = statistics.median(ts)
+        out[name] = {"ms": ms, "gbs": nbytes / (ms / 1e3) / 1e9, "exact": ok,
+                     "stream_bytes": int(d.numel())}
+        del d, ws
+    return out
 
 
 if __name__ == "__main__":

@@ -364,6 +364,23 @@ int bsgpu_decompress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_it
                            int *d_chunk_status, void *ws, size_t ws_bytes, uint32_t ctas_per_sm,
                            void *stream);
 
+/* The batch calls with a second launch-shape knob (Sec. 4.2.1: blocks are
+ * the independent units of work, the launch shape only decides how many
+ * are in flight): warps_per_cta of 1, 2 or 4 warps per CTA, each warp an
+ * independent worker with its own shared-memory slice; ctas_per_sm then
+ * counts CTAs of that many warps (0 = as many as fit).  The output is the
+ * same for every shape.  bsgpu_compress_batch / bsgpu_decompress_batch are
+ * these with warps_per_cta = 1.  BSGPU_ERR_ARG for any other warps_per_cta;
+ * otherwise as the calls above. */
+int bsgpu_compress_batch_ex(const void *d_table, uint32_t n_chunks, uint64_t n_items, int level,
+                            uint64_t *d_out_bytes, uint64_t *d_block_offsets, int *d_chunk_status,
+                            void *ws, size_t ws_bytes, uint32_t ctas_per_sm,
+                            uint32_t warps_per_cta, void *stream);
+int bsgpu_decompress_batch_ex(const void *d_table, uint32_t n_chunks, uint64_t n_items,
+                              const uint64_t *d_in_bytes, const uint64_t *d_block_offsets,
+                              int *d_chunk_status, void *ws, size_t ws_bytes,
+                              uint32_t ctas_per_sm, uint32_t warps_per_cta, void *stream);
+
 /* ------------------------------------------------------------------------
  * Offset allocator for a fixed device arena (host only; the paper has no
  * counterpart: it serves the admission control of a server that keeps one

@@ -21,7 +21,8 @@ function names the passage of the paper it follows:
 
 Parity is pinned by ``tests/test_oracle_*.py`` against closed forms, brute
 force, Python's exact rational arithmetic, numpy's bit routines, hand-built
-LZ4 streams in ``tests/golden/`` and (where present) the system liblz4.
+LZ4 streams written out from the LZ4 block format (``tests/test_oracle_lz4.py``)
+and (where present) the system liblz4.
 """
 from __future__ import annotations
 

@@ -13,7 +13,7 @@
  * is contracted (the float32 arithmetic of reading R1 below must be rounded
  * after every operation).
  *
- * Readings of the paper where it is silent (numbered as in the design doc):
+ * Readings of the paper where it is silent (numbered R1, R2, ...):
  *   R1  q = 12 f s^2 is evaluated in float32, each operation rounded to
  *       nearest: c = fl32(6 f / N); cross q = (c * A_i) * A_j;
  *       auto q = ((2c) * A_i) * A_i.

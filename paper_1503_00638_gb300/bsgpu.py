@@ -59,6 +59,10 @@ _SIGS = {
                               ctypes.c_uint32, _vp], _i),
     "bsgpu_decompress_batch": ([_vp, ctypes.c_uint32, ctypes.c_uint64, _vp, _vp, _vp, _vp, _sz,
                                 ctypes.c_uint32, _vp], _i),
+    "bsgpu_compress_batch_ex": ([_vp, ctypes.c_uint32, ctypes.c_uint64, _i, _vp, _vp, _vp, _vp,
+                                 _sz, ctypes.c_uint32, ctypes.c_uint32, _vp], _i),
+    "bsgpu_decompress_batch_ex": ([_vp, ctypes.c_uint32, ctypes.c_uint64, _vp, _vp, _vp, _vp, _sz,
+                                   ctypes.c_uint32, ctypes.c_uint32, _vp], _i),
     "bsgpu_arena_create": ([ctypes.c_uint64, ctypes.c_uint64], _vp),
     "bsgpu_arena_destroy": ([_vp], None),
     "bsgpu_arena_alloc": ([_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)], _i),
@@ -411,19 +415,22 @@ def batch_plan(op: int, chunks) -> tuple:
 
 def compress_batch(d_table: torch.Tensor, n_chunks: int, n_items: int, out_bytes: torch.Tensor,
                    offsets: torch.Tensor | None, status: torch.Tensor, ws: torch.Tensor,
-                   level: int = 0, ctas_per_sm: int = 0, stream=None) -> None:
-    _check(_lib.bsgpu_compress_batch(_ptr(d_table), n_chunks, n_items, level, _ptr(out_bytes),
-                                     _ptr(offsets), _ptr(status), _ptr(ws), ws.numel(),
-                                     ctas_per_sm, _stream(stream)), "bsgpu_compress_batch")
+                   level: int = 0, ctas_per_sm: int = 0, stream=None,
+                   warps_per_cta: int = 1) -> None:
+    _check(_lib.bsgpu_compress_batch_ex(_ptr(d_table), n_chunks, n_items, level, _ptr(out_bytes),
+                                        _ptr(offsets), _ptr(status), _ptr(ws), ws.numel(),
+                                        ctas_per_sm, warps_per_cta, _stream(stream)),
+           "bsgpu_compress_batch_ex")
 
 
 def decompress_batch(d_table: torch.Tensor, n_chunks: int, n_items: int,
                      in_bytes: torch.Tensor | None, offsets: torch.Tensor | None,
                      status: torch.Tensor, ws: torch.Tensor, ctas_per_sm: int = 0,
-                     stream=None) -> None:
-    _check(_lib.bsgpu_decompress_batch(_ptr(d_table), n_chunks, n_items, _ptr(in_bytes),
-                                       _ptr(offsets), _ptr(status), _ptr(ws), ws.numel(),
-                                       ctas_per_sm, _stream(stream)), "bsgpu_decompress_batch")
+                     stream=None, warps_per_cta: int = 1) -> None:
+    _check(_lib.bsgpu_decompress_batch_ex(_ptr(d_table), n_chunks, n_items, _ptr(in_bytes),
+                                          _ptr(offsets), _ptr(status), _ptr(ws), ws.numel(),
+                                          ctas_per_sm, warps_per_cta, _stream(stream)),
+           "bsgpu_decompress_batch_ex")
 
 
 class Arena:

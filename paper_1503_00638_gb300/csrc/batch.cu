@@ -149,17 +149,28 @@ BSG_D void batch_place(const BatchArgs &b, uint32_t c, uint32_t tile, const uint
     compress_place(a, tile, blk, cs, 12 + excl, lane);
 }
 
-// One warp per CTA, persistent, one shared buffer (as compress_fast_kernel):
-// per item, transpose the block, LZ4-encode it into this warp's staging slot,
+// Shared memory of one warp of the batch kernels, rounded up so that the
+// warps of a multi-warp CTA each get a 128-byte aligned slice.
+template <int LEVEL>
+__host__ __device__ constexpr uint32_t batch_compress_warp_smem() { return r128(FastPlan<LEVEL>::BYTES); }
+__host__ __device__ constexpr uint32_t batch_decompress_warp_smem() { return r128(INPLACE_BUF + 16); }
+
+// Persistent, one shared buffer per warp (as compress_fast_kernel): per
+// item, transpose the block, LZ4-encode it into this warp's staging slot,
 // publish its size in its chunk's look-back state, then place the PREVIOUS
 // item's block, whose predecessors have long published theirs.  Only the
 // chunk index and local block number live across an item; the chunk's
 // fields are re-read from its (cached) table record where they are used.
-template <int LEVEL>
-__global__ void __launch_bounds__(32, 20) compress_batch_kernel(const __grid_constant__ BatchArgs b)
+// A CTA holds 1, 2 or 4 warps (a launch-shape choice of the autotuner); they
+// share nothing but the CTA: each warp has its own slice of the dynamic
+// shared memory, its own barrier and staging slots, and takes its own items.
+template <int LEVEL, int W>
+__global__ void __launch_bounds__(32 * W, 20 / W) compress_batch_kernel(const __grid_constant__ BatchArgs b)
 {
     using L = FastPlan<LEVEL>;
-    extern __shared__ __align__(128) uint8_t sm[];
+    extern __shared__ __align__(128) uint8_t smem_all[];
+    const uint32_t warp = W == 1 ? 0u : threadIdx.x >> 5;
+    uint8_t *sm = smem_all + (size_t)warp * batch_compress_warp_smem<LEVEL>();
     uint8_t *tmp = sm;
     void *scratch = sm + L::TMP;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::TMP + r16(L::SCR));
@@ -169,7 +180,8 @@ __global__ void __launch_bounds__(32, 20) compress_batch_kernel(const __grid_con
         fence_mbar_init();
     }
     __syncwarp();
-    uint8_t *slot0 = b.slots + (size_t)(2 * blockIdx.x) * FAST_SLOT_BYTES;
+    const uint32_t gw = blockIdx.x * W + warp;   // this warp's slot pair
+    uint8_t *slot0 = b.slots + (size_t)(2 * gw) * FAST_SLOT_BYTES;
     uint8_t *slot1 = slot0 + FAST_SLOT_BYTES;
     uint32_t parity = 0;
     uint32_t ptile = ~0u, pchunk = 0, pcs = 0;  // the block waiting to be placed, in slot1
@@ -292,14 +304,17 @@ __device__ __noinline__ void batch_unshuffle8(uint8_t *buf, uint32_t Bb, uint32_
     unshuffle8_inplace(buf, Bb, lane);
 }
 
-// One warp per CTA, persistent, one shared buffer decoded in place (as
+// Persistent, one shared buffer per warp decoded in place (as
 // decompress_inplace_kernel): per item, wait for its stream bytes, LZ4-decode,
 // un-transpose and store, then fetch the next item's bytes (of whichever chunk
 // it belongs to) once the store has read the buffer.  As in the compressor
-// only chunk indices and block numbers live across an item.
-__global__ void __launch_bounds__(32, 20) decompress_batch_kernel(const __grid_constant__ BatchArgs b)
+// only chunk indices and block numbers live across an item, and a CTA holds 1,
+// 2 or 4 independent warps, each with its own slice of shared memory.
+template <int W>
+__global__ void __launch_bounds__(32 * W, 20 / W) decompress_batch_kernel(const __grid_constant__ BatchArgs b)
 {
-    extern __shared__ __align__(128) uint8_t sm[];
+    extern __shared__ __align__(128) uint8_t smem_all[];
+    uint8_t *sm = smem_all + (W == 1 ? 0u : (threadIdx.x >> 5) * batch_decompress_warp_smem());
     uint8_t *buf = sm;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + INPLACE_BUF);
     const uint32_t lane = threadIdx.x & 31u;
@@ -375,28 +390,24 @@ __global__ void __launch_bounds__(32, 20) decompress_batch_kernel(const __grid_c
     __syncwarp();
 }
 
-// Block offsets of every chunk by walking its chain of length fields (one
-// thread per chunk; slow for long chunks, used only without an index).
-__global__ void chain_walk_batch_kernel(const __grid_constant__ BatchArgs b)
+// Block offsets of every chunk without its own index by walking its chain of
+// length fields: one warp per chunk, the chunk's stream staged through
+// shared memory (chain_walk_staged).
+__global__ void __launch_bounds__(32, 1) chain_walk_batch_kernel(const __grid_constant__ BatchArgs b)
 {
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= b.n_chunks || b.chunks[c].offs) return;  // a chunk with its own index
-    const CodecArgs a = chunk_args(b, c);
-    const uint64_t tail_b = (uint64_t)a.tail_elems * a.es;
-    uint64_t D = 12;
-    for (uint32_t k = 0; k < a.nb; k++) {
-        if (D + 4 > a.in_bytes) {
-            set_status(a.status, BSGPU_ERR_CORRUPT);
-            for (; k < a.nb; k++) a.block_offsets[k] = 0;  // dec_issue rejects D < 12
-            return;
-        }
-        a.block_offsets[k] = D;
-        const uint8_t *p = a.in + D;
-        const uint32_t len = ((uint32_t)p[0] << 24) | ((uint32_t)p[1] << 16) |
-                             ((uint32_t)p[2] << 8) | (uint32_t)p[3];
-        D += 4ull + len;
+    extern __shared__ __align__(128) uint8_t sm[];
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t c = blockIdx.x; c < b.n_chunks; c += gridDim.x) {
+        if (b.chunks[c].offs) continue;   // a chunk with its own index
+        const CodecArgs a = chunk_args(b, c);
+        if (a.nb == 0) continue;
+        bool timely = true;
+        const bool ok = chain_walk_staged(a.in, a.in_bytes, a.nb, (uint64_t)a.tail_elems * a.es,
+                                          a.block_offsets, sm, lane, timely);
+        if (lane == 0 && !timely) set_status(a.status, BSGPU_ERR_TIMEOUT);
+        else if (lane == 0 && !ok) set_status(a.status, BSGPU_ERR_CORRUPT);
+        __syncwarp();
     }
-    if (D + tail_b != a.in_bytes) set_status(a.status, BSGPU_ERR_CORRUPT);
 }
 
 }  // namespace bsg
@@ -440,41 +451,65 @@ int sm_count()
     return sms;
 }
 
+// Resident CTAs of `warps` warps per SM (at least 1).
 template <typename K>
-uint32_t occupancy(K kernel, uint32_t smem)
+uint32_t occupancy(K kernel, uint32_t smem, uint32_t warps)
 {
     int n = 0;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 32, smem) != cudaSuccess || n < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, (int)(32 * warps), smem) !=
+            cudaSuccess || n < 1)
         n = 1;
     return (uint32_t)n;
 }
 
 template <typename K>
-cudaError_t launch_batch(K kernel, uint32_t smem, uint32_t grid, cudaStream_t s, const BatchArgs &b)
+cudaError_t launch_batch(K kernel, uint32_t smem, uint32_t grid, uint32_t warps, cudaStream_t s,
+                         const BatchArgs &b)
 {
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kernel<<<grid, 32, smem, s>>>(b);
+    kernel<<<grid, 32 * warps, smem, s>>>(b);
     return cudaGetLastError();
 }
 
-// Persistent grid: ctas_per_sm (0 = as many as fit) warps on every SM, never
-// more than the items or the staging slots.
-uint32_t batch_grid(uint32_t fit, uint32_t ctas_per_sm, uint64_t n_items)
+// Persistent grid of CTAs of `warps` warps: ctas_per_sm (0 = as many as fit)
+// on every SM, never more warps than the items or the staging slots.
+uint32_t batch_grid(uint32_t fit, uint32_t ctas_per_sm, uint32_t warps, uint64_t n_items)
 {
     uint32_t per = ctas_per_sm && ctas_per_sm < fit ? ctas_per_sm : fit;
     uint64_t g = (uint64_t)sm_count() * per;
-    if (g > FAST_MAX_WARPS) g = FAST_MAX_WARPS;
-    if (g > n_items) g = n_items;
+    if (g * warps > FAST_MAX_WARPS) g = FAST_MAX_WARPS / warps;
+    const uint64_t need = (n_items + warps - 1) / warps;
+    if (g > need) g = need;
     return g ? (uint32_t)g : 1u;
 }
 
 bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+template <int LEVEL, int W>
+cudaError_t launch_compress_batch(const BatchArgs &b, uint32_t ctas_per_sm, uint64_t n_items,
+                                  cudaStream_t s)
+{
+    const uint32_t smem = W * batch_compress_warp_smem<LEVEL>();
+    const uint32_t g = batch_grid(occupancy(compress_batch_kernel<LEVEL, W>, smem, W), ctas_per_sm,
+                                  W, n_items);
+    return launch_batch(compress_batch_kernel<LEVEL, W>, smem, g, W, s, b);
+}
+
+template <int W>
+cudaError_t launch_decompress_batch(const BatchArgs &b, uint32_t ctas_per_sm, uint64_t n_items,
+                                    cudaStream_t s)
+{
+    const uint32_t smem = W * batch_decompress_warp_smem();
+    const uint32_t g = batch_grid(occupancy(decompress_batch_kernel<W>, smem, W), ctas_per_sm, W,
+                                  n_items);
+    return launch_batch(decompress_batch_kernel<W>, smem, g, W, s, b);
+}
 
 }  // namespace
 
@@ -535,12 +570,14 @@ int bsgpu_batch_plan(int op, const bsgpu_chunk *chunks, uint32_t n_chunks, void 
     return BSGPU_OK;
 }
 
-int bsgpu_compress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_items, int level,
-                         uint64_t *d_out_bytes, uint64_t *d_block_offsets, int *d_chunk_status,
-                         void *ws, size_t ws_bytes, uint32_t ctas_per_sm, void *stream)
+int bsgpu_compress_batch_ex(const void *d_table, uint32_t n_chunks, uint64_t n_items, int level,
+                            uint64_t *d_out_bytes, uint64_t *d_block_offsets, int *d_chunk_status,
+                            void *ws, size_t ws_bytes, uint32_t ctas_per_sm,
+                            uint32_t warps_per_cta, void *stream)
 {
     if (!d_table || !n_chunks || !n_items || n_items >= (1ull << 31) || level < 0 || level > 1)
         return BSGPU_ERR_ARG;
+    if (warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4) return BSGPU_ERR_ARG;
     if (!d_out_bytes || !d_chunk_status || !ws) return BSGPU_ERR_ARG;
     if (!aligned(d_table, 16) || !aligned(ws, 16) || !aligned(d_out_bytes, 8) ||
         !aligned(d_block_offsets, 8) || !aligned(d_chunk_status, 4))
@@ -563,24 +600,35 @@ int bsgpu_compress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_item
     b.offsets = d_block_offsets;
     b.status = d_chunk_status;
     b.level = level;
-    const uint32_t smem = compress_fast_smem_bytes(level);
     cudaError_t e;
-    if (level >= 1) {
-        const uint32_t g = batch_grid(occupancy(compress_batch_kernel<1>, smem), ctas_per_sm, n_items);
-        e = launch_batch(compress_batch_kernel<1>, smem, g, s, b);
-    } else {
-        const uint32_t g = batch_grid(occupancy(compress_batch_kernel<0>, smem), ctas_per_sm, n_items);
-        e = launch_batch(compress_batch_kernel<0>, smem, g, s, b);
+    switch (warps_per_cta * 2 + (level >= 1 ? 1 : 0)) {
+    case 2: e = launch_compress_batch<0, 1>(b, ctas_per_sm, n_items, s); break;
+    case 3: e = launch_compress_batch<1, 1>(b, ctas_per_sm, n_items, s); break;
+    case 4: e = launch_compress_batch<0, 2>(b, ctas_per_sm, n_items, s); break;
+    case 5: e = launch_compress_batch<1, 2>(b, ctas_per_sm, n_items, s); break;
+    case 8: e = launch_compress_batch<0, 4>(b, ctas_per_sm, n_items, s); break;
+    case 9: e = launch_compress_batch<1, 4>(b, ctas_per_sm, n_items, s); break;
+    default: return BSGPU_ERR_ARG;   // 3 warps per CTA: not built
     }
     return e == cudaSuccess ? BSGPU_OK : BSGPU_ERR_CUDA;
 }
 
-int bsgpu_decompress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_items,
-                           const uint64_t *d_in_bytes, const uint64_t *d_block_offsets,
-                           int *d_chunk_status, void *ws, size_t ws_bytes, uint32_t ctas_per_sm,
-                           void *stream)
+int bsgpu_compress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_items, int level,
+                         uint64_t *d_out_bytes, uint64_t *d_block_offsets, int *d_chunk_status,
+                         void *ws, size_t ws_bytes, uint32_t ctas_per_sm, void *stream)
+{
+    return bsgpu_compress_batch_ex(d_table, n_chunks, n_items, level, d_out_bytes,
+                                   d_block_offsets, d_chunk_status, ws, ws_bytes, ctas_per_sm, 1,
+                                   stream);
+}
+
+int bsgpu_decompress_batch_ex(const void *d_table, uint32_t n_chunks, uint64_t n_items,
+                              const uint64_t *d_in_bytes, const uint64_t *d_block_offsets,
+                              int *d_chunk_status, void *ws, size_t ws_bytes,
+                              uint32_t ctas_per_sm, uint32_t warps_per_cta, void *stream)
 {
     if (!d_table || !n_chunks || !n_items || n_items >= (1ull << 31)) return BSGPU_ERR_ARG;
+    if (warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4) return BSGPU_ERR_ARG;
     if (!d_chunk_status || !ws) return BSGPU_ERR_ARG;
     if (!aligned(d_table, 16) || !aligned(ws, 16) || !aligned(d_in_bytes, 8) ||
         !aligned(d_block_offsets, 8) || !aligned(d_chunk_status, 4))
@@ -603,13 +651,31 @@ int bsgpu_decompress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_it
         b.offsets = const_cast<uint64_t *>(d_block_offsets);
     } else {
         b.offsets = reinterpret_cast<uint64_t *>((uint8_t *)ws + w.offsets);
-        chain_walk_batch_kernel<<<(n_chunks + 127) / 128, 128, 0, s>>>(b);
+        if (cudaFuncSetAttribute(chain_walk_batch_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)WALK_SMEM) != cudaSuccess)
+            return BSGPU_ERR_CUDA;
+        const uint32_t g = (uint32_t)(n_chunks < (uint32_t)sm_count() ? n_chunks : sm_count());
+        chain_walk_batch_kernel<<<g, 32, WALK_SMEM, s>>>(b);
         if (cudaGetLastError() != cudaSuccess) return BSGPU_ERR_CUDA;
     }
-    const uint32_t smem = INPLACE_BUF + 16;
-    const uint32_t g = batch_grid(occupancy(decompress_batch_kernel, smem), ctas_per_sm, n_items);
-    return launch_batch(decompress_batch_kernel, smem, g, s, b) == cudaSuccess ? BSGPU_OK
-                                                                               : BSGPU_ERR_CUDA;
+    cudaError_t e;
+    switch (warps_per_cta) {
+    case 1: e = launch_decompress_batch<1>(b, ctas_per_sm, n_items, s); break;
+    case 2: e = launch_decompress_batch<2>(b, ctas_per_sm, n_items, s); break;
+    case 4: e = launch_decompress_batch<4>(b, ctas_per_sm, n_items, s); break;
+    default: return BSGPU_ERR_ARG;   // 3 warps per CTA: not built
+    }
+    return e == cudaSuccess ? BSGPU_OK : BSGPU_ERR_CUDA;
+}
+
+int bsgpu_decompress_batch(const void *d_table, uint32_t n_chunks, uint64_t n_items,
+                           const uint64_t *d_in_bytes, const uint64_t *d_block_offsets,
+                           int *d_chunk_status, void *ws, size_t ws_bytes, uint32_t ctas_per_sm,
+                           void *stream)
+{
+    return bsgpu_decompress_batch_ex(d_table, n_chunks, n_items, d_in_bytes, d_block_offsets,
+                                     d_chunk_status, ws, ws_bytes, ctas_per_sm, 1, stream);
 }
 
 }  // extern "C"

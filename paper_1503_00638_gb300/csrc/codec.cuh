@@ -771,6 +771,136 @@ BSG_D DecLoad dec_issue(const CodecArgs &a, uint32_t tile, uint8_t *dst, uint64_
 }
 
 
+// ---------------------------------------------------------------------------
+// Block index of a stream that carries none: the chain of 4-byte big-endian
+// length fields (reading R11) walked from offset 12.  The walk is serial
+// (each block starts where the previous one ends), so its speed is the
+// latency of one read per block; read from global memory that is a DRAM
+// round trip per block.  Instead the stream's bytes stream through shared
+// memory in windows of WALK_WIN bytes, WALK_NBUF of them in flight on the
+// bulk-copy engine, and lane 0 walks the windows.  The ragged first and last
+// (< 16) bytes of the stream, which no bulk copy can move, are read once by
+// the warp beforehand.  Every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr uint32_t WALK_WIN = 16384, WALK_NBUF = 8;
+constexpr uint32_t WALK_SMEM = WALK_WIN * WALK_NBUF + 8 * WALK_NBUF + 32;
+
+struct ChainWalk {
+    uintptr_t in, a0, a1;   // stream start; its 16-byte aligned middle [a0, a1)
+    uint32_t nwin;          // windows over [a0, a1)
+    uint8_t *buf;           // WALK_NBUF windows
+    uint64_t *bar;          // one barrier per window buffer
+    uint8_t *edge;          // bytes [in, a0) at edge[0..15], [a1, end) at edge[16..31]
+    bool ok;                // every wait ended in time
+};
+
+BSG_D void walk_issue(ChainWalk &w, uint32_t k)
+{
+    const uintptr_t lo = w.a0 + (uintptr_t)k * WALK_WIN;
+    const uintptr_t hi = lo + WALK_WIN < w.a1 ? lo + WALK_WIN : w.a1;
+    uint64_t *bar = w.bar + k % WALK_NBUF;
+    mbar_arrive_expect_tx(bar, (uint32_t)(hi - lo));
+    bulk_g2s(w.buf + (size_t)(k % WALK_NBUF) * WALK_WIN, reinterpret_cast<const void *>(lo),
+             (uint32_t)(hi - lo), bar);
+}
+
+// Byte at address x of the stream; window k (that holds x) must have arrived.
+BSG_D uint32_t walk_byte(const ChainWalk &w, uintptr_t x)
+{
+    if (x < w.a0) return w.edge[x - w.in];
+    if (x >= w.a1) return w.edge[16 + (x - w.a1)];
+    const uintptr_t r = x - w.a0;
+    return w.buf[(size_t)((r / WALK_WIN) % WALK_NBUF) * WALK_WIN + r % WALK_WIN];
+}
+
+// Lane 0: block offsets of blocks 0 .. nb-1 of the stream `in` (in_bytes
+// long, tail_b verbatim bytes at its end) into offsets[]; false when the
+// chain does not end exactly at the verbatim tail.  The other lanes only
+// help with the edge bytes.
+BSG_D bool chain_walk_staged(const uint8_t *in, uint64_t in_bytes, uint32_t nb, uint64_t tail_b,
+                             uint64_t *offsets, uint8_t *smem, uint32_t lane, bool &timely)
+{
+    ChainWalk w;
+    w.in = (uintptr_t)in;
+    const uintptr_t end = w.in + in_bytes;
+    w.a0 = (w.in + 15) & ~(uintptr_t)15;
+    w.a1 = end & ~(uintptr_t)15;
+    if (w.a1 < w.a0) w.a1 = w.a0;   // a stream shorter than one aligned chunk
+    w.nwin = (uint32_t)((w.a1 - w.a0 + WALK_WIN - 1) / WALK_WIN);
+    w.buf = smem;
+    w.bar = reinterpret_cast<uint64_t *>(smem + (size_t)WALK_WIN * WALK_NBUF);
+    w.edge = reinterpret_cast<uint8_t *>(w.bar + WALK_NBUF);
+    w.ok = true;
+    // the ragged edges: [in, a0) and [a1, end) (each under 16 bytes; when the
+    // stream has no aligned middle, [in, end) is split between the two)
+    if (lane < 16 && w.in + lane < (w.a0 < end ? w.a0 : end)) w.edge[lane] = in[lane];
+    if (lane >= 16 && w.a1 + (lane - 16) < end && w.a1 + (lane - 16) >= w.a0)
+        w.edge[lane] = *reinterpret_cast<const uint8_t *>(w.a1 + (lane - 16));
+    if (lane == 0)
+        for (uint32_t k = 0; k < WALK_NBUF; k++) mbar_init(w.bar + k, 1);
+    fence_mbar_init();
+    __syncwarp();
+    bool good = true;
+    if (lane == 0) {
+        // windows are issued, waited for and released in order: window k
+        // reuses the buffer of window k - WALK_NBUF once that one has been
+        // waited for and lies wholly before the next length field
+        int32_t issued = 0, done = 0;
+        const int32_t nwin = (int32_t)w.nwin;
+        while (issued < nwin && issued < (int32_t)WALK_NBUF) walk_issue(w, (uint32_t)issued++);
+        uint64_t D = 12;
+        uint32_t b = 0;
+        for (; b < nb; b++) {
+            if (D + 4 > in_bytes) {
+                good = false;
+                break;
+            }
+            offsets[b] = D;
+            const uintptr_t x = w.in + D;
+            // windows holding the part of x .. x+3 inside [a0, a1)
+            const uintptr_t lo = x > w.a0 ? x : w.a0, hi = x + 3 < w.a1 ? x + 3 : w.a1 - 1;
+            if (lo <= hi && w.a1 > w.a0) {
+                const int32_t wb = (int32_t)((hi - w.a0) / WALK_WIN);
+                while (done <= wb && w.ok) {
+                    if (done >= issued) {        // skipped ahead: its buffer is free
+                        fence_proxy_async_smem();
+                        walk_issue(w, (uint32_t)issued++);
+                    }
+                    if (!mbar_wait_bounded(w.bar + done % WALK_NBUF, (uint32_t)(done / WALK_NBUF) & 1u))
+                        w.ok = false;
+                    done++;
+                }
+            }
+            if (!w.ok) {
+                good = false;
+                break;
+            }
+            const uint32_t len = (walk_byte(w, x) << 24) | (walk_byte(w, x + 1) << 16) |
+                                 (walk_byte(w, x + 2) << 8) | walk_byte(w, x + 3);
+            D += 4ull + len;
+            // prefetch: windows whose buffers held waited-for windows wholly
+            // before the next length field
+            const uintptr_t nx = w.in + (D < in_bytes ? D : in_bytes);
+            const int32_t nwa = nx < w.a0 ? 0 : (int32_t)((nx - w.a0) / WALK_WIN);
+            while (issued < nwin && issued - (int32_t)WALK_NBUF < done &&
+                   issued - (int32_t)WALK_NBUF < nwa) {
+                fence_proxy_async_smem();   // the reads of the buffer before its next bulk write
+                walk_issue(w, (uint32_t)issued++);
+            }
+        }
+        for (; b < nb; b++) offsets[b] = in_bytes;   // fails the decoder's range check
+        good = good && D + tail_b == in_bytes;
+        // no bulk copy may still be writing when the warp moves on
+        while (done < issued) {
+            if (!mbar_wait_bounded(w.bar + done % WALK_NBUF, (uint32_t)(done / WALK_NBUF) & 1u))
+                w.ok = false;
+            done++;
+        }
+    }
+    timely = __shfl_sync(FULL, w.ok ? 1u : 0u, 0) != 0;
+    return __shfl_sync(FULL, good ? 1u : 0u, 0) != 0;
+}
+
 template <typename K>
 inline cudaError_t launch_warp_kernel(K kernel, uint32_t smem, uint32_t grid, cudaStream_t s,
                                       const CodecArgs &a)

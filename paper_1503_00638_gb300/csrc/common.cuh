@@ -1,7 +1,7 @@
 // Device helpers shared by the bsgpu kernels (sm_103a).
 //
 // Bit manipulation helpers are __host__ __device__ so that the host-side
-// unit test (csrc/selftest.cu) can check them on a CPU.
+// unit test (tests/host_emu/device_code_test.cu) can check them on a CPU.
 #pragma once
 
 #include <cstddef>
@@ -160,11 +160,13 @@ BSG_HD int32_t round_int_pow2(int32_t x, int k)
     return (int32_t)y;
 }
 
-// Division by an invariant 32-bit divisor d >= 1 through a multiply-high
-// (the round-up method for division by invariant integers): with
-// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
-// n / d = (t + ((n - t) >> 1)) >> (l - 1) where t = mulhi(m, n), exact for
-// every 32-bit n; d = 1 is kept apart (l - 1 would be negative).
+// Division by an invariant 32-bit divisor d >= 1 through a multiply-high:
+// the unsigned method of T. Granlund and P. L. Montgomery, "Division by
+// invariant integers using multiplication" (PLDI 1994, Sec. 4, Fig. 4.1).
+// With l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (t + ((n - t) >> 1)) >> (l - 1) where t = mulhi(m, n); their
+// Theorem 4.2 makes it exact for every 32-bit n.  d = 1 is kept apart
+// (l - 1 would be negative).
 struct FastDiv {
     uint32_t m, sh, d;
 };

@@ -674,24 +674,18 @@ uint32_t decompress_inplace_blocks_per_sm(uint32_t es)
     return e == cudaSuccess && n > 0 ? (uint32_t)n : 1u;
 }
 
-// Block offsets by walking the chain of 4-byte length fields (one thread).
-__global__ void chain_walk_kernel(const __grid_constant__ CodecArgs a, uint64_t *offsets)
+// Block offsets by walking the chain of 4-byte length fields: one warp, the
+// stream staged through shared memory (chain_walk_staged).
+__global__ void __launch_bounds__(32, 1) chain_walk_kernel(const __grid_constant__ CodecArgs a,
+                                                           uint64_t *offsets)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const uint64_t tail_b = (uint64_t)a.tail_elems * a.es;
-    uint64_t D = 12;
-    uint32_t b = 0;
-    bool bad = false;
-    for (; b < a.nb; b++) {
-        if (D + 4 > a.in_bytes) {
-            bad = true;
-            break;
-        }
-        offsets[b] = D;
-        D += 4 + (uint64_t)get_be32(a.in + D);
-    }
-    for (; b < a.nb; b++) offsets[b] = a.in_bytes;  // fails the range check
-    if (bad || D + tail_b != a.in_bytes) set_status(a.status, BSGPU_ERR_CORRUPT);
+    extern __shared__ __align__(128) uint8_t sm[];
+    const uint32_t lane = threadIdx.x & 31u;
+    bool timely = true;
+    const bool ok = chain_walk_staged(a.in, a.in_bytes, a.nb, (uint64_t)a.tail_elems * a.es,
+                                      offsets, sm, lane, timely);
+    if (lane == 0 && !timely) set_status(a.status, BSGPU_ERR_TIMEOUT);
+    else if (lane == 0 && !ok) set_status(a.status, BSGPU_ERR_CORRUPT);
 }
 
 // n_elem < 8: the elements sit verbatim after the header.
@@ -1012,7 +1006,10 @@ cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, 
 
 cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, cudaStream_t s)
 {
-    chain_walk_kernel<<<1, 32, 0, s>>>(a, offsets);
+    cudaError_t e = cudaFuncSetAttribute(chain_walk_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WALK_SMEM);
+    if (e != cudaSuccess) return e;
+    chain_walk_kernel<<<1, 32, WALK_SMEM, s>>>(a, offsets);
     return cudaGetLastError();
 }
 

@@ -11,8 +11,8 @@ block) item of a batch.  This module is host orchestration around them:
 * CUDA-graph capture of the compress launch, the decompress launch or both
   (the decompressor reads the compressor's per-chunk lengths on the device,
   so the pair needs no host round trip);
-* an autotuner over the launch shape (resident one-warp CTAs per SM) and,
-  optionally, the block size.
+* an autotuner over the launch shape (warps per CTA and resident CTAs per
+  SM, each launch on its own) and over the block size (``tune``).
 
 Every step of the codec runs in libbsgpu's kernels; nothing here touches the
 data.
@@ -37,6 +37,15 @@ class TuneResult:
     ctas_per_sm: int
     ms: float
     table: dict
+    warps_per_cta: int = 1
+
+
+# Launch shapes the tuner times: (warps per CTA, CTAs per SM); 0 CTAs = as many
+# as fit.  With 96 registers a thread, at most 20 warps are resident per SM
+# (the kernels' launch bounds), so the shapes span 8 to 20 warps per SM in
+# CTAs of one, two or four warps.
+SHAPES = ((1, 8), (1, 12), (1, 16), (1, 0), (2, 4), (2, 6), (2, 8), (2, 0), (4, 2), (4, 3),
+          (4, 4), (4, 0))
 
 
 class BatchCodec:
@@ -89,6 +98,8 @@ class BatchCodec:
         self.status_c = torch.zeros(self.n, dtype=torch.int32, device=dev)
         self.ctas_c = 0
         self.ctas_d = 0
+        self.warps_c = 1
+        self.warps_d = 1
         self.round_trip = round_trip
         if round_trip:
             self.dec_off = []
@@ -112,14 +123,16 @@ class BatchCodec:
 
     def compress(self, stream=None) -> None:
         bsgpu.compress_batch(self.table_c, self.n, self.n_items, self.out_bytes, self.offsets,
-                             self.status_c, self.ws_c, self.level, self.ctas_c, stream)
+                             self.status_c, self.ws_c, self.level, self.ctas_c, stream,
+                             warps_per_cta=self.warps_c)
 
     def decompress(self, stream=None) -> None:
         if not self.round_trip:
             raise RuntimeError("planned without round_trip")
         # stream lengths straight from the compressor's device array
         bsgpu.decompress_batch(self.table_d, self.n, self.n_items, self.out_bytes, self.offsets,
-                               self.status_d, self.ws_d, self.ctas_d, stream)
+                               self.status_d, self.ws_d, self.ctas_d, stream,
+                               warps_per_cta=self.warps_d)
 
     def capture(self, compress: bool = True, decompress: bool = True) -> torch.cuda.CUDAGraph:
         """A CUDA graph of the chosen launches on a side stream (replay with
@@ -175,26 +188,30 @@ class BatchCodec:
             best = min(best, start.elapsed_time(end))
         return best
 
-    def autotune(self, candidates=(0, 8, 12, 16), reps: int = 3) -> tuple:
-        """Pick the resident CTAs per SM of each launch by timing every
-        candidate (0 = as many as fit).  Returns (compress, decompress) as
-        :class:`TuneResult`."""
+    def autotune(self, shapes=SHAPES, reps: int = 3) -> tuple:
+        """Pick the launch shape (warps per CTA, CTAs per SM) of each launch by
+        timing every candidate; a bare int k in `shapes` means (1, k).
+        Returns (compress, decompress) as :class:`TuneResult`, whose table
+        maps "WxC" (W warps per CTA, C CTAs per SM, 0 = as many as fit) to
+        the best time in ms."""
+        shapes = [(1, k) if isinstance(k, int) else tuple(k) for k in shapes]
         res = []
         for which in ("c", "d") if self.round_trip else ("c",):
             table = {}
-            for k in candidates:
+            for w, k in shapes:
                 if which == "c":
-                    self.ctas_c = k
-                    table[k] = self._time(self.compress, reps)
+                    self.warps_c, self.ctas_c = w, k
+                    table[f"{w}x{k}"] = (self._time(self.compress, reps), w, k)
                 else:
-                    self.ctas_d = k
-                    table[k] = self._time(self.decompress, reps)
-            best = min(table, key=table.get)
+                    self.warps_d, self.ctas_d = w, k
+                    table[f"{w}x{k}"] = (self._time(self.decompress, reps), w, k)
+            best = min(table, key=lambda key: table[key][0])
+            ms, w, k = table[best]
             if which == "c":
-                self.ctas_c = best
+                self.warps_c, self.ctas_c = w, k
             else:
-                self.ctas_d = best
-            res.append(TuneResult(best, table[best], table))
+                self.warps_d, self.ctas_d = w, k
+            res.append(TuneResult(k, ms, {key: v[0] for key, v in table.items()}, w))
         return tuple(res)
 
 
@@ -203,19 +220,44 @@ def choose_block_elems(inputs, elem_sizes, candidates_bytes=(2048, 4096, 8192), 
     """Block size (bytes, the same for every chunk) with the fastest round
     trip among those whose compressed size is within ``ratio_slack`` of the
     smallest.  Returns (best block bytes, {bytes: (ms, compressed bytes)})."""
-    results = {}
+    best, table, _ = tune(inputs, elem_sizes, candidates_bytes, level=level, reps=reps,
+                          ratio_slack=ratio_slack)
+    return best, {b: (v["round_trip_ms"], v["compressed_bytes"]) for b, v in table.items()}
+
+
+def tune(inputs, elem_sizes, candidates_bytes=(2048, 4096, 8192), level: int = 0,
+         shapes=SHAPES, reps: int = 2, ratio_slack: float = 0.02, keep: bool = True) -> tuple:
+    """The batch autotuner: for every candidate block size (bytes, the same
+    for every chunk; Sec. 4.2.1 makes it the tunable of the method) tune the
+    launch shape of each launch (:meth:`BatchCodec.autotune`), then time the
+    round trip with the chosen shapes.  The block size chosen is the fastest
+    round trip among those whose compressed size is within ``ratio_slack``
+    of the smallest (a smaller block may be faster but compress worse).
+    Returns (best block bytes, {bytes: record}, the codec of the best block
+    size with its shapes set, or None when keep is False)."""
+    results, engines = {}, {}
     for bb in candidates_bytes:
         blocks = [bb // es for es in elem_sizes]
         eng = BatchCodec(inputs, elem_sizes, blocks, level=level)
-        eng.autotune(reps=1)
+        tc, td = eng.autotune(shapes, reps=reps)
 
         def both():
             eng.compress()
             eng.decompress()
         ms = eng._time(both, reps)
-        results[bb] = (ms, eng.compressed_bytes())
-        del eng
-    smallest = min(v[1] for v in results.values())
-    ok = [b for b, v in results.items() if v[1] <= smallest * (1 + ratio_slack)]
-    best = min(ok, key=lambda b: results[b][0])
-    return best, results
+        results[bb] = {"round_trip_ms": ms, "compressed_bytes": eng.compressed_bytes(),
+                       "compress": {"warps_per_cta": tc.warps_per_cta, "ctas_per_sm": tc.ctas_per_sm,
+                                    "ms": tc.ms, "candidates_ms": tc.table},
+                       "decompress": {"warps_per_cta": td.warps_per_cta,
+                                      "ctas_per_sm": td.ctas_per_sm, "ms": td.ms,
+                                      "candidates_ms": td.table}}
+        if keep:
+            engines[bb] = eng
+        else:
+            del eng
+    smallest = min(v["compressed_bytes"] for v in results.values())
+    ok = [b for b, v in results.items() if v["compressed_bytes"] <= smallest * (1 + ratio_slack)]
+    best = min(ok, key=lambda b: results[b]["round_trip_ms"])
+    chosen = engines.pop(best) if keep else None
+    engines.clear()
+    return best, results, chosen

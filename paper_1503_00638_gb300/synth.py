@@ -23,7 +23,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["VisConfig", "CONFIG_SMALL", "CONFIG_CHIME", "visibilities", "visibilities_physical",
-           "random_walk",
+           "random_walk", "random_walk_device", "batch_specs",
            "n_products", "auto_product_index"]
 
 
@@ -220,3 +220,57 @@ def random_walk_torch(n: int, elem_size: int, seed: int = 0, device="cuda"):
     if elem_size == 4:
         return w.to(torch.int32).view(torch.uint8)
     return w.view(torch.uint8)
+
+
+def random_walk_device(n: int, elem_size: int, seed: int = 0, floating: bool = False,
+                       device="cuda", chunk: int = 1 << 26):
+    """The random walk of random_walk() made on `device` in pieces of `chunk`
+    steps (so that multi-GB arrays need no multi-GB temporaries), as the bytes
+    of n elements of elem_size bytes: wrapping integers, or float64 values
+    (floating=True, elem_size 8) as random_walk() makes them for float64."""
+    import torch
+    if floating and elem_size != 8:
+        raise ValueError("floating walks are float64")
+    out = torch.empty(n * elem_size, dtype=torch.uint8, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    carry_i = torch.zeros((), dtype=torch.int64, device=device)
+    carry_f = torch.zeros((), dtype=torch.float64, device=device)
+    for a in range(0, n, chunk):
+        m = min(chunk, n - a)
+        k = torch.randint(0, 7, (m,), generator=g, device=device, dtype=torch.int32)
+        sgn = torch.randint(0, 2, (m,), generator=g, device=device, dtype=torch.int32) * 2 - 1
+        step = (sgn << k).to(torch.int64)
+        dst = out[a * elem_size:(a + m) * elem_size]
+        if floating:
+            w = torch.cumsum(step.to(torch.float64), 0) + carry_f
+            carry_f = w[-1].clone()
+            dst.copy_(w.view(torch.uint8))
+        else:
+            w = torch.cumsum(step, 0) + carry_i
+            carry_i = w[-1].clone()
+            if elem_size == 8:
+                dst.copy_(w.view(torch.uint8))
+            else:
+                low = (w & ((1 << (8 * elem_size)) - 1)).to(torch.int32)
+                if elem_size == 4:
+                    dst.copy_(low.view(torch.uint8))
+                elif elem_size == 2:
+                    dst.copy_(low.to(torch.int16).view(torch.uint8))
+                else:
+                    dst.copy_(low.to(torch.uint8))
+        del k, sgn, step, w
+    return out
+
+
+def batch_specs(n_chunks: int, seed: int):
+    """The shapes of a batch of uneven chunks: (bytes, element size, kind) per
+    chunk, sizes log-uniform on [64 KiB, 64 MiB], element size uniform on
+    {2, 4, 8}, kind "vis" (a visibility cube to be rounded) or "walk" (a
+    random walk) with equal odds."""
+    rng = np.random.default_rng([seed, 4])
+    sizes = np.exp(rng.uniform(np.log(64 << 10), np.log(64 << 20), n_chunks)).astype(np.int64)
+    es = rng.choice([2, 4, 8], n_chunks)
+    kind = rng.random(n_chunks) < 0.5
+    return [(int(b) // int(e) * int(e), int(e), "vis" if k else "walk")
+            for b, e, k in zip(sizes, es, kind)]

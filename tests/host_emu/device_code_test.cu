@@ -217,6 +217,36 @@ static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc
         cases.push_back(sh);
         rows.push_back(512);
     }
+    // blocks made of stretches of zero words, repeated words, copies of the
+    // bit-row above, random words and mixtures, with lengths that start and
+    // end anywhere relative to the 256-byte segments of the fast encoder's
+    // lanes (matches spilling into the next segments, row and run candidates
+    // side by side at segment starts)
+    for (int t = 0; t < 48; t++) {
+        const int S = t < 32 ? 8192 : 128 * (1 + (int)(rng() % 64));
+        const uint32_t rl = t % 3 == 0 ? 256u : 4u * (uint32_t)(1 + rng() % 64);
+        std::vector<uint32_t> w(S / 4);
+        size_t i = 0;
+        while (i < w.size()) {
+            const int kind = (int)(rng() % 6);
+            size_t len = 1 + rng() % (rng() % 4 == 0 ? 700 : 40);
+            for (size_t k = 0; k < len && i < w.size(); k++, i++) {
+                const uint32_t r = (uint32_t)rng();
+                switch (kind) {
+                case 0: w[i] = 0; break;
+                case 1: w[i] = i ? w[i - 1] : r; break;
+                case 2: w[i] = i >= rl / 4 ? w[i - rl / 4] : r; break;
+                case 3: w[i] = r; break;
+                case 4: w[i] = (k % 5 == 4) ? r : (i ? w[i - 1] : 0); break;
+                default: w[i] = (i >= rl / 4 && k % 3) ? w[i - rl / 4] ^ (r & 0x01000000u) : r; break;
+                }
+            }
+        }
+        std::vector<uint8_t> m(S);
+        memcpy(m.data(), w.data(), S);
+        cases.push_back(m);
+        rows.push_back(rl);
+    }
     size_t tg = 0, to = 0, tin = 0;
     for (size_t ci = 0; ci < cases.size(); ci++) {
         auto &c = cases[ci];

@@ -139,8 +139,9 @@ def test_launch_shape_does_not_change_streams(bs, eng_mod):
     xs = [to_dev(a) for a in arrays]
     e = eng_mod.BatchCodec(xs, es_l, bl)
     ref = None
-    for k in (0, 1, 3, 16):
+    for w, k in ((1, 0), (1, 1), (1, 3), (1, 16), (2, 0), (2, 3), (4, 0), (4, 1)):
         e.ctas_c = e.ctas_d = k
+        e.warps_c = e.warps_d = w
         e.stream_arena.zero_()
         e.dec_arena.zero_()
         e.compress()
@@ -151,8 +152,35 @@ def test_launch_shape_does_not_change_streams(bs, eng_mod):
             ref = snap
         else:
             assert all(torch.equal(a, b) for a, b in zip(ref, snap))
-    c, d = e.autotune(candidates=(0, 4, 16), reps=1)
-    assert c.ctas_per_sm in (0, 4, 16) and d.ctas_per_sm in (0, 4, 16)
+    c, d = e.autotune(shapes=((1, 0), (1, 4), (2, 8), (4, 0)), reps=1)
+    assert (c.warps_per_cta, c.ctas_per_sm) in ((1, 0), (1, 4), (2, 8), (4, 0))
+    assert (d.warps_per_cta, d.ctas_per_sm) in ((1, 0), (1, 4), (2, 8), (4, 0))
+    assert set(c.table) == {"1x0", "1x4", "2x8", "4x0"}
+    with pytest.raises(bs.BsgpuError):
+        bs.compress_batch(e.table_c, e.n, e.n_items, e.out_bytes, e.offsets, e.status_c, e.ws_c,
+                          warps_per_cta=3)
+
+
+def test_tuner_picks_block_size_and_shapes(bs, eng_mod, orc):
+    """The batch autotuner over block size x warps per CTA x CTAs per SM:
+    every candidate is timed and listed, the chosen codec runs with the
+    chosen shapes, and its streams decode with the oracle."""
+    arrays, es_l, _ = mixed_batch(seed=13, n_chunks=24, max_elems=120_000)
+    xs = [to_dev(a) for a in arrays]
+    best, table, e = eng_mod.tune(xs, es_l, (2048, 8192), shapes=((1, 0), (2, 0), (4, 2)), reps=1)
+    assert best in (2048, 8192) and set(table) == {2048, 8192}
+    for rec in table.values():
+        assert set(rec["compress"]["candidates_ms"]) == {"1x0", "2x0", "4x2"}
+        assert rec["round_trip_ms"] > 0 and rec["compressed_bytes"] > 0
+    assert (e.warps_c, e.ctas_c) == (table[best]["compress"]["warps_per_cta"],
+                                     table[best]["compress"]["ctas_per_sm"])
+    e.compress()
+    e.decompress()
+    assert all(torch.equal(e.output(i), xs[i]) for i in range(e.n))
+    for i in range(0, e.n, 5):
+        rc, back = orc.decompress(e.stream(i).cpu().numpy().tobytes(), arrays[i].size,
+                                  arrays[i].dtype, best // es_l[i])
+        assert rc == 0 and np.array_equal(back, arrays[i])
 
 
 def test_graph_replay(bs, eng_mod):

@@ -1,7 +1,9 @@
-"""GPU tests of the serving layer: continuous batching and the one-at-a-time
-pipeline return, for every request, the same bytes as the request processed
-alone (compressed stream and block index, or the decompressed elements);
-admission never reserves more than the cap; timestamps are ordered."""
+"""GPU tests of the serving layer: every result of the continuous-batching
+server and of the one-at-a-time pipeline is checked against the CPU oracle
+(served streams decode with the oracle's strict decoder to the request's
+elements; decompressed results equal the elements the stream was made from);
+each request yields the same bytes alone and in the mix; admission never
+reserves more than the cap; timestamps are ordered."""
 import numpy as np
 import pytest
 import torch
@@ -53,18 +55,27 @@ def make_requests(bs, serve, n=60, seed=0, rate=2000.0):
 
 
 def check(bs, reqs, results, originals):
+    """Every served result against the oracle: a compressed stream must decode
+    with the oracle's strict decoder to exactly the request's elements, and
+    its block index must point at each block's length field; a decompressed
+    result must equal the elements the stream was made from."""
+    import oracle as orc
+    orc.lib()
     for r in reqs:
         assert r.status == 0, r.rid
         assert r.arrival <= r.admitted <= r.done
         out, idx = results[r.rid]
         x = originals[r.rid]
         if r.kind == "compress":
-            single = bs.compress(x, r.block_elems, elem_size=r.elem_size)
-            assert single.nbytes == out.numel(), r.rid
-            assert torch.equal(single.buf[:single.nbytes].cpu(), out), r.rid
+            a = x.cpu().numpy().view(DT[r.elem_size])
+            s = out.numpy().tobytes()
+            rc, back = orc.decompress(s, r.n_elem, a.dtype, r.block_elems)
+            assert rc == 0 and np.array_equal(back.view(np.uint8), a.view(np.uint8)), r.rid
             nb = bs.num_blocks(r.n_elem, r.elem_size, r.block_elems)
-            if nb:
-                assert torch.equal(single.offsets[:nb].cpu(), idx), r.rid
+            pos = 12
+            for b in range(nb):
+                assert int(idx[b]) == pos, r.rid
+                pos += 4 + int.from_bytes(s[pos:pos + 4], "big")
         else:
             assert torch.equal(out, x.cpu()), r.rid
 
