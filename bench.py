@@ -1512,8 +1512,9 @@ def ratio_side_by_side(cfg, vis, args):
 
 def time_no_index(bsgpu, streams, want, n_fl, nbytes, indexed_ms, reps=5):
     """Decompression of whole-cube streams WITHOUT their block index (the
-    device first walks the chain of length fields, chain_walk_kernel), next
-    to the indexed figure; each output is checked against `want`."""
+    device first recovers it from the chain of length fields: the parallel
+    segment walk, checked, else the staged serial walk), next to the same
+    stream decoded with its index; each output is checked against `want`."""
     import torch
     out = {"indexed_decompress_gbs": nbytes / (indexed_ms / 1e3) / 1e9}
     dec = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
@@ -1532,9 +1533,28 @@ def time_no_index(bsgpu, streams, want, n_fl, nbytes, indexed_ms, reps=5):
             ts.append(e0.elapsed_time(e1))
         ok = bool(torch.equal(dec, want)) and bsgpu.status(ws) == 0
         ms = statistics.median(ts)
+        # the same stream with its block index (read off the length fields
+        # on the host), for the decoder's own time on it
+        h = d.cpu().numpy()
+        offs, D = [], 12
+        while len(offs) < bsgpu.num_blocks(n_fl, 4, BLOCK_ELEMS):
+            offs.append(D)
+            D += 4 + int.from_bytes(h[D:D + 4].tobytes(), "big")
+        od = torch.tensor(offs, dtype=torch.int64, device="cuda")
+        ti = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bsgpu.decompress(d, d.numel(), n_fl, 4, BLOCK_ELEMS, offsets=od, out=dec, ws=ws)
+            e1.record()
+            e1.synchronize()
+            ti.append(e0.elapsed_time(e1))
+        ok = ok and bool(torch.equal(dec, want))
+        mi = statistics.median(ti)
         out[name] = {"ms": ms, "gbs": nbytes / (ms / 1e3) / 1e9, "exact": ok,
-                     "stream_bytes": int(d.numel())}
-        del d, ws
+                     "with_index_ms": mi, "with_index_gbs": nbytes / (mi / 1e3) / 1e9,
+                     "index_recovery_ms": ms - mi, "stream_bytes": int(d.numel())}
+        del d, ws, od
     return out
 
 

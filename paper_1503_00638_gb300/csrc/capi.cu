@@ -10,6 +10,18 @@
 #include "kernels.cuh"
 #include "shuffle.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// An NVTX range around a C-ABI call, so that a profiler's timeline shows
+// the library's entry points (header-only NVTX: without a tool attached
+// each push and pop is a check of a null callback).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 using namespace bsg;
 
 namespace {
@@ -76,7 +88,7 @@ uint32_t persistent_grid(uint32_t smem_per_cta, uint64_t work)
 }
 
 struct WsLayout {
-    size_t state, autos, pairs, cft, qtab, offsets, slots, total;
+    size_t state, autos, pairs, cft, qtab, offsets, segs, slots, total;
 };
 
 // What the flags of the visibility entry points add to the workspace.
@@ -137,6 +149,8 @@ WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint
     if (op == BSGPU_OP_DECOMPRESS) {
         L.offsets = o;
         o += r256((size_t)g.nb * 8);
+        L.segs = o;   // the parallel recovery of a missing block index
+        o += r256(SEG_WS_BYTES);
     }
     L.total = o;
     return L;
@@ -275,6 +289,7 @@ int bsgpu_reduce_precision_ex(const void *in, void *out, int dtype, int64_t n_fr
                               int64_t n_inputs, int64_t n_time, double N, double f, int flags,
                               void *ws, size_t ws_bytes, void *stream)
 {
+    const NvtxRange nvtx_range("bsgpu_reduce_precision_ex");
     uint64_t n_prod, n_cplx;
     if (!vis_dtype_ok(dtype, flags, n_inputs)) return BSGPU_ERR_ARG;
     int rc = vis_check(n_freq, n_inputs, n_time, N, f, n_prod, n_cplx);
@@ -316,6 +331,7 @@ int bsgpu_full_noise_var(const void *vis, int dtype, int64_t n_freq, int64_t n_i
                          int64_t n_time, double N, int flags, double *d_s2, void *ws,
                          size_t ws_bytes, void *stream)
 {
+    const NvtxRange nvtx_range("bsgpu_full_noise_var");
     uint64_t n_prod, n_cplx;
     flags |= BSGPU_VIS_FULL_COV;
     if (!vis_dtype_ok(dtype, flags, n_inputs) || (flags & BSGPU_VIS_COMPENSATE))
@@ -339,6 +355,7 @@ int bsgpu_full_noise_var(const void *vis, int dtype, int64_t n_freq, int64_t n_i
 int bsgpu_reorder_time(const void *in, void *out, uint64_t n_time, uint64_t n_series,
                        size_t elem_size, void *stream)
 {
+    const NvtxRange nvtx_range("bsgpu_reorder_time");
     if (elem_size != 1 && elem_size != 2 && elem_size != 4 && elem_size != 8) return BSGPU_ERR_ARG;
     if (n_time == 0 || n_series == 0) return BSGPU_OK;
     if (!in || !out) return BSGPU_ERR_ARG;
@@ -374,12 +391,14 @@ static int shuffle_common(const void *in, void *out, size_t n_elem, size_t elem_
 int bsgpu_bitshuffle(const void *in, void *out, size_t n_elem, size_t elem_size,
                      size_t block_elems, void *stream)
 {
+    const NvtxRange nvtx_range("bsgpu_bitshuffle");
     return shuffle_common(in, out, n_elem, elem_size, block_elems, stream, false);
 }
 
 int bsgpu_bitunshuffle(const void *in, void *out, size_t n_elem, size_t elem_size,
                        size_t block_elems, void *stream)
 {
+    const NvtxRange nvtx_range("bsgpu_bitunshuffle");
     return shuffle_common(in, out, n_elem, elem_size, block_elems, stream, true);
 }
 
@@ -454,6 +473,7 @@ int bsgpu_compress(const void *in, size_t n_elem, size_t elem_size, size_t block
                    int level, void *out, size_t out_cap, uint64_t *d_out_bytes, uint64_t *d_block_offsets,
                    void *ws, size_t ws_bytes, void *stream)
 {
+    const NvtxRange nvtx_range("bsgpu_compress");
     Geometry g;
     int rc = geometry(n_elem, elem_size, block_elems, g);
     if (rc) return rc;
@@ -472,6 +492,7 @@ int bsgpu_compress_vis_ex(const void *vis, int dtype, int64_t n_freq, int64_t n_
                           uint64_t *d_out_bytes, uint64_t *d_block_offsets, void *ws,
                           size_t ws_bytes, void *stream)
 {
+    const NvtxRange nvtx_range("bsgpu_compress_vis_ex");
     uint64_t n_prod, n_cplx;
     if (!vis_dtype_ok(dtype, flags, n_inputs) || (elem_size != 4 && elem_size != 8))
         return BSGPU_ERR_ARG;
@@ -514,6 +535,7 @@ int bsgpu_decompress(const void *in, size_t in_bytes, void *out, size_t n_elem, 
                      size_t block_elems, const uint64_t *d_block_offsets, void *ws,
                      size_t ws_bytes, void *stream)
 {
+    const NvtxRange nvtx_range("bsgpu_decompress");
     Geometry g;
     int rc = geometry(n_elem, elem_size, block_elems, g);
     if (rc) return rc;
@@ -540,7 +562,7 @@ int bsgpu_decompress(const void *in, size_t in_bytes, void *out, size_t n_elem, 
         a.block_offsets = const_cast<uint64_t *>(d_block_offsets);
     } else if (g.nb) {
         a.block_offsets = reinterpret_cast<uint64_t *>((uint8_t *)ws + L.offsets);
-        cudaError_t e = launch_chain_walk(a, a.block_offsets, s);
+        cudaError_t e = launch_chain_walk(a, a.block_offsets, (uint8_t *)ws + L.segs, s);
         if (e != cudaSuccess) return BSGPU_ERR_CUDA;
     }
     uint32_t maxb = maxb_class(g.B * g.es);

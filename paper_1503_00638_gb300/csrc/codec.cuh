@@ -901,6 +901,64 @@ BSG_D bool chain_walk_staged(const uint8_t *in, uint64_t in_bytes, uint32_t nb, 
     return __shfl_sync(FULL, good ? 1u : 0u, 0) != 0;
 }
 
+// ---------------------------------------------------------------------------
+// The same block index recovered in parallel, exactly.  The stream's block
+// area [12, end) is cut into K segments, each at least SEG_M + 1 of the
+// largest blocks long.  Warp k takes as its start the first position of its
+// segment that reads as a block start (a length field in [1, lz4b(S)] whose
+// chain stays inside the area for SEG_DEPTH more blocks, or ends exactly at
+// its end) and walks the chain: it counts the blocks that start in the
+// segment and records the first SEG_M of them and the first SEG_M chain
+// positions past the segment.  Warp 0 starts at 12, so its walk is the true
+// chain.  A false start of warp k either dies (and the check below fails)
+// or falls onto the true chain; the chains meet where warp k - 1's positions
+// past its segment (true, by induction) meet warp k's first positions, and
+// from there warp k walks the true chain.  A scan checks that every pair
+// meets within SEG_M steps, corrects each count by the meeting point,
+// checks that the counts add up to nb and the last walk ends at the area's
+// end, and numbers the blocks; only then are the offsets written.  A stream
+// that fails any check takes the staged serial walk instead, so the index
+// is exact either way.
+// ---------------------------------------------------------------------------
+constexpr uint32_t SEG_MAX = 2048;   // segments (warps) of the parallel recovery
+constexpr uint32_t SEG_M = 8;        // chain positions recorded at each end of a segment
+constexpr uint32_t SEG_DEPTH = 8;    // blocks a start candidate's chain must survive
+
+struct SegRec {
+    uint64_t head[SEG_M];    // the first chain positions inside the segment (from the start)
+    uint64_t after[SEG_M];   // the first chain positions at or past the segment's end
+    uint64_t start, base;    // after the scan: the true first block start, its block number
+    uint32_t c, nh;          // blocks counted inside the segment; entries of head
+    uint32_t na, ok;         // entries of after; the walk stayed valid
+};
+static_assert(sizeof(SegRec) == 2 * 8 * SEG_M + 32, "segment record");
+constexpr size_t SEG_WS_REC = 256 + sizeof(SegRec) * SEG_MAX;
+
+// Big-endian 32-bit length field at offset p of the stream (4 byte loads,
+// issued together).
+BSG_D uint32_t stream_be32(const uint8_t *in, uint64_t p)
+{
+    const uint32_t b0 = __ldg(in + p), b1 = __ldg(in + p + 1), b2 = __ldg(in + p + 2),
+                   b3 = __ldg(in + p + 3);
+    return (b0 << 24) | (b1 << 16) | (b2 << 8) | b3;
+}
+
+// Whether offset p reads as a block start: a length field in [1, maxlen]
+// and a chain that stays inside [12, end) for `depth` more blocks or ends
+// exactly at end.
+BSG_D bool seg_plausible(const uint8_t *in, uint64_t p, uint64_t end, uint32_t maxlen,
+                         uint32_t depth)
+{
+    for (uint32_t v = 0; v <= depth; v++) {
+        if (p == end) return true;
+        if (p + 4 > end) return false;
+        const uint32_t len = stream_be32(in, p);
+        if (len < 1 || len > maxlen || p + 4 + len > end) return false;
+        p += 4ull + len;
+    }
+    return true;
+}
+
 template <typename K>
 inline cudaError_t launch_warp_kernel(K kernel, uint32_t smem, uint32_t grid, cudaStream_t s,
                                       const CodecArgs &a)

@@ -674,12 +674,189 @@ uint32_t decompress_inplace_blocks_per_sm(uint32_t es)
     return e == cudaSuccess && n > 0 ? (uint32_t)n : 1u;
 }
 
+static_assert(SEG_WS_BYTES >= SEG_WS_REC, "workspace of the parallel index recovery");
+
+// Parallel recovery of the block index, phase 1: warp k takes the first
+// plausible block start of segment k and walks the chain across the
+// segment and SEG_M positions past it.
+__global__ void __launch_bounds__(128) chain_seg_find_kernel(const __grid_constant__ CodecArgs a,
+                                                            SegRec *recs, uint32_t K, uint64_t Z,
+                                                            uint32_t maxlen)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (k >= K) return;
+    const uint64_t tail_b = (uint64_t)a.tail_elems * a.es;
+    SegRec *rec = recs + k;
+    uint32_t c = 0, nh = 0, na = 0;
+    bool ok = false;
+    if (a.in_bytes >= 12 + tail_b) {
+        const uint64_t end = a.in_bytes - tail_b;
+        const uint64_t lo = 12 + (uint64_t)k * Z;
+        const uint64_t hi = (k + 1 == K || lo + Z > end) ? end : lo + Z;
+        uint64_t f = k == 0 ? 12ull : ~0ull;
+        // candidates in address order, 128 per step: lane l tests the four
+        // offsets c0 + 4 l .. c0 + 4 l + 3 from seven bytes
+        for (uint64_t c0 = lo; k && c0 < hi && f == ~0ull; c0 += 128) {
+            const uint64_t p = c0 + 4 * lane;
+            uint32_t b[7];
+#pragma unroll
+            for (int t = 0; t < 7; t++) b[t] = p + t < end ? __ldg(a.in + p + t) : 0u;
+            uint32_t mine = 0;
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const uint64_t q = p + t;
+                const uint32_t len = (b[t] << 24) | (b[t + 1] << 16) | (b[t + 2] << 8) | b[t + 3];
+                if (q < hi && q + 4 <= end && len >= 1 && len <= maxlen && q + 4 + len <= end)
+                    mine |= 1u << t;
+            }
+            uint32_t m = __ballot_sync(FULL, mine != 0);
+            while (m) {   // deeper checks in address order (the warp in step)
+                const uint32_t l = __ffs(m) - 1;
+                m &= m - 1;
+                uint32_t bits = __shfl_sync(FULL, mine, l);
+                while (bits) {
+                    const uint32_t t = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const uint64_t q = c0 + 4 * l + t;
+                    if (seg_plausible(a.in, q, end, maxlen, SEG_DEPTH)) {
+                        f = q;
+                        break;
+                    }
+                }
+                if (f != ~0ull) break;
+            }
+        }
+        ok = f != ~0ull;
+        uint64_t D = f;
+        // each step advances D by 5 bytes at least; past the segment at most
+        // SEG_M more steps
+        while (ok && D < end) {
+            if (D < hi) {
+                if (nh < SEG_M && lane == 0) rec->head[nh] = D;
+                if (nh < SEG_M) nh++;
+                c++;
+            } else {
+                if (na == SEG_M) break;
+                if (lane == 0) rec->after[na] = D;
+                na++;
+            }
+            if (D + 4 > end) {
+                ok = false;
+                break;
+            }
+            const uint32_t len = stream_be32(a.in, D);
+            if (len < 1 || len > maxlen || D + 4 + len > end) {
+                ok = false;
+                break;
+            }
+            D += 4ull + len;
+        }
+        if (ok && D == end && na < SEG_M) {   // the chain reached the area's end
+            if (lane == 0) rec->after[na] = D;
+            na++;
+        }
+    }
+    if (lane == 0) {
+        rec->c = c;
+        rec->nh = nh;
+        rec->na = na;
+        rec->ok = ok ? 1u : 0u;
+    }
+}
+
+// Phase 2 (one CTA of 1024 threads): warp k - 1's positions past its
+// segment must meet warp k's first positions within SEG_M steps; the
+// meeting point corrects warp k's count (the true blocks before it that
+// start in segment k, minus warp k's own blocks before it); the counts must
+// add up to nb and the last walk must end at the area's end.  Then the
+// counts' exclusive scan numbers each segment's first block.
+__global__ void __launch_bounds__(1024) chain_seg_scan_kernel(const __grid_constant__ CodecArgs a,
+                                                             SegRec *recs, uint32_t K, uint64_t Z,
+                                                             uint32_t *verified)
+{
+    __shared__ uint64_t part[1024];
+    const uint32_t t = threadIdx.x;
+    const uint64_t tail_b = (uint64_t)a.tail_elems * a.es;
+    const uint64_t end = a.in_bytes >= 12 + tail_b ? a.in_bytes - tail_b : 0;
+    bool good = end != 0;
+    uint64_t cnt = 0;
+    uint64_t cnt_k[2] = {0, 0}, start_k[2] = {0, 0};
+    for (uint32_t k = 2 * t, u = 0; u < 2 && k < K; k++, u++) {
+        const SegRec &r = recs[k];
+        good = good && r.ok;
+        const uint64_t hi = (k + 1 == K || 12 + (uint64_t)(k + 1) * Z > end) ? end
+                                                                            : 12 + (uint64_t)(k + 1) * Z;
+        uint64_t ck = r.c, st = 12;
+        if (k > 0) {
+            const SegRec &q = recs[k - 1];
+            // first position past segment k - 1 that warp k's walk also visits
+            uint32_t hit_i = SEG_M, hit_j = 0;
+            for (uint32_t i = 0; i < q.na && hit_i == SEG_M; i++)
+                for (uint32_t j = 0; j < r.nh; j++)
+                    if (q.after[i] == r.head[j]) {
+                        hit_i = i;
+                        hit_j = j;
+                        break;
+                    }
+            // the true blocks before the meeting point must start in this segment
+            good = good && hit_i < SEG_M && (hit_i == 0 || q.after[hit_i - 1] < hi);
+            if (hit_i < SEG_M) {
+                ck = hit_i + (uint64_t)r.c - hit_j;
+                st = q.na ? q.after[0] : 0;
+            }
+        } else {
+            good = good && r.nh > 0 && r.head[0] == 12;
+        }
+        if (k + 1 == K) good = good && r.na > 0 && r.after[0] == end;
+        cnt_k[u] = ck;
+        start_k[u] = st;
+        cnt += ck;
+    }
+    part[t] = cnt;
+    __syncthreads();
+    for (uint32_t d = 1; d < 1024; d <<= 1) {   // inclusive scan (Hillis-Steele)
+        const uint64_t v = t >= d ? part[t - d] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    uint64_t base = part[t] - cnt;
+    for (uint32_t k = 2 * t, u = 0; u < 2 && k < K; k++, u++) {
+        recs[k].base = base;
+        recs[k].start = start_k[u];
+        recs[k].c = (uint32_t)cnt_k[u];
+        base += cnt_k[u];
+    }
+    const int all = __syncthreads_and(good ? 1 : 0);
+    if (t == 0) *verified = (all && part[1023] == a.nb) ? 1u : 0u;
+}
+
+// Phase 3: each segment writes the offsets of the true blocks starting in
+// it, walking the chain from its true first block.
+__global__ void __launch_bounds__(128) chain_seg_write_kernel(const __grid_constant__ CodecArgs a,
+                                                             const SegRec *recs, uint32_t K,
+                                                             const uint32_t *verified,
+                                                             uint64_t *offsets)
+{
+    const uint32_t k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (k >= K || !*verified || (threadIdx.x & 31u) != 0) return;
+    const SegRec &r = recs[k];
+    uint64_t D = r.start;
+    for (uint32_t i = 0; i < r.c; i++) {
+        offsets[r.base + i] = D;
+        D += 4ull + stream_be32(a.in, D);
+    }
+}
+
 // Block offsets by walking the chain of 4-byte length fields: one warp, the
-// stream staged through shared memory (chain_walk_staged).
+// stream staged through shared memory (chain_walk_staged); skipped when the
+// parallel recovery has verified its index (*done set).
 __global__ void __launch_bounds__(32, 1) chain_walk_kernel(const __grid_constant__ CodecArgs a,
-                                                           uint64_t *offsets)
+                                                           uint64_t *offsets, const uint32_t *done)
 {
     extern __shared__ __align__(128) uint8_t sm[];
+    if (done && *done) return;
     const uint32_t lane = threadIdx.x & 31u;
     bool timely = true;
     const bool ok = chain_walk_staged(a.in, a.in_bytes, a.nb, (uint64_t)a.tail_elems * a.es,
@@ -1004,12 +1181,31 @@ cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, 
     return launch_warp_kernel(decompress_kernel<65536, 0>, smem, grid, s, a);
 }
 
-cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, cudaStream_t s)
+cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, void *seg_ws,
+                              cudaStream_t s)
 {
     cudaError_t e = cudaFuncSetAttribute(chain_walk_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WALK_SMEM);
     if (e != cudaSuccess) return e;
-    chain_walk_kernel<<<1, 32, WALK_SMEM, s>>>(a, offsets);
+    uint32_t *verified = nullptr;
+    if (seg_ws) {
+        // the parallel recovery: segments of at least four largest blocks
+        const uint32_t S = (uint32_t)((uint64_t)a.B * a.es);
+        const uint32_t maxlen = S + S / 255u + 16u;
+        const uint64_t tail_b = (uint64_t)a.tail_elems * a.es;
+        const uint64_t area = a.in_bytes > 12 + tail_b ? a.in_bytes - 12 - tail_b : 0;
+        uint64_t K = area / ((SEG_M + 1ull) * (maxlen + 4));
+        if (K > SEG_MAX) K = SEG_MAX;
+        if (K < 1) K = 1;
+        const uint64_t Z = (area + K - 1) / K;
+        verified = reinterpret_cast<uint32_t *>(seg_ws);
+        SegRec *recs = reinterpret_cast<SegRec *>((uint8_t *)seg_ws + 256);
+        const uint32_t ctas = (uint32_t)((K + 3) / 4);
+        chain_seg_find_kernel<<<ctas, 128, 0, s>>>(a, recs, (uint32_t)K, Z, maxlen);
+        chain_seg_scan_kernel<<<1, 1024, 0, s>>>(a, recs, (uint32_t)K, Z, verified);
+        chain_seg_write_kernel<<<ctas, 128, 0, s>>>(a, recs, (uint32_t)K, verified, offsets);
+    }
+    chain_walk_kernel<<<1, 32, WALK_SMEM, s>>>(a, offsets, verified);
     return cudaGetLastError();
 }
 

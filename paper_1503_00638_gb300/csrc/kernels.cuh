@@ -116,7 +116,10 @@ constexpr uint32_t FAST_SLOT_BYTES = 8304;
 constexpr uint32_t FAST_MAX_WARPS = 3072;
 cudaError_t launch_compress_small(const CodecArgs &a, cudaStream_t s);
 cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s);
-cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, cudaStream_t s);
+// Block index of a stream without one (seg_ws: SEG_WS_BYTES of workspace for
+// the parallel recovery, or null for the staged serial walk alone).
+constexpr size_t SEG_WS_BYTES = 256 + 160 * 2048;
+cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, void *seg_ws, cudaStream_t s);
 
 // Block-size class: the smallest supported shared-memory plan for `bytes`.
 inline uint32_t maxb_class(uint32_t bytes)
