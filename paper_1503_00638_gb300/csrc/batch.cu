@@ -152,13 +152,16 @@ BSG_D void batch_prepare(const BatchChunk &ch, uint32_t tile, uint32_t Bb, uint8
 }
 
 // Exclusive prefix of block `tile` of chunk c by look-back, then its
-// placement (index entry, chunk header, verbatim tail, stream length).
+// placement (index entry, chunk header, verbatim tail, stream length); the
+// staging slot's lines are then dropped from L2.
 BSG_D void batch_place(const BatchArgs &b, uint32_t c, uint32_t tile, const uint8_t *blk,
                        uint32_t cs, uint32_t lane)
 {
     const CodecArgs a = chunk_args(b, c);
     const uint64_t excl = lookback_resolve(a.tile_state, tile, 4ull + cs, a.status, lane);
     compress_place(a, tile, blk, cs, 12 + excl, lane);
+    __syncwarp();
+    discard_slot(blk, 4 + cs, lane);
 }
 
 // Shared memory of one warp of the batch kernels, rounded up so that the

@@ -886,6 +886,145 @@ __global__ void decompress_small_kernel(const __grid_constant__ CodecArgs a)
 // ---------------------------------------------------------------------------
 // Standalone Bitshuffle / un-Bitshuffle (no LZ4): static tiles per warp
 // ---------------------------------------------------------------------------
+// Standalone Bitshuffle of blocks larger than 16 KiB (4- or 8-byte elements,
+// a multiple of 1024 elements): a block's groups of 32 elements are
+// independent, so the unit of work is a tile of 32 groups (1024 elements;
+// lane l takes group l), whatever the block size; only the stride of a
+// bit-row (B / 32 words) depends on it.  Forward: the tile is bulk-copied
+// into shared memory (the next one prefetched), each lane transposes its
+// group in registers and row r of the tile goes out as one coalesced
+// 128-byte store per row.  Inverse: lane l loads word l of each of the
+// tile's rows (coalesced), transposes and writes its group to shared
+// memory, and the tile is bulk-stored.  A warp holds two tiles (8 or 16
+// KiB) instead of whole blocks, so many warps fit on an SM.  Full blocks
+// only; the shortened last block and the verbatim tail take shuffle_kernel.
+constexpr uint32_t TILE_ELEMS = 1024;
+
+template <int ES, bool INV>
+__global__ void __launch_bounds__(32, 16) shuffle_tile_kernel(const __grid_constant__ CodecArgs a,
+                                                              uint32_t nfull)
+{
+    constexpr uint32_t TB = TILE_ELEMS * ES;   // bytes of a tile
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *buf[2] = {sm, sm + TB};
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * TB);
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const uint32_t tpb = a.B / TILE_ELEMS;             // tiles per block
+    const uint64_t items = (uint64_t)nfull * tpb;
+    const uint32_t rs = a.B / 32;                       // words per bit-row
+    const uint32_t rot = lane & (ES == 4 ? 7u : 15u);
+    uint32_t parity[2] = {0u, 0u};
+    auto tile_src = [&](uint64_t it) {   // the tile's bytes in the element order
+        const uint64_t b = it / tpb, t = it - b * tpb;
+        return (b * a.B + t * TILE_ELEMS) * ES;
+    };
+    uint64_t it = blockIdx.x;
+    int cur = 0;
+    if (!INV && it < items && lane == 0) {
+        mbar_arrive_expect_tx(&bar[0], TB);
+        bulk_g2s(buf[0], a.in + tile_src(it), TB, &bar[0]);
+    }
+    for (; it < items; it += gridDim.x) {
+        const uint64_t nxt = it + gridDim.x;
+        const uint64_t b = it / tpb, t = it - b * tpb;
+        if (!INV) {
+            if (!mbar_wait_bounded(&bar[cur], parity[cur]) && lane == 0)
+                set_status(a.status, BSGPU_ERR_TIMEOUT);
+            parity[cur] ^= 1u;
+            if (nxt < items && lane == 0) {
+                // the other buffer's generic reads finished before this step
+                mbar_arrive_expect_tx(&bar[cur ^ 1], TB);
+                bulk_g2s(buf[cur ^ 1], a.in + tile_src(nxt), TB, &bar[cur ^ 1]);
+            }
+            // rows of the tile: words [t * 32, t * 32 + 32) of each bit-row
+            uint32_t *o32 = reinterpret_cast<uint32_t *>(a.out + b * a.B * ES) + t * 32 + lane;
+            const uint8_t *grp = buf[cur] + (size_t)(ES * 32) * lane;
+            if (ES == 4) {
+                uint32_t v[32];
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(grp + 16u * ((k + rot) & 7u));
+                    v[4 * k] = q.x;
+                    v[4 * k + 1] = q.y;
+                    v[4 * k + 2] = q.z;
+                    v[4 * k + 3] = q.w;
+                }
+                transpose32(v);
+#pragma unroll
+                for (int r = 0; r < 32; r++) o32[(size_t)r * rs] = rotl(v[r], 4u * rot);
+            } else {
+                uint32_t lo[32], hi[32];
+#pragma unroll
+                for (int k = 0; k < 16; k++) {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(grp + 16u * ((k + rot) & 15u));
+                    lo[2 * k] = q.x;
+                    hi[2 * k] = q.y;
+                    lo[2 * k + 1] = q.z;
+                    hi[2 * k + 1] = q.w;
+                }
+                transpose32(lo);
+#pragma unroll
+                for (int r = 0; r < 32; r++) o32[(size_t)r * rs] = rotl(lo[r], 2u * rot);
+                transpose32(hi);
+#pragma unroll
+                for (int r = 0; r < 32; r++) o32[(size_t)(32 + r) * rs] = rotl(hi[r], 2u * rot);
+            }
+            __syncwarp();
+            fence_proxy_async_smem();   // the reads of buf[cur] before its next bulk write
+            __syncwarp();
+        } else {
+            const uint32_t *i32 =
+                reinterpret_cast<const uint32_t *>(a.in + b * a.B * ES) + t * 32 + lane;
+            // the previous bulk store from this buffer must have read it
+            if (lane == 0) bulk_wait_read0();
+            __syncwarp();
+            uint8_t *grp = buf[cur] + (size_t)(ES * 32) * lane;
+            if (ES == 4) {
+                uint32_t v[32];
+#pragma unroll
+                for (int r = 0; r < 32; r++) v[r] = rotr(__ldg(i32 + (size_t)r * rs), 4u * rot);
+                transpose32(v);
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    *reinterpret_cast<uint4 *>(grp + 16u * ((k + rot) & 7u)) =
+                        make_uint4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            } else {
+                uint32_t lo[32], hi[32];
+#pragma unroll
+                for (int r = 0; r < 32; r++) {
+                    lo[r] = rotr(__ldg(i32 + (size_t)r * rs), 2u * rot);
+                    hi[r] = rotr(__ldg(i32 + (size_t)(32 + r) * rs), 2u * rot);
+                }
+                transpose32(lo);
+                transpose32(hi);
+#pragma unroll
+                for (int k = 0; k < 16; k++)
+                    *reinterpret_cast<uint4 *>(grp + 16u * ((k + rot) & 15u)) =
+                        make_uint4(lo[2 * k], hi[2 * k], lo[2 * k + 1], hi[2 * k + 1]);
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                bulk_s2g(a.out + tile_src(it), buf[cur], TB);
+                bulk_commit();
+            }
+        }
+        cur ^= 1;
+    }
+    if (INV && lane == 0) bulk_wait0();
+    // the verbatim tail, when every block is full
+    if (nfull == a.nb && blockIdx.x == 0) {
+        const uint64_t first = (a.n_elem - a.tail_elems) * ES;
+        for (uint32_t k = lane; k < a.tail_elems * ES; k += 32) a.out[first + k] = a.in[first + k];
+    }
+}
+
 template <uint32_t MAXB, bool INV>
 __global__ void __launch_bounds__(32) shuffle_kernel(const __grid_constant__ CodecArgs a)
 {
@@ -908,7 +1047,7 @@ __global__ void __launch_bounds__(32) shuffle_kernel(const __grid_constant__ Cod
     }
     uint32_t parity[2] = {0u, 0u};
     bool pend[2] = {false, false};
-    uint32_t tile = blockIdx.x;
+    uint32_t tile = a.tile_begin + blockIdx.x;   // tile_begin: blocks before it are done
     int cur = 0;
     if (tile < a.nb)
         pend[0] = load_block(buf[0], a.in + (uint64_t)tile * a.B * a.es,
@@ -1109,9 +1248,47 @@ cudaError_t launch_reduce_precision(const float *in, float *out, uint64_t n_cplx
     return cudaGetLastError();
 }
 
-cudaError_t launch_shuffle(const CodecArgs &a, bool inverse, uint32_t maxb, uint32_t grid,
+template <typename K>
+cudaError_t launch_tiles(K kernel, uint32_t smem, uint32_t grid, cudaStream_t s, const CodecArgs &a,
+                         uint32_t nfull)
+{
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kernel<<<grid, 32, smem, s>>>(a, nfull);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shuffle(const CodecArgs &a_in, bool inverse, uint32_t maxb, uint32_t grid,
                            cudaStream_t s)
 {
+    CodecArgs a = a_in;
+    if (maxb > 16384 && (a.es == 4 || a.es == 8) && a.B % TILE_ELEMS == 0 && a.nb) {
+        // full blocks by tiles; the shortened last block (if any) and the
+        // tail below
+        const uint32_t nfull = a.last_B == a.B ? a.nb : a.nb - 1;
+        if (nfull) {
+            const uint32_t tsm = 2 * TILE_ELEMS * a.es + 16;
+            int dev = 0, sms = 148;
+            if (cudaGetDevice(&dev) == cudaSuccess)
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const uint64_t items = (uint64_t)nfull * (a.B / TILE_ELEMS);
+            uint64_t g = (uint64_t)sms * 16;
+            if (g > items) g = items;
+            cudaError_t e;
+            if (a.es == 4)
+                e = inverse ? launch_tiles(shuffle_tile_kernel<4, true>, tsm, (uint32_t)g, s, a, nfull)
+                            : launch_tiles(shuffle_tile_kernel<4, false>, tsm, (uint32_t)g, s, a, nfull);
+            else
+                e = inverse ? launch_tiles(shuffle_tile_kernel<8, true>, tsm, (uint32_t)g, s, a, nfull)
+                            : launch_tiles(shuffle_tile_kernel<8, false>, tsm, (uint32_t)g, s, a, nfull);
+            if (e != cudaSuccess || nfull == a.nb) return e;
+        }
+        a.tile_begin = nfull;   // the shortened last block and the tail
+        grid = 1;
+    }
     uint32_t smem = shuffle_smem_bytes(maxb);
     if (maxb <= 8192)
         return inverse ? launch_warp_kernel(shuffle_kernel<8192, true>, smem, grid, s, a)

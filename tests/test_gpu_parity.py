@@ -84,7 +84,11 @@ def test_reduce_precision_special_values(bs, orc):
 SHUF = [(es, B, n) for es in (1, 2, 4, 8) for B in (8, 24, 512, 2048)
         for n in (0, 5, 8, 9, 2047, 4096 + 13, 20000)]
 SHUF += [(4, 2048, 2048 * 300 + 77), (8, 1024, 1024 * 200 + 9), (2, 4096, 4096 * 64 + 15),
-         (1, 8192, 8192 * 40 + 3), (4, 0, 50000), (8, 8192, 8192 * 7), (4, 16384, 16384 * 5 + 8)]
+         (1, 8192, 8192 * 40 + 3), (4, 0, 50000), (8, 8192, 8192 * 7), (4, 16384, 16384 * 5 + 8),
+         # blocks over 16 KiB go by 1024-element tiles: full blocks, a shortened
+         # last block, a verbatim tail
+         (4, 8192, 8192 * 40 + 19), (4, 8192, 8192 * 3), (8, 4096, 4096 * 30 + 5),
+         (8, 8192, 8192 * 9 + 1029), (4, 5120, 5120 * 11 + 8), (8, 3072, 3072 * 7 + 100)]
 
 
 @pytest.mark.parametrize("es,B,n", SHUF)
@@ -313,13 +317,21 @@ def test_chime_full_size_all_slabs(bs, orc, f):
         rc, back = orc.decompress(_substream(buf, offs, fr * per, (fr + 1) * per, 8192),
                                   slab // 4, np.float32, 2048)
         ok = ok and rc == 0 and np.array_equal(back.view(np.uint8), wb)
-        return ok, len(orc.compress(want.view(np.float32).reshape(-1), 2048)) - 12
+        return ok, orc.compress(want.view(np.float32).reshape(-1), 2048)[12:]
 
     with cf.ThreadPoolExecutor(max_workers=max(1, len(os.sched_getaffinity(0)))) as ex:
         res = list(ex.map(check, range(1024)))
     bad = [fr for fr, (ok, _) in enumerate(res) if not ok]
     assert not bad, f"slabs differing from the oracle: {bad[:10]}"
-    orc_bytes = 12 + sum(n for _, n in res)
+    orc_bytes = 12 + sum(len(b) for _, b in res)
+    # both whole-cube streams decode on the GPU without their block index
+    # (recovered on the device from the chain of length fields)
+    whole = vis.nbytes.to_bytes(8, "big") + (8192).to_bytes(4, "big") + b"".join(b for _, b in res)
+    od = torch.frombuffer(bytearray(whole), dtype=torch.uint8).cuda()
+    for st in (c.buf[:c.nbytes], od):
+        ws = bs.new_workspace(bs.workspace_size(bs.OP_DECOMPRESS, n_fl, 4, 2048))
+        o2 = bs.decompress(st, st.numel(), n_fl, 4, 2048, offsets=None, ws=ws)
+        assert bs.status(ws) == 0 and np.array_equal(o2.cpu().numpy(), got)
     print(f"f={f}: ratio gpu {c.nbytes / vis.nbytes:.4f} oracle {orc_bytes / vis.nbytes:.4f}")
     assert c.nbytes < 1.15 * orc_bytes
 
