@@ -16,6 +16,13 @@ its output does not fit.
 * :class:`SerialServer`: the plain pipeline, one request at a time through
   the single-stream calls (bsgpu_compress / bsgpu_decompress).
 
+A request may carry a deadline for its admission, and a client may cancel
+a request (set its ``cancelled`` flag, from any thread) while it waits: a
+request that is still waiting past its deadline, or cancelled, leaves the
+queue without touching the GPU, with status ``EXPIRED`` or ``CANCELLED``
+(host-side failures: nothing on the device waits for it).  A request already
+admitted completes normally.
+
 Latency is measured from arrival to the observed completion.  Each request's
 output is the same bytes alone or in any mix (tests check it); ``on_done``
 sees it before its range returns to the arena.  Host orchestration only:
@@ -33,6 +40,8 @@ import torch
 from . import bsgpu
 
 ALIGN = 256
+EXPIRED = -101     # status of a request still waiting at its deadline
+CANCELLED = -102   # status of a request cancelled while waiting
 
 
 def _round(x: int) -> int:
@@ -50,6 +59,8 @@ class Request:
     block_elems: int = 0
     level: int = 0
     index: torch.Tensor | None = None   # decompress: the stream's block index
+    deadline: float | None = None       # latest admission time (seconds after the start)
+    cancelled: bool = False             # set by the client to withdraw a waiting request
     # filled in by the server
     admitted: float | None = None
     done: float | None = None
@@ -83,6 +94,7 @@ class Request:
 
 
 def latency_summary(reqs) -> dict:
+    reqs = [r for r in reqs if r.status not in (EXPIRED, CANCELLED)]
     lat = sorted(r.latency for r in reqs)
     q = lambda p: lat[min(len(lat) - 1, int(p * len(lat)))]  # noqa: E731
     span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
@@ -123,6 +135,16 @@ class _Server:
         r.out_off, r.out_cap = off, need
         return True
 
+    def _purge(self, waiting, now: float) -> int:
+        """Withdraw waiting requests that are cancelled or past their deadline."""
+        gone = [r for r in waiting
+                if r.cancelled or (r.deadline is not None and now > r.deadline)]
+        for r in gone:
+            waiting.remove(r)
+            r.status = CANCELLED if r.cancelled else EXPIRED
+            r.done = now
+        return len(gone)
+
     def _finish(self, r: Request, now: float):
         r.done = now
         if self.on_done:
@@ -142,6 +164,8 @@ class _Server:
                 waiting.append(reqs[nxt])
                 nxt += 1
             n_done += self._retire(now)
+            if waiting:
+                n_done += self._purge(waiting, now)
             launched = self._launch(waiting, now) if waiting else False
             if not launched and not self._busy():
                 if nxt < len(reqs):

@@ -138,3 +138,30 @@ def test_request_larger_than_cap_is_refused(mods):
     r = serve.Request(0, "compress", 0.0, x, x.numel() // 4, 4, 0)
     with pytest.raises(ValueError):
         serve.BatchingServer(cap_bytes=1 << 20).run([r])
+
+
+def test_expired_and_cancelled_requests_leave_the_queue(mods):
+    """Host-side failures of the serving loop: with a small cap, later
+    requests wait behind earlier ones; those whose admission deadline passes
+    while they wait, and those the client cancels, leave the queue without a
+    launch (status EXPIRED / CANCELLED), and every other request completes
+    with a result the oracle decodes."""
+    bs, serve = mods
+    reqs, originals = make_requests(bs, serve, n=40, seed=21, rate=1e6)
+    for r in reqs[10::5]:
+        r.deadline = r.arrival          # expires unless admitted at once
+    for r in reqs[12::7]:
+        r.cancelled = True
+    results = {}
+    srv = serve.BatchingServer(cap_bytes=16 << 20, depth=1, max_chunks=4,
+                               on_done=collector(results))
+    srv.run(reqs)
+    gone = [r for r in reqs if r.status in (serve.EXPIRED, serve.CANCELLED)]
+    assert any(r.status == serve.CANCELLED for r in gone)
+    assert all(r.cancelled or r.deadline is not None for r in gone)
+    assert all(r.rid not in results for r in gone)
+    kept = [r for r in reqs if r not in gone]
+    check(bs, kept, results, originals)
+    assert srv.arena.stats()["used"] == 0
+    s = serve.latency_summary(reqs)
+    assert s["n"] == len(kept)
