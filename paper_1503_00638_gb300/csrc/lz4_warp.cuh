@@ -502,9 +502,25 @@ BSG_D uint32_t lz4_encode_bitmap(const uint8_t *src, uint32_t S, uint32_t rowlen
     return o;
 }
 
-// Shared scratch of lz4_encode_bitmap_fast: four 64-word bitmaps and three
-// "next non-zero word" tables of 65 entries.
-constexpr uint32_t LZ4_FAST_SCRATCH = 4u * 64u * 4u + 3u * 80u;
+// The level-0 parse as a graph.  A match of kind k (the previous bit-row, or
+// a run of equal words) that starts anywhere in a maximal run of kind-k
+// candidate words ends at the same place: three words after the run's last
+// candidate (its equal words end there), capped at the match limit, plus the
+// equal low bytes of the next word.  So the greedy parse only ever stands at
+// such run ends (and at the block start).  Those are the nodes; a node's
+// successor (the first candidate at or after its position, the kind the parse
+// takes there and the candidate run holding it) does not depend on how the
+// parse got there, so the warp computes every node's successor at once and
+// the serial part of the parse is one shared load per sequence.  A block with
+// LZ4_NODE_CAP nodes or more walks from candidate to match end instead; both
+// give the same greedy parse, byte for byte.
+constexpr uint32_t LZ4_NODE_CAP = 128;
+
+// Shared scratch of lz4_encode_bitmap_fast: four 64-word bitmaps (candidates
+// of either kind, bit-row candidates, and the last candidates of bit-row and
+// of run candidate runs), the next-non-zero table of the first (65 entries in
+// 80 bytes), two 64-entry rank tables and the node table.
+constexpr uint32_t LZ4_FAST_SCRATCH = 4u * 64u * 4u + 80u + 2u * 64u + 4u * LZ4_NODE_CAP;
 
 // First set bit in [from, to] of a 64-word shared bitmap, through its table
 // nnz[k] = first k' >= k with bm[k'] != 0 (64 when none): one or two
@@ -546,19 +562,35 @@ BSG_D void smap_store(uint32_t *bm, uint8_t *nnz, const uint32_t (&w)[2], uint32
     if (lane == 0) nnz[64] = 64;
 }
 
+// Bit w of the result: bit w of c set and bit w + 1 clear (the last of a run
+// of set bits), for a lane's two words of a 64-word bitmap (word lane + 32 j
+// in c[j]); bits past word 63 count as clear.
+BSG_D void run_ends(const uint32_t (&c)[2], uint32_t (&e)[2], uint32_t lane)
+{
+    const uint32_t n0 = __shfl_down_sync(FULL, c[0], 1), n1 = __shfl_down_sync(FULL, c[1], 1);
+    const uint32_t w32 = __shfl_sync(FULL, c[1], 0);
+    const uint32_t h0 = lane == 31 ? w32 : n0, h1 = lane == 31 ? 0u : n1;
+    e[0] = c[0] & ~((c[0] >> 1) | (h0 << 31));
+    e[1] = c[1] & ~((c[1] >> 1) | (h1 << 31));
+}
+
 // Level-0 encoder for the fast path (S a multiple of 128, at most 8192): the
 // same parse as lz4_encode_bitmap.  The equality bitmaps are built in
 // registers (two words per lane) and kept in shared memory `scr`
-// (LZ4_FAST_SCRATCH bytes, 4-byte aligned) with next-non-zero tables, so
-// that each step of the (inherently sequential) parse is a few broadcast
-// loads.  The sequences are emitted 32 at a time in parallel: the parse
-// collects up to 32 (literal start, match start, match length, offset)
-// descriptors, one per lane; a warp scan of their encoded lengths places
-// them; each lane writes its own token, length and offset bytes; the literal
-// runs are copied one after another by the whole warp.
+// (LZ4_FAST_SCRATCH bytes, 4-byte aligned) with the candidate-run ends and
+// their ranks, from which the warp builds the parse graph (node table: the
+// node's position in 13 bits, the first candidate after it in 11, the
+// successor node in 8, 255 for none).  The sequences are emitted 32 at a time
+// in parallel: the parse collects up to 32 (literal start, match start, match
+// length, offset) descriptors, one per lane; a warp scan of their encoded
+// lengths places them; each lane writes its own token, length and offset
+// bytes; the literal runs are copied one after another by the whole warp.
+// NODE_CAP below LZ4_NODE_CAP only serves tests of the candidate walk.
+template <uint32_t NODE_CAP = LZ4_NODE_CAP>
 BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t rowlen, uint8_t *dst,
                                       uint32_t *scr)
 {
+    static_assert(NODE_CAP >= 1 && NODE_CAP <= LZ4_NODE_CAP && LZ4_NODE_CAP < 255, "node table");
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
     const uint32_t NW = S / 4, NB = NW / 32;
@@ -607,14 +639,55 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
         }
     }
     const uint32_t Cany[2] = {Crow[0] | Crun[0], Crow[1] | Crun[1]};
-    const uint32_t Zrow[2] = {~Erow[0], ~Erow[1]}, Zrun[2] = {~Erun[0], ~Erun[1]};
-    uint32_t *sCany = scr, *sCrow = scr + 64, *sZrow = scr + 128, *sZrun = scr + 192;
-    uint8_t *nCany = reinterpret_cast<uint8_t *>(scr + 256), *nZrow = nCany + 80, *nZrun = nZrow + 80;
+    uint32_t CEr[2], CEu[2];
+    run_ends(Crow, CEr, lane);
+    run_ends(Crun, CEu, lane);
+    uint32_t *sCany = scr, *sCrow = scr + 64, *sCEr = scr + 128, *sCEu = scr + 192;
+    uint8_t *nCany = reinterpret_cast<uint8_t *>(scr + 256);
+    uint8_t *preR = nCany + 80, *preU = preR + 64;
+    uint32_t *node = scr + 256 + (80 + 128) / 4;
     smap_store(sCany, nCany, Cany, lane);
-    smap_store(sZrow, nZrow, Zrow, lane);
-    smap_store(sZrun, nZrun, Zrun, lane);
     sCrow[lane] = Crow[0];
     sCrow[lane + 32] = Crow[1];
+    sCEr[lane] = CEr[0];
+    sCEr[lane + 32] = CEr[1];
+    sCEu[lane] = CEu[0];
+    sCEu[lane + 32] = CEu[1];
+    // run ends of each kind in the words before word k (bit-row in the low,
+    // run in the high 16 bits): the rank of a candidate run among its kind
+    const uint32_t c0 = (uint32_t)__popc(CEr[0]) | ((uint32_t)__popc(CEu[0]) << 16);
+    const uint32_t c1 = (uint32_t)__popc(CEr[1]) | ((uint32_t)__popc(CEu[1]) << 16);
+    uint32_t i0 = c0, i1 = c1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t0 = __shfl_up_sync(FULL, i0, d), t1 = __shfl_up_sync(FULL, i1, d);
+        if (lane >= (uint32_t)d) {
+            i0 += t0;
+            i1 += t1;
+        }
+    }
+    const uint32_t tot0 = __shfl_sync(FULL, i0, 31);
+    const uint32_t tot = __shfl_sync(FULL, i1, 31) + tot0;
+    const uint32_t x0 = i0 - c0, x1 = i1 - c1 + tot0;  // exclusive, words lane and lane + 32
+    const uint32_t Nr = tot & 0xffffu, N = Nr + (tot >> 16);
+    const bool graph = N < NODE_CAP;  // nodes 0 .. N - 1 and the start, N
+    if (graph) {
+        preR[lane] = (uint8_t)x0;
+        preR[lane + 32] = (uint8_t)x1;
+        preU[lane] = (uint8_t)(x0 >> 16);
+        preU[lane + 32] = (uint8_t)(x1 >> 16);
+        // node ids in position order within each kind: the last word of a
+        // bit-row candidate run first, then those of run candidate runs
+#pragma unroll
+        for (uint32_t j = 0; j < 2; j++) {
+            const uint32_t wb = 32u * (lane + 32u * j), x = j ? x1 : x0;
+            uint32_t m = j ? CEr[1] : CEr[0], id = x & 0xffffu;
+            for (; m; m &= m - 1) node[id++] = wb + (uint32_t)(__ffs(m) - 1);
+            m = j ? CEu[1] : CEu[0];
+            id = Nr + (x >> 16);
+            for (; m; m &= m - 1) node[id++] = wb + (uint32_t)(__ffs(m) - 1);
+        }
+    }
     __syncwarp();
 
     uint32_t anchor = 0, o = 0;
@@ -622,32 +695,79 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
         const uint32_t wlim = (S - LZ4_LASTLITERALS - LZ4_L0_MINMATCH) / 4;
         const uint32_t matchlimit = S - LZ4_LASTLITERALS;
         const uint32_t cap = matchlimit / 4;
+        if (graph) {
+            // each node's position and successor (a lane reads and rewrites
+            // only its own entries)
+            for (uint32_t id = lane; id <= N; id += 32) {
+                uint32_t p = 0;
+                if (id < N) {
+                    uint32_t e = node[id] + LZ4_L0_MINWORDS;
+                    if (e > cap) e = cap;
+                    p = 4 * e;
+                    if (p < matchlimit) {
+                        const uint32_t x = s32[e] ^ s32[e - (id < Nr ? R : 1u)];
+                        uint32_t eq = x ? ((uint32_t)(__ffs(x) - 1) >> 3) : 4u;
+                        if (eq > matchlimit - p) eq = matchlimit - p;
+                        p += eq;
+                    }
+                }
+                const uint32_t w = smap_first_set(sCany, nCany, (p + 3) / 4, wlim);
+                uint32_t rec = p | (255u << 24);
+                if (w != ~0u) {
+                    // the previous bit-row wins a tie
+                    const uint32_t wd = w >> 5, below = (1u << (w & 31u)) - 1u;
+                    const bool row = (sCrow[wd] >> (w & 31u)) & 1u;
+                    const uint32_t nx = row ? preR[wd] + (uint32_t)__popc(sCEr[wd] & below)
+                                            : Nr + preU[wd] + (uint32_t)__popc(sCEu[wd] & below);
+                    rec = p | (w << 13) | (nx << 24);
+                }
+                node[id] = rec;
+            }
+            __syncwarp();
+        }
+        uint32_t rec = graph ? node[N] : 0u;
         uint32_t pos = 0;
         bool more = true;
         for (uint32_t guard = 0; more && guard <= NW; guard++) {
             // parse up to 32 sequences; lane k keeps the k-th
             uint32_t my_anchor = 0, my_mp = 0, my_len = 0, my_off = 0, n = 0;
             for (; n < 32; n++) {
-                const uint32_t w0 = (pos + 3) / 4;
-                const uint32_t w = smap_first_set(sCany, nCany, w0, wlim);
-                if (w == ~0u) {
-                    more = false;
-                    break;
+                uint32_t mp, len, off;
+                if (graph) {
+                    const uint32_t nx = rec >> 24;
+                    if (nx == 255u) {
+                        more = false;
+                        break;
+                    }
+                    const uint32_t nrec = node[nx];
+                    mp = 4 * ((rec >> 13) & 2047u);
+                    len = (nrec & 8191u) - mp;
+                    off = nx < Nr ? rowlen : 4u;
+                    rec = nrec;
+                } else {
+                    const uint32_t w = smap_first_set(sCany, nCany, (pos + 3) / 4, wlim);
+                    if (w == ~0u) {
+                        more = false;
+                        break;
+                    }
+                    // the previous bit-row wins a tie
+                    const bool row = (sCrow[w >> 5] >> (w & 31u)) & 1u;
+                    const uint32_t *ce = row ? sCEr : sCEu;
+                    // the candidate run holding w ends at or after it
+                    uint32_t wd = w >> 5, m = ce[wd] & (~0u << (w & 31u));
+                    while (m == 0 && wd < 63) m = ce[++wd];
+                    uint32_t e = m ? 32 * wd + (uint32_t)(__ffs(m) - 1) + LZ4_L0_MINWORDS : cap;
+                    if (e > cap) e = cap;
+                    off = row ? rowlen : 4u;
+                    mp = 4 * w;
+                    len = 4 * (e - w);
+                    if (4 * e < matchlimit) {
+                        const uint32_t x = s32[e] ^ s32[e - off / 4];
+                        uint32_t eq = x ? ((uint32_t)(__ffs(x) - 1) >> 3) : 4u;
+                        if (eq > matchlimit - 4 * e) eq = matchlimit - 4 * e;
+                        len += eq;
+                    }
                 }
-                // the previous bit-row wins a tie
-                const uint32_t isrow = (sCrow[w >> 5] >> (w & 31u)) & 1u;
-                const uint32_t off = isrow ? rowlen : 4u;
-                uint32_t wz = smap_first_set(isrow ? sZrow : sZrun, isrow ? nZrow : nZrun,
-                                             w + LZ4_L0_MINWORDS, cap - 1);
-                if (wz == ~0u) wz = cap;
-                uint32_t len = 4 * (wz - w);
-                if (4 * wz < matchlimit) {
-                    const uint32_t x = s32[wz] ^ s32[wz - off / 4];
-                    uint32_t eq = x ? ((uint32_t)(__ffs(x) - 1) >> 3) : 4u;
-                    if (eq > matchlimit - 4 * wz) eq = matchlimit - 4 * wz;
-                    len += eq;
-                }
-                const uint32_t mp = 4 * w;
                 if (lane == n) {
                     my_anchor = pos;
                     my_mp = mp;

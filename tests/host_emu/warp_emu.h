@@ -25,6 +25,7 @@ template <class T> inline T __shfl_down_sync(uint32_t, T x, unsigned d) { static
 template <class T> inline T __shfl_xor_sync(uint32_t, T x, int m) { uint64_t u = 0; memcpy(&u,&x,sizeof(T)); static thread_local int dummy; (void)dummy; uint64_t *v64 = reinterpret_cast<uint64_t *>(g_warp->v64); v64[threadIdx.x] = u; g_warp->bar.arrive_and_wait(); uint64_t r = v64[threadIdx.x ^ m]; g_warp->bar.arrive_and_wait(); T o; memcpy(&o,&r,sizeof(T)); return o; }
 inline uint32_t __match_any_sync(uint32_t, uint32_t x) { g_warp->v[threadIdx.x] = x; g_warp->bar.arrive_and_wait(); uint32_t r = 0; for (int i = 0; i < 32; i++) if (g_warp->v[i] == x) r |= 1u << i; g_warp->bar.arrive_and_wait(); return r; }
 inline int __ffs(uint32_t x) { return x ? __builtin_ctz(x) + 1 : 0; }
+inline int __popc(uint32_t x) { return __builtin_popcount(x); }
 inline int __clz(uint32_t x) { return x ? __builtin_clz(x) : 32; }
 inline uint32_t atomicMax(uint32_t* p, uint32_t v) { std::lock_guard<std::mutex> g(g_warp->mu); uint32_t o = *p; if (v > o) *p = v; return o; }
 inline void __nanosleep(unsigned) {}
