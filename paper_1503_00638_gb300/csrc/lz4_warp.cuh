@@ -886,17 +886,30 @@ BSG_D void lz4_match_copy(uint8_t *dst, uint32_t op, uint32_t off, uint32_t ML, 
 // end).  Returns 0, or a nonzero code for: input ending early (1), a literal
 // run overrunning the output (2), a bad offset or match length, or a match
 // breaking the end-of-block rules (3), a final length other than S (6).
+// The token and the offset are each read together with the byte after them
+// (one funnel-shifted word), so a length of 15..269 costs no extra read.
 BSG_D int lz4_decode_warp(const uint8_t *src, uint32_t ip0, uint32_t clen, uint8_t *dst,
                           uint32_t S)
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t end = ip0 + clen;
     uint32_t ip = ip0, op = 0;
-    for (uint32_t guard = 0; guard <= clen; guard++) {
+    // every pass consumes at least its token byte, so the loop ends
+    while (true) {
         if (ip >= end) return 1;
-        const uint32_t token = src[ip++];
+        const uint32_t t4 = ld32u(src, ip);
+        const uint32_t token = t4 & 255u;
         uint32_t LL = token >> 4;
-        if (LL == 15 && !lz4_read_len(src, end, ip, LL, lane)) return 1;
+        ip += 1;
+        if (LL == 15u) {
+            const uint32_t b = (t4 >> 8) & 255u;
+            if (b != 255u && ip < end) {
+                LL += b;
+                ip += 1;
+            } else if (!lz4_read_len(src, end, ip, LL, lane)) {
+                return 1;
+            }
+        }
         if (LL > end - ip) return 1;
         if (LL > S - op) return 2;
         warp_copy_ordered(dst, op, src, ip, LL, lane);
@@ -904,13 +917,22 @@ BSG_D int lz4_decode_warp(const uint8_t *src, uint32_t ip0, uint32_t clen, uint8
         op += LL;
         if (ip == end) break;
         if (end - ip < 2) return 1;
-        const uint32_t off = (uint32_t)src[ip] | ((uint32_t)src[ip + 1] << 8);
+        const uint32_t o4 = ld32u(src, ip);
+        const uint32_t off = o4 & 0xffffu;
         ip += 2;
         uint32_t ML = token & 15u;
-        if (ML == 15 && !lz4_read_len(src, end, ip, ML, lane)) return 1;
+        if (ML == 15u) {
+            const uint32_t b = (o4 >> 16) & 255u;
+            if (b != 255u && ip < end) {
+                ML += b;
+                ip += 1;
+            } else if (!lz4_read_len(src, end, ip, ML, lane)) {
+                return 1;
+            }
+        }
         ML += LZ4_MINMATCH;
-        if (off == 0 || off > op || ML > S - op || op + LZ4_MFLIMIT > S ||
-            op + ML + LZ4_LASTLITERALS > S)
+        // (ML is below 2^31: at most 255 per stream byte)
+        if ((off == 0) | (off > op) | (ML + LZ4_LASTLITERALS > S - op) | (op + LZ4_MFLIMIT > S))
             return 3;
         __syncwarp();
         lz4_match_copy(dst, op, off, ML, lane);
