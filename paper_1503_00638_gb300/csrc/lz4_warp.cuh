@@ -81,10 +81,14 @@ BSG_D void warp_copy(uint8_t *dst, uint32_t d, const uint8_t *src, uint32_t s, u
 }
 
 // Copy of up to 32 independent byte ranges, range k (k < n) held by lane k as
-// (source offset a, destination offset d, length len): four ranges at a time,
-// eight lanes each (head bytes up to dst's word boundary, whole words from
-// funnel-shifted loads, ragged end), so that short runs do not each cost a
-// whole-warp pass.  The ranges must not overlap each other or the sources.
+// (source offset a, destination offset d, length len).  Ranges of at most
+// LZ4_RANGE_SHORT bytes go four at a time, eight lanes each (head bytes up to
+// dst's word boundary, whole words from funnel-shifted loads, ragged end), so
+// that short runs do not each cost a whole-warp pass; longer ones go one
+// after another with the whole warp, so that a long run does not keep 24
+// lanes idle.  The ranges must not overlap each other or the sources.
+constexpr uint32_t LZ4_RANGE_SHORT = 64;
+
 BSG_D void warp_copy_ranges(uint8_t *dst, const uint8_t *src, uint32_t n, uint32_t a, uint32_t d,
                             uint32_t len, uint32_t lane)
 {
@@ -98,7 +102,7 @@ BSG_D void warp_copy_ranges(uint8_t *dst, const uint8_t *src, uint32_t n, uint32
         const uint32_t k = base + g;
         const uint32_t ak = __shfl_sync(FULL, a, k & 31u), dk = __shfl_sync(FULL, d, k & 31u);
         const uint32_t lk0 = __shfl_sync(FULL, len, k & 31u);
-        const uint32_t lk = k < n ? lk0 : 0u;
+        const uint32_t lk = k < n && lk0 <= LZ4_RANGE_SHORT ? lk0 : 0u;
         if (lk == 0) continue;
         if (lk <= 8) {
             if (sl < lk) dst[dk + sl] = src[ak + sl];
@@ -109,6 +113,19 @@ BSG_D void warp_copy_ranges(uint8_t *dst, const uint8_t *src, uint32_t n, uint32
         if (sl < head) dst[dk + sl] = src[ak + sl];
         if (sl >= 4 && sl - 4 < tail) dst[a1 + sl - 4] = src[ak + (a1 - dk) + sl - 4];
         for (uint32_t w = (a0 >> 2) + sl; w < (a1 >> 2); w += 8) d32[w] = ld32u(src, ak + 4 * w - dk);
+    }
+    uint32_t longs = __ballot_sync(FULL, lane < n && len > LZ4_RANGE_SHORT);
+    while (longs) {
+        const uint32_t k = (uint32_t)(__ffs(longs) - 1);
+        longs &= longs - 1;
+        const uint32_t ak = __shfl_sync(FULL, a, k), dk = __shfl_sync(FULL, d, k);
+        const uint32_t lk = __shfl_sync(FULL, len, k);
+        const uint32_t a0 = (dk + 3u) & ~3u, a1 = (dk + lk) & ~3u;
+        const uint32_t head = a0 - dk, tail = dk + lk - a1;
+        if (lane < head) dst[dk + lane] = src[ak + lane];
+        if (lane >= 4 && lane - 4 < tail) dst[a1 + lane - 4] = src[ak + (a1 - dk) + lane - 4];
+        const uint32_t q = ak - dk;  // source byte of destination byte 0 (mod 2^32)
+        for (uint32_t w = (a0 >> 2) + lane; w < (a1 >> 2); w += 32) d32[w] = ld32u(src, q + 4 * w);
     }
 }
 
