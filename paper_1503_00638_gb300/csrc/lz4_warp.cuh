@@ -742,26 +742,57 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
             }
             __syncwarp();
         }
-        uint32_t rec = graph ? node[N] : 0u;
+        static_assert(4 * LZ4_NODE_CAP <= 2 * 64 * 4, "jump tables in the run-end bitmaps");
+        uint8_t *jmp = reinterpret_cast<uint8_t *>(sCEr);
+        if (graph) {
+            // jump tables: jmp[b * LZ4_NODE_CAP + x] = the node 2^(b + 1)
+            // steps after node x (255: past the end), in the space of the
+            // run-end bitmaps, which the graph parse no longer reads
+            for (uint32_t x = lane; x <= N; x += 32) {
+                const uint32_t y = node[x] >> 24;
+                jmp[x] = (uint8_t)(y == 255u ? 255u : node[y] >> 24);
+            }
+            __syncwarp();
+#pragma unroll
+            for (uint32_t b = 1; b < 4; b++) {
+                const uint8_t *jp = jmp + (b - 1) * LZ4_NODE_CAP;
+                for (uint32_t x = lane; x <= N; x += 32) {
+                    const uint32_t y = jp[x];
+                    jmp[b * LZ4_NODE_CAP + x] = (uint8_t)(y == 255u ? 255u : jp[y]);
+                }
+                __syncwarp();
+            }
+        }
+        uint32_t x0 = N;  // graph: the node the next 32 sequences start from
         uint32_t pos = 0;
         bool more = true;
         for (uint32_t guard = 0; more && guard <= NW; guard++) {
-            // parse up to 32 sequences; lane k keeps the k-th
+            // up to 32 sequences; lane k keeps the k-th
             uint32_t my_anchor = 0, my_mp = 0, my_len = 0, my_off = 0, n = 0;
-            for (; n < 32; n++) {
-                uint32_t mp, len, off;
-                if (graph) {
-                    const uint32_t nx = rec >> 24;
-                    if (nx == 255u) {
-                        more = false;
-                        break;
-                    }
+            if (graph) {
+                // lane k: the node k steps after x0 (the start of its
+                // sequence) and the node after that (its end)
+                uint32_t x = x0;
+                if (lane & 1u) x = node[x] >> 24;
+#pragma unroll
+                for (uint32_t b = 0; b < 4; b++)
+                    if (((lane >> (b + 1)) & 1u) && x != 255u) x = jmp[b * LZ4_NODE_CAP + x];
+                const uint32_t rec = x != 255u ? node[x] : 0u;
+                const uint32_t nx = x != 255u ? rec >> 24 : 255u;
+                if (nx != 255u) {
                     const uint32_t nrec = node[nx];
-                    mp = 4 * ((rec >> 13) & 2047u);
-                    len = (nrec & 8191u) - mp;
-                    off = nx < Nr ? rowlen : 4u;
-                    rec = nrec;
-                } else {
+                    my_anchor = rec & 8191u;
+                    my_mp = 4 * ((rec >> 13) & 2047u);
+                    my_len = (nrec & 8191u) - my_mp;
+                    my_off = nx < Nr ? rowlen : 4u;
+                }
+                n = (uint32_t)__popc(__ballot_sync(FULL, nx != 255u));
+                if (n) pos = __shfl_sync(FULL, my_mp + my_len, n - 1);
+                x0 = __shfl_sync(FULL, nx, 31);
+                more = n == 32 && x0 != 255u;
+            } else {
+                for (; n < 32; n++) {
+                    uint32_t mp, len, off;
                     const uint32_t w = smap_first_set(sCany, nCany, (pos + 3) / 4, wlim);
                     if (w == ~0u) {
                         more = false;
@@ -784,14 +815,14 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
                         if (eq > matchlimit - 4 * e) eq = matchlimit - 4 * e;
                         len += eq;
                     }
+                    if (lane == n) {
+                        my_anchor = pos;
+                        my_mp = mp;
+                        my_len = len;
+                        my_off = off;
+                    }
+                    pos = mp + len;  // the backward extension below leaves the match end alone
                 }
-                if (lane == n) {
-                    my_anchor = pos;
-                    my_mp = mp;
-                    my_len = len;
-                    my_off = off;
-                }
-                pos = mp + len;  // the backward extension below leaves the match end alone
             }
             // each lane backs its match up over up to 3 equal bytes (never
             // before its literal anchor), off the parse's critical path
