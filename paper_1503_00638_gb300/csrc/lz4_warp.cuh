@@ -612,9 +612,11 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
     const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
     const uint32_t NW = S / 4, NB = NW / 32;
     const uint32_t R = (rowlen & 3u) ? 0u : rowlen / 4;
-    // equality bitmaps: bit w of Erow (Erun) set when word w equals word w - R (w - 1)
+    // equality bitmaps: bit w of Erow (Erun) set when word w equals word w - R (w - 1).
+    // Both neighbours are read from shared memory; words without one (w < R,
+    // w = 0) read some word of the block instead and have their bits cleared
+    // after the loop.
     uint32_t Erow[2] = {0u, 0u}, Erun[2] = {0u, 0u};
-    uint32_t prev_last = ~s32[0];  // last word of the previous 32 (none before word 0)
 #pragma unroll
     for (uint32_t j = 0; j < 2; j++) {
         const uint32_t kend = NB < 32 * (j + 1) ? (NB > 32 * j ? NB - 32 * j : 0u) : 32u;
@@ -622,18 +624,23 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
         for (uint32_t kk = 0; kk < kend; kk++) {
             const uint32_t w = 32 * (32 * j + kk) + lane;
             const uint32_t x = s32[w];
-            uint32_t xp = __shfl_up_sync(FULL, x, 1);
-            if (lane == 0) xp = prev_last;
-            prev_last = __shfl_sync(FULL, x, 31);
-            const bool rowok = w >= R && R != 0;
-            const uint32_t xr = s32[rowok ? w - R : w];
-            const uint32_t row = __ballot_sync(FULL, rowok && x == xr);
+            const uint32_t xp = s32[w > 0 ? w - 1 : 0u];
+            const uint32_t xr = s32[w > R ? w - R : 0u];
+            const uint32_t row = __ballot_sync(FULL, x == xr);
             const uint32_t run = __ballot_sync(FULL, x == xp);
             if (lane == kk) {
                 Erow[j] = row;
                 Erun[j] = run;
             }
         }
+    }
+    // no word before word 0, no bit-row before words 0 .. R - 1 (none at all for R = 0)
+    if (lane == 0) Erun[0] &= ~1u;
+#pragma unroll
+    for (uint32_t j = 0; j < 2; j++) {
+        const uint32_t k0 = 32 * (lane + 32 * j);  // first word of bitmap word lane + 32 j
+        if (R == 0 || k0 + 32 <= R) Erow[j] = 0u;
+        else if (k0 < R) Erow[j] &= ~0u << (R - k0);
     }
     // candidate bitmaps: bits w .. w + LZ4_L0_MINWORDS - 1 all set (LZ4_L0_MINMATCH
     // equal bytes)
