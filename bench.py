@@ -78,6 +78,10 @@ def parse():
                    help="shuffle workload: leave out the codec-only size x block grid")
     p.add_argument("--no-sub", action="store_true",
                    help="leave the batch and serving records out of the default run's line")
+    p.add_argument("--batch-fixed", default="",
+                   help="BLOCK_BYTES:WxC -- the batch workload with this one block size and "
+                        "launch shape (W warps per CTA, C CTAs per SM, 0 = as many as fit) "
+                        "instead of the autotuner's choice; for profiling one launch shape")
     return p.parse_args()
 
 
@@ -382,10 +386,19 @@ def run_batch(args, rank, world, local, barrier, gpu_index, chunks=None, steps=N
     xs, raw = batch_inputs(specs, rank, keep_raw=True)
     es_l = [es for _, es, _ in specs]
     nbytes = sum(nb for nb, _, _ in specs)
-    # the autotuner: block size x warps per CTA x CTAs per SM, each launch
-    # tuned on its own (one codec at a time, so that a 40 GB batch fits)
-    block_bytes, tune_table, _ = engine.tune(xs, es_l, BATCH_BLOCK_CANDIDATES, level=LEVEL,
-                                             reps=2, keep=False)
+    if args.batch_fixed:
+        # one given launch, no tuning (profiles of a single launch shape)
+        fb, fs = args.batch_fixed.split(":")
+        fw, fc = (int(v) for v in fs.split("x"))
+        block_bytes = int(fb)
+        shape = {"warps_per_cta": fw, "ctas_per_sm": fc}
+        tune_table = {block_bytes: {"compress": dict(shape), "decompress": dict(shape),
+                                    "note": "fixed by --batch-fixed, not tuned"}}
+    else:
+        # the autotuner: block size x warps per CTA x CTAs per SM, each launch
+        # tuned on its own (one codec at a time, so that a 40 GB batch fits)
+        block_bytes, tune_table, _ = engine.tune(xs, es_l, BATCH_BLOCK_CANDIDATES, level=LEVEL,
+                                                 reps=2, keep=False)
     torch.cuda.empty_cache()
     bl = [block_bytes // es for es in es_l]
     eng = engine.BatchCodec(xs, es_l, bl, level=LEVEL)
