@@ -154,14 +154,25 @@ BSG_D void batch_prepare(const BatchChunk &ch, uint32_t tile, uint32_t Bb, uint8
 // Exclusive prefix of block `tile` of chunk c by look-back, then its
 // placement (index entry, chunk header, verbatim tail, stream length); the
 // staging slot's lines are then dropped from L2.
-BSG_D void batch_place(const BatchArgs &b, uint32_t c, uint32_t tile, const uint8_t *blk,
-                       uint32_t cs, uint32_t lane)
+BSG_D void batch_place(const BatchArgs &b, uint32_t c, uint32_t tile, const uint8_t *slot,
+                       uint32_t cs, uint8_t *buf, uint64_t *bar, uint32_t &parity, uint32_t lane)
 {
     const CodecArgs a = chunk_args(b, c);
-    const uint64_t excl = lookback_resolve(a.tile_state, tile, 4ull + cs, a.status, lane);
-    compress_place(a, tile, blk, cs, 12 + excl, lane);
+    // the staged bytes come back into the warp's free block buffer by one
+    // bulk copy while the look-back finds the block's offset
+    const uint32_t bytes = r16(4 + cs);
+    fence_proxy_async_all();
     __syncwarp();
-    discard_slot(blk, 4 + cs, lane);
+    if (lane == 0) {
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(buf, slot, bytes, bar);
+    }
+    const uint64_t excl = lookback_resolve(a.tile_state, tile, 4ull + cs, a.status, lane);
+    if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);
+    parity ^= 1u;
+    compress_place(a, tile, buf, cs, 12 + excl, lane);
+    __syncwarp();
+    discard_slot(slot, 4 + cs, lane);
 }
 
 // Shared memory of one warp of the batch kernels, rounded up so that the
@@ -183,6 +194,9 @@ template <int LEVEL, int W>
 __global__ void __launch_bounds__(32 * W, 20 / W) compress_batch_kernel(const __grid_constant__ BatchArgs b)
 {
     using L = FastPlan<LEVEL>;
+    // a staged block comes back into the buffer and the encoder's scratch
+    // after it (both free by then) for its placement
+    static_assert(L::TMP + L::SCR >= r16(4 + lz4b(L::MAXB)), "placement buffer");
     extern __shared__ __align__(128) uint8_t smem_all[];
     const uint32_t warp = W == 1 ? 0u : threadIdx.x >> 5;
     uint8_t *sm = smem_all + (size_t)warp * batch_compress_warp_smem<LEVEL>();
@@ -231,7 +245,7 @@ __global__ void __launch_bounds__(32 * W, 20 / W) compress_batch_kernel(const __
             lookback_publish(b.state + ch.item0, tile, 4ull + cs, lane);
         }
         const uint32_t nxt = grab_tile(b.counter, lane);
-        if (ptile != ~0u) batch_place(b, pchunk, ptile, slot1, pcs, lane);
+        if (ptile != ~0u) batch_place(b, pchunk, ptile, slot1, pcs, tmp, bar, parity, lane);
         __syncwarp();
         if (nb != 0) {
             ptile = tile;
@@ -248,7 +262,7 @@ __global__ void __launch_bounds__(32 * W, 20 / W) compress_batch_kernel(const __
         fence_proxy_async_smem();
         __syncwarp();
     }
-    if (ptile != ~0u) batch_place(b, pchunk, ptile, slot1, pcs, lane);
+    if (ptile != ~0u) batch_place(b, pchunk, ptile, slot1, pcs, tmp, bar, parity, lane);
 }
 
 // Header of a chunk's stream (checked with its first item).
