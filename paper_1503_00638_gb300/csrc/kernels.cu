@@ -13,17 +13,21 @@ uint32_t compress_smem_bytes(uint32_t maxb, int level)
 {
     if (level >= 1)
         return maxb <= 8192 ? CompPlan<8192, 1>::BYTES
-                            : (maxb <= 16384 ? CompPlan<16384, 1>::BYTES : CompPlan<65536, 1>::BYTES);
+             : maxb <= 16384 ? CompPlan<16384, 1>::BYTES
+             : maxb <= 32768 ? CompPlan<32768, 1>::BYTES : CompPlan<65536, 1>::BYTES;
     return maxb <= 8192 ? CompPlan<8192, 0>::BYTES
-                        : (maxb <= 16384 ? CompPlan<16384, 0>::BYTES : CompPlan<65536, 0>::BYTES);
+         : maxb <= 16384 ? CompPlan<16384, 0>::BYTES
+         : maxb <= 32768 ? CompPlan<32768, 0>::BYTES : CompPlan<65536, 0>::BYTES;
 }
 uint32_t decompress_smem_bytes(uint32_t maxb)
 {
     return maxb <= 8192 ? DecPlan<8192>::BYTES
-                        : (maxb <= 16384 ? DecPlan<16384>::BYTES : DecPlan<65536>::BYTES);
+         : maxb <= 16384 ? DecPlan<16384>::BYTES
+         : maxb <= 32768 ? DecPlan<32768>::BYTES : DecPlan<65536>::BYTES;
 }
 uint32_t shuffle_smem_bytes(uint32_t maxb)
 {
+    // (blocks over 16 KiB share the largest plan)
     return maxb <= 8192 ? ShufPlan<8192>::BYTES
                         : (maxb <= 16384 ? ShufPlan<16384>::BYTES : ShufPlan<65536>::BYTES);
 }
@@ -1306,10 +1310,12 @@ cudaError_t launch_compress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cu
     if (a.level >= 1) {
         if (maxb <= 8192) return launch_warp_kernel(compress_kernel<8192, 1>, smem, grid, s, a);
         if (maxb <= 16384) return launch_warp_kernel(compress_kernel<16384, 1>, smem, grid, s, a);
+        if (maxb <= 32768) return launch_warp_kernel(compress_kernel<32768, 1>, smem, grid, s, a);
         return launch_warp_kernel(compress_kernel<65536, 1>, smem, grid, s, a);
     }
     if (maxb <= 8192) return launch_warp_kernel(compress_kernel<8192, 0>, smem, grid, s, a);
     if (maxb <= 16384) return launch_warp_kernel(compress_kernel<16384, 0>, smem, grid, s, a);
+    if (maxb <= 32768) return launch_warp_kernel(compress_kernel<32768, 0>, smem, grid, s, a);
     return launch_warp_kernel(compress_kernel<65536, 0>, smem, grid, s, a);
 }
 
@@ -1355,6 +1361,7 @@ cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, 
         return launch_warp_kernel(decompress_kernel<8192, 0>, smem, grid, s, a);
     }
     if (maxb <= 16384) return launch_warp_kernel(decompress_kernel<16384, 0>, smem, grid, s, a);
+    if (maxb <= 32768) return launch_warp_kernel(decompress_kernel<32768, 0>, smem, grid, s, a);
     return launch_warp_kernel(decompress_kernel<65536, 0>, smem, grid, s, a);
 }
 

@@ -124,7 +124,7 @@ cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, void *seg_w
 // Block-size class: the smallest supported shared-memory plan for `bytes`.
 inline uint32_t maxb_class(uint32_t bytes)
 {
-    return bytes <= 8192 ? 8192u : (bytes <= 16384 ? 16384u : 65536u);
+    return bytes <= 8192 ? 8192u : (bytes <= 16384 ? 16384u : (bytes <= 32768 ? 32768u : 65536u));
 }
 
 }  // namespace bsg
