@@ -88,8 +88,13 @@ uint32_t persistent_grid(uint32_t smem_per_cta, uint64_t work)
 }
 
 struct WsLayout {
-    size_t state, autos, pairs, cft, qtab, offsets, segs, slots, total;
+    size_t state, autos, pairs, cft, qtab, offsets, segs, slots, gslots, total;
+    uint32_t gslot_warps;  // warps the general compressor's slots cover
 };
+
+// SMs the general compressor's staging slots are sized for (at least the
+// device's count; GB300 has 152)
+constexpr uint32_t GEN_MAX_SMS = 160;
 
 // What the flags of the visibility entry points add to the workspace.
 struct VisOpts {
@@ -130,6 +135,21 @@ WsLayout ws_layout(int op, const Geometry &g, size_t n_auto, size_t n_prod, uint
         if (g.nb && fast_shape(g)) {
             L.slots = o;
             o += (size_t)FAST_MAX_WARPS * 2 * FAST_SLOT_BYTES;
+        }
+        // the general compressor's staging slots: for its one shortened last
+        // block after the fast path, else for as many warps as can be
+        // resident (at most GEN_MAX_SMS SMs)
+        const uint32_t gwork = !g.nb ? 0u : fast_shape(g) ? (g.last_B != g.B ? 1u : 0u) : g.nb;
+        if (gwork) {
+            const uint32_t maxb = maxb_class(g.B * g.es);
+            const uint32_t smem = compress_smem_bytes(maxb, 0, true);
+            uint32_t per_sm = (228u * 1024u) / (smem + 1024u);
+            if (per_sm == 0) per_sm = 1;
+            uint64_t w = (uint64_t)GEN_MAX_SMS * per_sm;
+            if (w > gwork) w = gwork;
+            L.gslots = o;
+            L.gslot_warps = (uint32_t)w;
+            o += r256((size_t)w * 2 * compress_slot_bytes(maxb));
         }
     }
     if (op == BSGPU_OP_COMPRESS_VIS || op == BSGPU_OP_REDUCE_PRECISION) {
@@ -465,7 +485,10 @@ static int compress_common(const void *in, const Geometry &g, int level, void *o
     a.tile_end = g.nb;
     a.tile_counter = reinterpret_cast<uint32_t *>((uint8_t *)ws + 8);
     uint32_t maxb = maxb_class(g.B * g.es);
-    uint32_t grid = persistent_grid(compress_smem_bytes(maxb, level), g.nb - done);
+    a.slots = L.gslots ? reinterpret_cast<uint8_t *>(ws) + L.gslots : nullptr;
+    a.nslot_warps = L.gslot_warps;
+    uint32_t grid = persistent_grid(compress_smem_bytes(maxb, level, a.slots != nullptr), g.nb - done);
+    if (a.slots && grid > a.nslot_warps) grid = a.nslot_warps;
     return cuda_err(launch_compress(a, maxb, grid, s));
 }
 

@@ -33,6 +33,12 @@ struct CompPlan {
     static constexpr int HBITS = MAXB <= 8192 ? 11 : (MAXB <= 16384 ? 12 : 13);
     static constexpr uint32_t SCR = LEVEL >= 1 ? (2u << HBITS) : 2u * 4u * (MAXB / 128u + 2u);
     static constexpr uint32_t BYTES = IN + TMP + OUT + r16(SCR) + 16;
+    // staged: the LZ4 output goes to a staging slot in global memory and the
+    // block is placed one block later, coming back into `tmp` and the scratch
+    // after it (so no output buffer; two barriers)
+    static constexpr uint32_t SLOT = r16(4 + lz4b(MAXB) + 32);
+    static constexpr uint32_t BYTES_STAGED = IN + TMP + r16(SCR) + 32;
+    static_assert(TMP + SCR >= r16(4 + lz4b(MAXB)), "placement buffer");
 };
 
 template <uint32_t MAXB>
@@ -561,6 +567,26 @@ BSG_D uint32_t compress_encode(const CodecArgs &a, uint32_t Bb, const uint8_t *t
     if (lane == 0) put_be32(dst, cs);
     __syncwarp();
     return cs;
+}
+
+// Place block `ptile`, staged in global `slot` (4 + cs bytes): the bytes come
+// back into the warp's block buffer `buf` (free until the next block's load,
+// with the encoder's scratch after it) by one bulk copy that runs while the
+// look-back finds the block's offset, and go out from there.
+BSG_D void place_staged(const CodecArgs &a, uint32_t ptile, const uint8_t *slot, uint32_t cs,
+                        uint8_t *buf, uint64_t *bar, uint32_t &parity, uint32_t lane)
+{
+    const uint32_t bytes = r16(4 + cs);
+    fence_proxy_async_all();  // the slot was written by this warp's generic stores
+    __syncwarp();
+    if (lane == 0) {
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(buf, slot, bytes, bar);
+    }
+    const uint64_t excl = lookback_resolve(a.tile_state, ptile, 4ull + cs, a.status, lane);
+    if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);
+    parity ^= 1u;
+    compress_place(a, ptile, buf, cs, 12 + excl, lane);
 }
 
 // LZ4-encode the bit-rows in `tmp` into `out`, place the block by look-back

@@ -18,26 +18,6 @@ namespace bsg {
 // round_group_full).  PS (a cube whose time axis is not a multiple of 16, so
 // 16-sample groups would straddle products): the samples are rounded one by
 // one before the plain transpose, and with TS gathered one by one.
-// Place block `ptile`, staged in global `slot` (4 + cs bytes): the bytes come
-// back into the warp's block buffer `buf` (free until the next block's load,
-// with the encoder's scratch after it) by one bulk copy that runs while the
-// look-back finds the block's offset, and go out from there.
-BSG_D void place_staged(const CodecArgs &a, uint32_t ptile, const uint8_t *slot, uint32_t cs,
-                        uint8_t *buf, uint64_t *bar, uint32_t &parity, uint32_t lane)
-{
-    const uint32_t bytes = r16(4 + cs);
-    fence_proxy_async_all();  // the slot was written by this warp's generic stores
-    __syncwarp();
-    if (lane == 0) {
-        mbar_arrive_expect_tx(bar, bytes);
-        bulk_g2s(buf, slot, bytes, bar);
-    }
-    const uint64_t excl = lookback_resolve(a.tile_state, ptile, 4ull + cs, a.status, lane);
-    if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);
-    parity ^= 1u;
-    compress_place(a, ptile, buf, cs, 12 + excl, lane);
-}
-
 template <int LEVEL, int ES, bool GEN = false, bool TS = false, bool PS = false>
 __global__ void __launch_bounds__(32, 20) compress_fast_kernel(const __grid_constant__ CodecArgs a)
 {

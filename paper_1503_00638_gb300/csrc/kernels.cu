@@ -9,15 +9,26 @@
 
 namespace bsg {
 
-uint32_t compress_smem_bytes(uint32_t maxb, int level)
+template <uint32_t MAXB, int LEVEL>
+constexpr uint32_t comp_plan_bytes(bool staged)
+{
+    return staged ? CompPlan<MAXB, LEVEL>::BYTES_STAGED : CompPlan<MAXB, LEVEL>::BYTES;
+}
+uint32_t compress_smem_bytes(uint32_t maxb, int level, bool staged)
 {
     if (level >= 1)
-        return maxb <= 8192 ? CompPlan<8192, 1>::BYTES
-             : maxb <= 16384 ? CompPlan<16384, 1>::BYTES
-             : maxb <= 32768 ? CompPlan<32768, 1>::BYTES : CompPlan<65536, 1>::BYTES;
-    return maxb <= 8192 ? CompPlan<8192, 0>::BYTES
-         : maxb <= 16384 ? CompPlan<16384, 0>::BYTES
-         : maxb <= 32768 ? CompPlan<32768, 0>::BYTES : CompPlan<65536, 0>::BYTES;
+        return maxb <= 8192 ? comp_plan_bytes<8192, 1>(staged)
+             : maxb <= 16384 ? comp_plan_bytes<16384, 1>(staged)
+             : maxb <= 32768 ? comp_plan_bytes<32768, 1>(staged) : comp_plan_bytes<65536, 1>(staged);
+    return maxb <= 8192 ? comp_plan_bytes<8192, 0>(staged)
+         : maxb <= 16384 ? comp_plan_bytes<16384, 0>(staged)
+         : maxb <= 32768 ? comp_plan_bytes<32768, 0>(staged) : comp_plan_bytes<65536, 0>(staged);
+}
+uint32_t compress_slot_bytes(uint32_t maxb)
+{
+    return maxb <= 8192 ? CompPlan<8192, 0>::SLOT
+         : maxb <= 16384 ? CompPlan<16384, 0>::SLOT
+         : maxb <= 32768 ? CompPlan<32768, 0>::SLOT : CompPlan<65536, 0>::SLOT;
 }
 uint32_t decompress_smem_bytes(uint32_t maxb)
 {
@@ -370,9 +381,12 @@ __global__ void __launch_bounds__(256) reduce_precision_kernel(const uint2 *__re
 
 // One warp per CTA, persistent.  Per block: wait for its bulk copy into `in`,
 // round + transpose into `tmp`, start the next block's copy into `in`, then
-// LZ4 into `out`, look-back placement and the write-out, which overlap the
-// next block's copy.
-template <uint32_t MAXB, int LEVEL>
+// LZ4.  STAGED (the workspace holds two staging slots per warp): the block
+// is encoded into a slot in global memory, its size published, and the
+// PREVIOUS block placed, as the fast kernel does, so that the look-back
+// rarely waits and no output buffer is needed; otherwise the block is
+// encoded into `out`, placed by look-back and written out at once.
+template <uint32_t MAXB, int LEVEL, bool STAGED>
 __global__ void __launch_bounds__(32, MAXB <= 8192 ? 9 : 1)
     compress_kernel(const __grid_constant__ CodecArgs a)
 {
@@ -380,16 +394,21 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 9 : 1)
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t *in = sm;
     uint8_t *tmp = sm + L::IN;
-    uint8_t *out = tmp + L::TMP;
-    void *scratch = out + L::OUT;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(out + L::OUT + r16(L::SCR));
+    uint8_t *out = tmp + L::TMP;  // not STAGED
+    void *scratch = STAGED ? static_cast<void *>(tmp + L::TMP) : static_cast<void *>(out + L::OUT);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(scratch) + r16(L::SCR));
+    uint64_t *bar2 = bar + 1;  // STAGED: the placement copies
     const uint32_t lane = threadIdx.x & 31u;
     if (lane == 0) {
         mbar_init(bar, 1);
+        if (STAGED) mbar_init(bar2, 1);
         fence_mbar_init();
     }
     __syncwarp();
-    uint32_t parity = 0;
+    uint8_t *slot0 = STAGED ? a.slots + (size_t)(2 * blockIdx.x) * L::SLOT : nullptr;
+    uint8_t *slot1 = STAGED ? slot0 + L::SLOT : nullptr;
+    uint32_t parity = 0, parity2 = 0;
+    uint32_t ptile = ~0u, pcs = 0;  // STAGED: the block waiting to be placed, in slot1
     uint32_t tile = a.tile_begin + grab_tile(a.tile_counter, lane);
     bool pend = tile < a.tile_end && load_block_any(a, in, tile, bar, lane);
     while (tile < a.tile_end) {
@@ -407,10 +426,23 @@ __global__ void __launch_bounds__(32, MAXB <= 8192 ? 9 : 1)
             __syncwarp();
             pend = load_block_any(a, in, nxt, bar, lane);
         }
-        compress_finish<MAXB, LEVEL>(a, tile, tmp, out, scratch, lane);
+        if (STAGED) {
+            const uint32_t cs =
+                compress_encode<LEVEL, L::HBITS>(a, block_elems_of(a, tile), tmp, slot0, scratch, lane);
+            lookback_publish(a.tile_state, tile, 4ull + cs, lane);
+            if (ptile != ~0u) place_staged(a, ptile, slot1, pcs, tmp, bar2, parity2, lane);
+            ptile = tile;
+            pcs = cs;
+            uint8_t *t = slot0;
+            slot0 = slot1;
+            slot1 = t;
+        } else {
+            compress_finish<MAXB, LEVEL>(a, tile, tmp, out, scratch, lane);
+        }
         __syncwarp();
         tile = nxt;
     }
+    if (STAGED && ptile != ~0u) place_staged(a, ptile, slot1, pcs, tmp, bar2, parity2, lane);
 }
 
 
@@ -1304,19 +1336,25 @@ cudaError_t launch_shuffle(const CodecArgs &a_in, bool inverse, uint32_t maxb, u
                    : launch_warp_kernel(shuffle_kernel<65536, false>, smem, grid, s, a);
 }
 
+template <bool STAGED>
+cudaError_t launch_compress_t(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s)
+{
+    const uint32_t smem = compress_smem_bytes(maxb, a.level, STAGED);
+    if (a.level >= 1) {
+        if (maxb <= 8192) return launch_warp_kernel(compress_kernel<8192, 1, STAGED>, smem, grid, s, a);
+        if (maxb <= 16384) return launch_warp_kernel(compress_kernel<16384, 1, STAGED>, smem, grid, s, a);
+        if (maxb <= 32768) return launch_warp_kernel(compress_kernel<32768, 1, STAGED>, smem, grid, s, a);
+        return launch_warp_kernel(compress_kernel<65536, 1, STAGED>, smem, grid, s, a);
+    }
+    if (maxb <= 8192) return launch_warp_kernel(compress_kernel<8192, 0, STAGED>, smem, grid, s, a);
+    if (maxb <= 16384) return launch_warp_kernel(compress_kernel<16384, 0, STAGED>, smem, grid, s, a);
+    if (maxb <= 32768) return launch_warp_kernel(compress_kernel<32768, 0, STAGED>, smem, grid, s, a);
+    return launch_warp_kernel(compress_kernel<65536, 0, STAGED>, smem, grid, s, a);
+}
+
 cudaError_t launch_compress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s)
 {
-    uint32_t smem = compress_smem_bytes(maxb, a.level);
-    if (a.level >= 1) {
-        if (maxb <= 8192) return launch_warp_kernel(compress_kernel<8192, 1>, smem, grid, s, a);
-        if (maxb <= 16384) return launch_warp_kernel(compress_kernel<16384, 1>, smem, grid, s, a);
-        if (maxb <= 32768) return launch_warp_kernel(compress_kernel<32768, 1>, smem, grid, s, a);
-        return launch_warp_kernel(compress_kernel<65536, 1>, smem, grid, s, a);
-    }
-    if (maxb <= 8192) return launch_warp_kernel(compress_kernel<8192, 0>, smem, grid, s, a);
-    if (maxb <= 16384) return launch_warp_kernel(compress_kernel<16384, 0>, smem, grid, s, a);
-    if (maxb <= 32768) return launch_warp_kernel(compress_kernel<32768, 0>, smem, grid, s, a);
-    return launch_warp_kernel(compress_kernel<65536, 0>, smem, grid, s, a);
+    return a.slots ? launch_compress_t<true>(a, maxb, grid, s) : launch_compress_t<false>(a, maxb, grid, s);
 }
 
 cudaError_t launch_compress_fast(const CodecArgs &a, uint32_t grid, cudaStream_t s)

@@ -67,13 +67,16 @@ struct CodecArgs {
     int level;               // compress: LZ4 search level (0 structural, 1 + hash)
     uint32_t tile_begin;     // compress: tiles [tile_begin, tile_end) of this launch
     uint32_t tile_end;
-    uint8_t *slots;          // compress fast path: two staging slots per warp
+    uint8_t *slots;          // compress: two staging slots per warp (null: none)
     uint32_t nslot_warps;    // warps the slots cover
     VisParams vis;
 };
 
-// Shared-memory bytes per warp-CTA for each kernel family and block-size class.
-uint32_t compress_smem_bytes(uint32_t maxb, int level);
+// Shared-memory bytes per warp-CTA for each kernel family and block-size class
+// (staged: the general compressor with staging slots, see launch_compress).
+uint32_t compress_smem_bytes(uint32_t maxb, int level, bool staged = false);
+// bytes of one staging slot of the general compressor
+uint32_t compress_slot_bytes(uint32_t maxb);
 uint32_t decompress_smem_bytes(uint32_t maxb);
 // resident CTAs per SM of the one-buffer (in-place) decompress kernel
 uint32_t decompress_inplace_blocks_per_sm(uint32_t es);
@@ -98,6 +101,10 @@ cudaError_t launch_reduce_precision(const float *in, float *out, uint64_t n_cplx
                                     const VisParams &v, uint32_t grid, cudaStream_t s);
 cudaError_t launch_shuffle(const CodecArgs &a, bool inverse, uint32_t maxb, uint32_t grid,
                            cudaStream_t s);
+// General compressor, tiles [a.tile_begin, a.tile_end).  With a.slots (two
+// slots of compress_slot_bytes(maxb) per CTA of the grid, grid <=
+// a.nslot_warps) blocks are placed one block late from the slots; without,
+// each block is placed as soon as it is encoded.
 cudaError_t launch_compress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s);
 // Fast path for full blocks that the in-place register transposes take
 // (shuffle_inplace_ok; for a cube also n_time % 16 == 0): tiles

@@ -193,6 +193,51 @@ def test_compress_decodes_with_oracle(bs, orc, es, B, n, kind, level):
     assert np.array_equal(host_bytes(out), a.view(np.uint8))
 
 
+def _structured_rows(rng, nwords, rowwords, kind):
+    """One block's bit-rows as 32-bit words, built so that the level-0 parse
+    sees many short matches: runs of equal words ("runs"), words copied from
+    the bit-row above ("rows") or both with long zero stretches ("mixed").
+    "runs" places a 4-word run every 40 words (about 50 candidate runs, so
+    more than 32 sequences); "dense" every 12 (more than 127 candidate runs)."""
+    w = rng.integers(0, 2 ** 32, size=nwords, dtype=np.uint64).astype(np.uint32)
+    step = {"runs": 40, "dense": 12, "rows": 30, "mixed": 23}[kind]
+    for i in range(step, nwords - 8, step):
+        if kind in ("runs", "dense") or (kind == "mixed" and (i // step) % 3 == 0):
+            w[i:i + 4] = w[i - 1]
+        elif i >= rowwords:
+            w[i:i + 5] = w[i - rowwords:i - rowwords + 5]
+    if kind == "mixed":
+        z0 = int(rng.integers(0, nwords // 2))
+        w[z0:z0 + int(rng.integers(70, 300))] = 0
+    return w
+
+
+@pytest.mark.parametrize("es", [2, 4, 8])
+def test_fast_encoder_structured_blocks(bs, orc, es):
+    """Blocks whose bit-rows hold many short matches (more than 32 sequences,
+    and more than 127 candidate runs, which take the encoder's walk instead
+    of its parse graph) round-trip through the oracle's decoder."""
+    B = 8192 // es
+    rng = np.random.default_rng(20 + es)
+    kinds = ["runs", "dense", "rows", "mixed"] * 3
+    rows = np.concatenate([_structured_rows(rng, 2048, B // 32, k) for k in kinds])
+    dt = {2: np.uint16, 4: np.int32, 8: np.float64}[es]
+    a = orc.bitunshuffle(rows.view(dt), B)
+    assert np.array_equal(orc.bitshuffle(a, B).view(np.uint32), rows)
+    tail = np.arange(5, dtype=np.uint8).view(np.uint8)
+    full = np.concatenate([a.view(np.uint8), np.resize(tail, 5 * es)]).view(dt)
+    n = full.size
+    c = bs.compress(to_dev(full), B, elem_size=es, level=0)
+    assert bs.status(c.ws) == 0
+    s = c.buf[:c.nbytes].cpu().numpy().tobytes()
+    rc, back = orc.decompress(s, n, dt, B)
+    assert rc == 0 and np.array_equal(back.view(np.uint8), full.view(np.uint8))
+    out = bs.decompress(c.buf, c.nbytes, n, es, B, offsets=c.offsets)
+    assert np.array_equal(host_bytes(out), full.view(np.uint8))
+    # the matches were found: the stream is well below the input
+    assert c.nbytes < 0.97 * full.nbytes
+
+
 def test_ratio_close_to_oracle(bs, orc):
     """Compression ratio of the GPU encoder beside the oracle's greedy one on a
     rounded visibility cube (reported; the GPU must stay within 10 %)."""
