@@ -589,6 +589,11 @@ int bsgpu_decompress(const void *in, size_t in_bytes, void *out, size_t n_elem, 
         if (e != cudaSuccess) return BSGPU_ERR_CUDA;
     }
     uint32_t maxb = maxb_class(g.B * g.es);
+    if (g.nb && !(maxb <= 8192 && g.es != 1) && (g.B * g.es) % 16u == 0) {
+        // blocks over 8 KiB and 1-byte elements: decoded in place as well
+        const uint32_t grid = persistent_grid(decompress_inplace_any_smem_bytes(maxb), g.nb);
+        return cuda_err(launch_decompress_inplace_any(a, maxb, grid, s));
+    }
     uint32_t grid = persistent_grid(decompress_smem_bytes(maxb), g.nb ? g.nb : 1);
     if (maxb <= 8192 && (g.es == 2 || g.es == 4 || g.es == 8)) {
         // the in-place kernel: as many warps as fit, never more than the blocks

@@ -700,6 +700,85 @@ __global__ void __launch_bounds__(32, 20) decompress_inplace_kernel(const __grid
     __syncwarp();
 }
 
+// In-place decoding for the shapes the 8 KiB kernel does not take (blocks
+// over 8 KiB, 1-byte elements): one buffer per warp with the block's
+// compressed image at its end and the bit-rows decoded from its start (the
+// margin argument above, scaled: the unread input stays ahead of the output
+// for a buffer of S + 2 S / 255 + 55 bytes and the image 32 bytes before
+// its end), un-transposed from there straight into the output, which is
+// 16-byte aligned for every block (the caller checks B * es).  A third of
+// the shared memory of decompress_kernel, which also holds the decoded
+// block: two to three times the resident warps.
+template <uint32_t MAXB>
+__global__ void __launch_bounds__(32, MAXB <= 8192 ? 20 : (MAXB <= 16384 ? 12 : (MAXB <= 32768 ? 6 : 3)))
+    decompress_inplace_any_kernel(const __grid_constant__ CodecArgs a)
+{
+    constexpr uint32_t BUF = inplace_any_buf(MAXB);
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *buf = sm;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + BUF);
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t parity = 0;
+    bool header_checked = false;
+    uint32_t tile = grab_tile(a.tile_counter, lane);
+    DecLoad ld{};
+    if (tile < a.nb) ld = dec_issue(a, tile, buf, bar, lane, BUF);
+    while (tile < a.nb) {
+        const DecLoad cur = ld;
+        if (cur.bulk) {
+            if (!mbar_wait_bounded(bar, parity) && lane == 0) set_status(a.status, BSGPU_ERR_TIMEOUT);
+            parity ^= 1u;
+        }
+        if (!header_checked) {
+            header_checked = true;
+            uint32_t ok = 1;
+            if (lane < 12) {
+                uint8_t want = lane < 8 ? (uint8_t)((a.n_elem * a.es) >> (8 * (7 - lane)))
+                                        : (uint8_t)(((uint64_t)a.B * a.es) >> (8 * (11 - lane)));
+                ok = a.in_bytes >= 12 && a.in[lane] == want;
+            }
+            if (__ballot_sync(FULL, !ok) && lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);
+        }
+        const uint32_t Bb = block_elems_of(a, tile);
+        const uint32_t S = Bb * a.es;
+        const uint32_t nxt = grab_tile(a.tile_counter, lane);
+        uint8_t *comp = buf + cur.off;
+        bool good = cur.ok;
+        if (good) {
+            if (cur.eidx != ~0u) comp[cur.eidx] = cur.ebyte;
+            __syncwarp();
+            good = get_be32(comp + cur.delta) == cur.clen &&
+                   lz4_decode_warp(comp, cur.delta + 4, cur.clen, buf, S) == 0;
+        }
+        if (!good && lane == 0) set_status(a.status, BSGPU_ERR_CORRUPT);
+        __syncwarp();
+        if (good) unshuffle_block(buf, a.out + (uint64_t)tile * a.B * a.es, Bb, a.es, lane);
+        if (tile + 1 == a.nb) {
+            const uint32_t tb = a.tail_elems * a.es;
+            const uint64_t first = (a.n_elem - a.tail_elems) * a.es;
+            if (a.in_bytes >= tb)
+                for (uint32_t k = lane; k < tb; k += 32)
+                    a.out[first + k] = a.in[a.in_bytes - tb + k];
+        }
+        // the next block's bytes go into the buffer once the un-transpose has read it
+        fence_proxy_async_smem();
+        __syncwarp();
+        ld = DecLoad{};
+        if (nxt < a.nb) ld = dec_issue(a, nxt, buf, bar, lane, BUF);
+        tile = nxt;
+    }
+}
+
+uint32_t decompress_inplace_any_smem_bytes(uint32_t maxb)
+{
+    return inplace_any_buf(maxb) + 16;
+}
+
 uint32_t decompress_inplace_blocks_per_sm(uint32_t es)
 {
     int n = 0;
@@ -1401,6 +1480,16 @@ cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, 
     if (maxb <= 16384) return launch_warp_kernel(decompress_kernel<16384, 0>, smem, grid, s, a);
     if (maxb <= 32768) return launch_warp_kernel(decompress_kernel<32768, 0>, smem, grid, s, a);
     return launch_warp_kernel(decompress_kernel<65536, 0>, smem, grid, s, a);
+}
+
+cudaError_t launch_decompress_inplace_any(const CodecArgs &a, uint32_t maxb, uint32_t grid,
+                                          cudaStream_t s)
+{
+    const uint32_t smem = decompress_inplace_any_smem_bytes(maxb);
+    if (maxb <= 8192) return launch_warp_kernel(decompress_inplace_any_kernel<8192>, smem, grid, s, a);
+    if (maxb <= 16384) return launch_warp_kernel(decompress_inplace_any_kernel<16384>, smem, grid, s, a);
+    if (maxb <= 32768) return launch_warp_kernel(decompress_inplace_any_kernel<32768>, smem, grid, s, a);
+    return launch_warp_kernel(decompress_inplace_any_kernel<65536>, smem, grid, s, a);
 }
 
 cudaError_t launch_chain_walk(const CodecArgs &a, uint64_t *offsets, void *seg_ws,

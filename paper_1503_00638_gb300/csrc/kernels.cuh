@@ -80,6 +80,8 @@ uint32_t compress_slot_bytes(uint32_t maxb);
 uint32_t decompress_smem_bytes(uint32_t maxb);
 // resident CTAs per SM of the one-buffer (in-place) decompress kernel
 uint32_t decompress_inplace_blocks_per_sm(uint32_t es);
+// shared memory of the in-place decompress kernel for other shapes
+uint32_t decompress_inplace_any_smem_bytes(uint32_t maxb);
 uint32_t shuffle_smem_bytes(uint32_t maxb);
 
 // Launchers (return cudaGetLastError()).  `grid` warps of 32 threads.
@@ -123,6 +125,10 @@ constexpr uint32_t FAST_SLOT_BYTES = 8304;
 constexpr uint32_t FAST_MAX_WARPS = 3072;
 cudaError_t launch_compress_small(const CodecArgs &a, cudaStream_t s);
 cudaError_t launch_decompress(const CodecArgs &a, uint32_t maxb, uint32_t grid, cudaStream_t s);
+// In-place decoding for blocks over 8 KiB and 1-byte elements, the output
+// 16-byte aligned for every block ((a.B * a.es) % 16 == 0, a.out aligned).
+cudaError_t launch_decompress_inplace_any(const CodecArgs &a, uint32_t maxb, uint32_t grid,
+                                          cudaStream_t s);
 // Block index of a stream without one (seg_ws: SEG_WS_BYTES of workspace for
 // the parallel recovery, or null for the staged serial walk alone).
 constexpr size_t SEG_WS_BYTES = 256 + 160 * 2048;

@@ -276,13 +276,18 @@ def test_compress_vis_matches_oracle(bs, orc, name, cfg, B, level):
 
 # ------------------------------------------------------------- corruption --
 
-def test_corrupt_streams_report_status(bs, orc):
-    a = synth.random_walk(4096 * 5 + 3, np.int32, seed=1)
+@pytest.mark.parametrize("es,B", [(4, 1024), (1, 2048), (2, 8192), (4, 8192)])
+def test_corrupt_streams_report_status(bs, orc, es, B):
+    """Corrupt streams give CORRUPT and never a fault, in the 8 KiB in-place
+    decoder (4-byte elements) and in the in-place decoder for other shapes
+    (1-byte elements, 16 and 32 KiB blocks)."""
+    dt = {1: np.uint8, 2: np.uint16, 4: np.int32}[es]
+    a = synth.random_walk(B * 5 + 3, dt, seed=1)
     d = to_dev(a)
-    c = bs.compress(d, 1024, elem_size=4)
+    c = bs.compress(d, B, elem_size=es)
     n, nbytes = a.size, c.nbytes
     good = c.buf[:nbytes].clone()
-    ws = bs.new_workspace(bs.workspace_size(bs.OP_DECOMPRESS, n, 4, 1024))
+    ws = bs.new_workspace(bs.workspace_size(bs.OP_DECOMPRESS, n, es, B))
     cases = []
     t = good.clone(); t[3] ^= 1; cases.append((t, nbytes, "header"))
     cases.append((good.clone(), nbytes - 1, "truncated"))
@@ -291,7 +296,7 @@ def test_corrupt_streams_report_status(bs, orc):
     t = good.clone(); t[12] = 0xFF; cases.append((t, nbytes, "length field"))
     for buf, L, what in cases:
         for offs in (None, c.offsets):
-            bs.decompress(buf, L, n, 4, 1024, offsets=offs, ws=ws)
+            bs.decompress(buf, L, n, es, B, offsets=offs, ws=ws)
             assert bs.status(ws) == bs.ERR_CORRUPT, what
     # random byte flips: never a fault; status is OK or CORRUPT
     rng = np.random.default_rng(3)
@@ -299,10 +304,10 @@ def test_corrupt_streams_report_status(bs, orc):
         t = good.clone()
         k = int(rng.integers(12, nbytes))
         t[k] ^= int(rng.integers(1, 256))
-        bs.decompress(t, nbytes, n, 4, 1024, offsets=c.offsets, ws=ws)
+        bs.decompress(t, nbytes, n, es, B, offsets=c.offsets, ws=ws)
         assert bs.status(ws) in (0, bs.ERR_CORRUPT)
     # the good stream still decodes with the same workspace
-    out = bs.decompress(good, nbytes, n, 4, 1024, offsets=c.offsets, ws=ws)
+    out = bs.decompress(good, nbytes, n, es, B, offsets=c.offsets, ws=ws)
     assert bs.status(ws) == 0 and np.array_equal(host_bytes(out), a.view(np.uint8))
 
 
