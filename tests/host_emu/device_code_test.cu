@@ -285,15 +285,18 @@ static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc
                     bad++;
                 }
                 // a node table of 8 entries: most blocks take the candidate walk
-                memset(E, 0xCD, S + 64);
-                run_warp([&] {
-                    uint32_t o = lz4_encode_bitmap_fast<8>(A, S, rows[ci], E, FS);
-                    if (threadIdx.x == 0) cs3 = o;
-                });
-                if (cs3 != cs || memcmp(E, Bf, cs)) {
-                    fprintf(stderr, "fast bitmap encoder (walk) differs S=%u rows=%u %u vs %u\n", S,
-                            rows[ci], cs3, cs);
-                    bad++;
+                // (every other case, to keep the emulation's run time down)
+                if (ci % 2 == 0) {
+                    memset(E, 0xCD, S + 64);
+                    run_warp([&] {
+                        uint32_t o = lz4_encode_bitmap_fast<8>(A, S, rows[ci], E, FS);
+                        if (threadIdx.x == 0) cs3 = o;
+                    });
+                    if (cs3 != cs || memcmp(E, Bf, cs)) {
+                        fprintf(stderr, "fast bitmap encoder (walk) differs S=%u rows=%u %u vs %u\n", S,
+                                rows[ci], cs3, cs);
+                        bad++;
+                    }
                 }
             }
         }
