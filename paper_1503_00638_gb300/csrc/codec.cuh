@@ -749,14 +749,17 @@ struct NoRound {
 constexpr uint32_t INPLACE_BUF = 8352;
 
 // The same buffer for any block size up to maxb (decompress_inplace_any_kernel):
-// room for the image (4 + lz4b(maxb), 48 before the end at most) and the
-// in-place margin (S + 2 S / 255 + 55).
+// room for the image (4 + lz4b(maxb), placed at most 48 bytes before the end)
+// and the in-place margin (at least S + 2 S / 255 + 49 bytes).
 __host__ __device__ constexpr uint32_t inplace_any_buf(uint32_t maxb)
 {
     return maxb <= 8192 ? INPLACE_BUF : r16(maxb + 2u * maxb / 255u + 160u);
 }
-static_assert(inplace_any_buf(65536) >= 4 + lz4b(65536) + 48 &&
-                  inplace_any_buf(65536) >= 65536 + 2 * 65536 / 255 + 55 + 32 + 15 + 4,
+static_assert(inplace_any_buf(16384) >= 4 + lz4b(16384) + 48 &&
+                  inplace_any_buf(16384) >= 16384 + 2 * 16384 / 255 + 49 &&
+                  inplace_any_buf(65536) >= 4 + lz4b(65536) + 48 &&
+                  inplace_any_buf(65536) >= 65536 + 2 * 65536 / 255 + 49 &&
+                  INPLACE_BUF >= 4 + lz4b(8192) + 48 && INPLACE_BUF >= 8192 + 2 * 8192 / 255 + 49,
               "in-place buffer");
 static_assert(INPLACE_BUF >= 4 + lz4b(8192) + 48, "in-place buffer: image does not fit");
 static_assert(INPLACE_BUF >= 8192 + 119, "in-place buffer: margin below the LZ4 bound");

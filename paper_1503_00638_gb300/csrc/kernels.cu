@@ -702,13 +702,15 @@ __global__ void __launch_bounds__(32, 20) decompress_inplace_kernel(const __grid
 
 // In-place decoding for the shapes the 8 KiB kernel does not take (blocks
 // over 8 KiB, 1-byte elements): one buffer per warp with the block's
-// compressed image at its end and the bit-rows decoded from its start (the
-// margin argument above, scaled: the unread input stays ahead of the output
-// for a buffer of S + 2 S / 255 + 55 bytes and the image 32 bytes before
-// its end), un-transposed from there straight into the output, which is
-// 16-byte aligned for every block (the caller checks B * es).  A third of
-// the shared memory of decompress_kernel, which also holds the decoded
-// block: two to three times the resident warps.
+// compressed image near its end and the bit-rows decoded from its start,
+// un-transposed from there straight into the output, which is 16-byte
+// aligned for every block (the caller checks B * es).  The margin argument
+// above holds for any S: the LZ4 bytes must start at least 2 + 2 S / 255
+// bytes after S - clen, and dec_issue puts them at least E - clen - 47
+// bytes in (E the buffer size), so E >= S + 2 S / 255 + 49 suffices
+// (inplace_any_buf gives S + 2 S / 255 + 160).  Half the shared memory of
+// decompress_kernel, which holds the compressed and the decoded block apart:
+// twice the resident warps or more.
 template <uint32_t MAXB>
 __global__ void __launch_bounds__(32, MAXB <= 8192 ? 20 : (MAXB <= 16384 ? 12 : (MAXB <= 32768 ? 6 : 3)))
     decompress_inplace_any_kernel(const __grid_constant__ CodecArgs a)
