@@ -42,6 +42,10 @@ __global__ void __launch_bounds__(32, 20) compress_fast_kernel(const __grid_cons
     uint32_t tile = grab_tile(a.tile_counter, lane);
     while (tile < a.tile_end) {
         const uint32_t Bb = a.B;  // the fast path takes full blocks only
+        // 2048 4-byte elements at level 0 (the CHIME-shaped default): the
+        // transpose also yields the encoder's equality bitmaps
+        const bool EQ = LEVEL == 0 && ES == 4 && !PS && Bb == 2048;
+        uint32_t Erow[2], Erun[2];
         if (TS) {
             if (PS)
                 gather_tslow_samples(a, tmp, tile, lane);
@@ -82,16 +86,24 @@ __global__ void __launch_bounds__(32, 20) compress_fast_kernel(const __grid_cons
             __syncwarp();
             shuffle4_inplace(tmp, Bb, lane, NoRound{});
         } else if (a.vis.enabled) {
-            shuffle4_inplace(tmp, Bb, lane,
-                             VisGroupRound<GEN>{&a.vis, (uint32_t)(((uint64_t)tile * a.B) >> 1)});
+            const VisGroupRound<GEN> round{&a.vis, (uint32_t)(((uint64_t)tile * a.B) >> 1)};
+            if (EQ)
+                shuffle4_inplace_eq(tmp, lane, round, Erow, Erun);
+            else
+                shuffle4_inplace(tmp, Bb, lane, round);
+        } else if (EQ) {
+            shuffle4_inplace_eq(tmp, lane, NoRound{}, Erow, Erun);
         } else {
             shuffle4_inplace(tmp, Bb, lane, NoRound{});
         }
         __syncwarp();
         uint32_t cs;
         if (LEVEL == 0 && (Bb * ES) % 128u == 0) {
-            cs = lz4_encode_bitmap_fast(tmp, Bb * ES, Bb / 8, slot0 + 4,
-                                        static_cast<uint32_t *>(scratch));
+            if (!EQ)
+                lz4_eq_bitmaps(reinterpret_cast<const uint32_t *>(tmp), Bb * ES / 128, Bb / 32, lane, Erow,
+                               Erun);
+            cs = lz4_encode_bitmap_fast_eq(tmp, Bb * ES, Bb / 8, slot0 + 4,
+                                           static_cast<uint32_t *>(scratch), Erow, Erun);
             if (lane == 0) put_be32(slot0, cs);
             __syncwarp();
         } else {

@@ -591,32 +591,17 @@ BSG_D void run_ends(const uint32_t (&c)[2], uint32_t (&e)[2], uint32_t lane)
     e[1] = c[1] & ~((c[1] >> 1) | (h1 << 31));
 }
 
-// Level-0 encoder for the fast path (S a multiple of 128, at most 8192): the
-// same parse as lz4_encode_bitmap.  The equality bitmaps are built in
-// registers (two words per lane) and kept in shared memory `scr`
-// (LZ4_FAST_SCRATCH bytes, 4-byte aligned) with the candidate-run ends and
-// their ranks, from which the warp builds the parse graph (node table: the
-// node's position in 13 bits, the first candidate after it in 11, the
-// successor node in 8, 255 for none).  The sequences are emitted 32 at a time
-// in parallel: the parse collects up to 32 (literal start, match start, match
-// length, offset) descriptors, one per lane; a warp scan of their encoded
-// lengths places them; each lane writes its own token, length and offset
-// bytes; the literal runs are copied one after another by the whole warp.
-// NODE_CAP below LZ4_NODE_CAP only serves tests of the candidate walk.
-template <uint32_t NODE_CAP = LZ4_NODE_CAP>
-BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t rowlen, uint8_t *dst,
-                                      uint32_t *scr)
+// Equality bitmaps of a block of NW = 32 NB words (NB <= 64) in shared
+// memory: bit w of Erow set when word w equals word w - R (the bit-row
+// above; none for R = 0), of Erun when it equals word w - 1; bitmap word k
+// kept by lane k mod 32 in [k / 32].
+BSG_D void lz4_eq_bitmaps(const uint32_t *s32, uint32_t NB, uint32_t R, uint32_t lane,
+                          uint32_t (&Erow)[2], uint32_t (&Erun)[2])
 {
-    static_assert(NODE_CAP >= 1 && NODE_CAP <= LZ4_NODE_CAP && LZ4_NODE_CAP < 255, "node table");
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
-    const uint32_t NW = S / 4, NB = NW / 32;
-    const uint32_t R = (rowlen & 3u) ? 0u : rowlen / 4;
-    // equality bitmaps: bit w of Erow (Erun) set when word w equals word w - R (w - 1).
     // Both neighbours are read from shared memory; words without one (w < R,
     // w = 0) read some word of the block instead and have their bits cleared
     // after the loop.
-    uint32_t Erow[2] = {0u, 0u}, Erun[2] = {0u, 0u};
+    Erow[0] = Erow[1] = Erun[0] = Erun[1] = 0u;
 #pragma unroll
     for (uint32_t j = 0; j < 2; j++) {
         const uint32_t kend = NB < 32 * (j + 1) ? (NB > 32 * j ? NB - 32 * j : 0u) : 32u;
@@ -642,6 +627,30 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
         if (R == 0 || k0 + 32 <= R) Erow[j] = 0u;
         else if (k0 < R) Erow[j] &= ~0u << (R - k0);
     }
+}
+
+// Level-0 encoder for the fast path (S a multiple of 128, at most 8192): the
+// same parse as lz4_encode_bitmap.  From the equality bitmaps (two words per
+// lane, as lz4_eq_bitmaps leaves them) it derives candidate bitmaps, kept in
+// shared memory `scr` (LZ4_FAST_SCRATCH bytes, 4-byte aligned) with the
+// candidate-run ends and their ranks, from which the warp builds the parse graph (node table: the
+// node's position in 13 bits, the first candidate after it in 11, the
+// successor node in 8, 255 for none).  The sequences are emitted 32 at a time
+// in parallel: the parse collects up to 32 (literal start, match start, match
+// length, offset) descriptors, one per lane; a warp scan of their encoded
+// lengths places them; each lane writes its own token, length and offset
+// bytes; the literal runs are copied one after another by the whole warp.
+// NODE_CAP below LZ4_NODE_CAP only serves tests of the candidate walk.
+template <uint32_t NODE_CAP = LZ4_NODE_CAP>
+BSG_D uint32_t lz4_encode_bitmap_fast_eq(const uint8_t *src, uint32_t S, uint32_t rowlen,
+                                         uint8_t *dst, uint32_t *scr, const uint32_t (&Erow)[2],
+                                         const uint32_t (&Erun)[2])
+{
+    static_assert(NODE_CAP >= 1 && NODE_CAP <= LZ4_NODE_CAP && LZ4_NODE_CAP < 255, "node table");
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
+    const uint32_t NW = S / 4;
+    const uint32_t R = (rowlen & 3u) ? 0u : rowlen / 4;
     // candidate bitmaps: bits w .. w + LZ4_L0_MINWORDS - 1 all set (LZ4_L0_MINMATCH
     // equal bytes)
     uint32_t Crow[2], Crun[2];
@@ -874,6 +883,17 @@ BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t r
     o = lz4_emit_last(dst, o, src, anchor, S, lane);
     __syncwarp();
     return o;
+}
+
+// The same, building its equality bitmaps from the block in shared memory.
+template <uint32_t NODE_CAP = LZ4_NODE_CAP>
+BSG_D uint32_t lz4_encode_bitmap_fast(const uint8_t *src, uint32_t S, uint32_t rowlen, uint8_t *dst,
+                                      uint32_t *scr)
+{
+    uint32_t Erow[2], Erun[2];
+    lz4_eq_bitmaps(reinterpret_cast<const uint32_t *>(src), S / 128, (rowlen & 3u) ? 0u : rowlen / 4,
+                   threadIdx.x & 31u, Erow, Erun);
+    return lz4_encode_bitmap_fast_eq<NODE_CAP>(src, S, rowlen, dst, scr, Erow, Erun);
 }
 
 // Warp-parallel read of 255-continued length bytes at src[ip..]; adds them to

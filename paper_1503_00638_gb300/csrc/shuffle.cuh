@@ -276,6 +276,86 @@ BSG_D void shuffle4_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane, Fix fix)
     for (int r = 0; r < 32; r++) d32[r * 64 + g1] = rotl(b[r], rot1);
 }
 
+// shuffle4_inplace for Bb == 2048 that also returns the level-0 LZ4
+// encoder's equality bitmaps of the bit-rows it writes, as
+// lz4_eq_bitmaps computes them from shared memory: bit w of Erow set when
+// word w of the rows equals word w - 64 (the same group one bit-row up),
+// of Erun when it equals word w - 1; bitmap word k (words 32 k .. 32 k + 31)
+// kept by lane k mod 32 in [k / 32].  Word 64 r + 32 j + lane is row r of
+// group 32 j + lane, so each stored word is compared as it is stored with
+// the lane's previous row (same lane) and with the lane before (a shuffle);
+// the first word of each half-row, whose left neighbour is the other half's
+// last group, is compared from shared memory after the stores.
+template <class Fix>
+BSG_D void shuffle4_inplace_eq(uint8_t *buf, uint32_t lane, Fix fix, uint32_t (&Erow)[2],
+                               uint32_t (&Erun)[2])
+{
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(buf);
+    auto read_group = [&](uint32_t g, uint32_t (&a)[32]) {
+        const uint8_t *grp = buf + 128u * g;
+        const uint32_t rot = g & 7u;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            uint4 v = *reinterpret_cast<const uint4 *>(grp + 16u * ((k + rot) & 7u));
+            a[4 * k] = v.x;
+            a[4 * k + 1] = v.y;
+            a[4 * k + 2] = v.z;
+            a[4 * k + 3] = v.w;
+        }
+        fix(g, a);
+        transpose32(a);
+    };
+    const uint32_t rot = 4u * (lane & 7u);  // groups lane and lane + 32 share it
+    Erow[0] = Erow[1] = Erun[0] = Erun[1] = 0u;
+    auto put = [&](int r, uint32_t j, uint32_t v, uint32_t vup) {
+        d32[r * 64 + 32 * j + lane] = v;
+        const uint32_t left = __shfl_up_sync(FULL, v, 1);
+        const uint32_t row = __ballot_sync(FULL, r > 0 && v == vup);
+        const uint32_t run = __ballot_sync(FULL, v == left);  // lane 0: fixed below
+        const uint32_t k = 2u * (uint32_t)r + j;
+        if (lane == (k & 31u)) {
+            Erow[k >> 5] = row;
+            Erun[k >> 5] = run;
+        }
+    };
+    uint32_t a[32];
+    read_group(lane, a);
+    __syncwarp();
+    uint32_t up = 0;
+#pragma unroll
+    for (int r = 0; r < 16; r++) {
+        const uint32_t v = rotl(a[r], rot);
+        put(r, 0, v, up);
+        up = v;
+    }
+    uint32_t b[32];
+    read_group(lane + 32u, b);
+    __syncwarp();
+#pragma unroll
+    for (int r = 16; r < 32; r++) {
+        const uint32_t v = rotl(a[r], rot);
+        put(r, 0, v, up);
+        up = v;
+    }
+    up = 0;
+#pragma unroll
+    for (int r = 0; r < 32; r++) {
+        const uint32_t v = rotl(b[r], rot);
+        put(r, 1, v, up);
+        up = v;
+    }
+    __syncwarp();
+    // word 64 r + 32 j (r = lane) against word 64 r + 32 j - 1; none before word 0
+    const uint32_t x0 = d32[64 * lane], p0 = lane ? d32[64 * lane - 1] : ~x0;
+    const uint32_t x1 = d32[64 * lane + 32], p1 = d32[64 * lane + 31];
+    const uint32_t f0 = __ballot_sync(FULL, x0 == p0), f1 = __ballot_sync(FULL, x1 == p1);
+#pragma unroll
+    for (uint32_t h = 0; h < 2; h++) {
+        const uint32_t k = 32u * h + lane;  // bitmap word 2 r + j
+        Erun[h] = (Erun[h] & ~1u) | ((((k & 1u) ? f1 : f0) >> (k >> 1)) & 1u);
+    }
+}
+
 // 8-byte elements, at most 32 groups (one per lane).
 BSG_D void shuffle8_inplace(uint8_t *buf, uint32_t Bb, uint32_t lane)
 {

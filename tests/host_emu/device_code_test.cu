@@ -159,6 +159,40 @@ static int test_inplace_unshuffle(std::mt19937 &rng)
                 bad += memcmp(rows.data(), C, S) != 0;
             }
         }
+    // the transpose that also yields the encoder's equality bitmaps: bit-rows
+    // with runs of equal words and words copied from the row above, the
+    // bitmaps against lz4_eq_bitmaps on the rows it wrote
+    for (int t = 0; t < 6; t++) {
+        static uint32_t w[2048];
+        for (int i = 0; i < 2048; i++) w[i] = (uint32_t)rng();
+        for (int i = 1 + (int)(rng() % 7); i < 2040; i += 3 + (int)(rng() % 29)) {
+            const int len = 1 + (int)(rng() % 6);
+            for (int k = 0; k < len && i + k < 2048; k++)
+                w[i + k] = (rng() & 1) ? w[i + k - 1] : (i + k >= 64 ? w[i + k - 64] : 0u);
+        }
+        if (t & 1)
+            for (int i = 64 * (t + 3); i < 64 * (t + 5); i++) w[i] = 0;  // whole zero rows
+        orc_bitshuffle(w, A, 2048, 4, 2048, 1);
+        memcpy(C, A, 8192);
+        uint32_t er[32][2], eu[32][2], fr[32][2], fu[32][2];
+        run_warp([&] {
+            uint32_t R2[2], U2[2];
+            shuffle4_inplace_eq(C, threadIdx.x, [](uint32_t, uint32_t (&)[32]) {}, R2, U2);
+            er[threadIdx.x][0] = R2[0], er[threadIdx.x][1] = R2[1];
+            eu[threadIdx.x][0] = U2[0], eu[threadIdx.x][1] = U2[1];
+        });
+        bad += memcmp(C, w, 8192) != 0;
+        run_warp([&] {
+            uint32_t R2[2], U2[2];
+            lz4_eq_bitmaps(reinterpret_cast<const uint32_t *>(C), 64, 64, threadIdx.x, R2, U2);
+            fr[threadIdx.x][0] = R2[0], fr[threadIdx.x][1] = R2[1];
+            fu[threadIdx.x][0] = U2[0], fu[threadIdx.x][1] = U2[1];
+        });
+        if (memcmp(er, fr, sizeof er) || memcmp(eu, fu, sizeof eu)) {
+            fprintf(stderr, "fused equality bitmaps differ (case %d)\n", t);
+            bad++;
+        }
+    }
     return bad;
 }
 
