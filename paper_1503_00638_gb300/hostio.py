@@ -12,6 +12,11 @@ kind's in one queue (measured on the CHIME-shaped cube: 88 GB/s round trip
 with one upload and one download stream, 103 GB/s with one per kind).  Slabs are independent: the noise of Sec. 3.1 only needs a
 slab's own autocorrelations.
 
+`HostBatchCodec` does the same for the batch workload: groups of chunks,
+one batched launch per group and direction (measured on 447 chunks of the
+batch generator, 4.3 GB: 90 GB/s round trip, against 44 GB/s with the
+copies and launches one after another on one stream).
+
 Host orchestration only (pinned buffers, streams, events); the rounding,
 shuffling and coding run in libbsgpu's kernels.
 """
@@ -173,3 +178,120 @@ class HostVisCodec:
         streams = sum(c.nbytes for c in chunks)
         idx = sum(c.index.numel() * 8 for c in chunks)
         return cube + streams + idx, streams + idx + cube + 8 * len(chunks)
+
+
+class HostBatchCodec:
+    """Round trip of many chunks that live in pinned host memory (the batch
+    workload: uneven sizes and element widths), in groups of consecutive
+    chunks: each group is one `engine.BatchCodec` (one persistent launch per
+    direction over every block of its chunks), and the upload of one group,
+    the kernels of another and the downloads of a third overlap, with one
+    CUDA stream per kind of copy as in `HostVisCodec`.  Every chunk's stream
+    (its exact length) and block index go to host memory and are read back
+    from there for the decompression, so the round trip moves what storing
+    the streams would.
+
+    sizes       : bytes of each chunk
+    elem_sizes  : element size of each chunk (1, 2, 4 or 8)
+    block_elems : block size (elements) of each chunk, or one for all
+    group_bytes : uncompressed bytes per group (a group holds at least one chunk)
+    launch      : (warps per CTA, CTAs per SM) of the compress and the
+                  decompress launch, e.g. the autotuner's choice
+    """
+
+    def __init__(self, sizes, elem_sizes, block_elems, level: int = 0,
+                 group_bytes: int = 512 << 20, launch=((1, 0), (1, 0)), device="cuda"):
+        from . import engine
+        self.dev = torch.device(device)
+        self.sizes = [int(s) for s in sizes]
+        self.es = [int(e) for e in elem_sizes]
+        n = len(self.sizes)
+        bl = block_elems if isinstance(block_elems, (list, tuple)) else [block_elems] * n
+        self.groups = []
+        i = 0
+        while i < n:
+            j, acc = i, 0
+            while j < n and (j == i or acc + self.sizes[j] <= group_bytes):
+                acc += self.sizes[j]
+                j += 1
+            self.groups.append((i, j))
+            i = j
+        self.codecs = []
+        for g0, g1 in self.groups:
+            xs = [torch.empty(self.sizes[k], dtype=torch.uint8, device=self.dev) for k in range(g0, g1)]
+            c = engine.BatchCodec(xs, self.es[g0:g1], list(bl[g0:g1]), level=level)
+            (c.warps_c, c.ctas_c), (c.warps_d, c.ctas_d) = launch
+            self.codecs.append(c)
+        self.s_k = torch.cuda.Stream(device=self.dev)
+        self.s_upc = torch.cuda.Stream(device=self.dev)   # chunks up
+        self.s_dns = torch.cuda.Stream(device=self.dev)   # streams down
+        self.s_ups = torch.cuda.Stream(device=self.dev)   # streams up
+        self.s_dnc = torch.cuda.Stream(device=self.dev)   # chunks down
+        self.h_len = [torch.empty(c.n, dtype=torch.int64).pin_memory() for c in self.codecs]
+        self.h_streams = [[torch.empty(cap, dtype=torch.uint8).pin_memory() for cap in c.caps]
+                          for c in self.codecs]
+        self.h_index = [torch.empty(max(c.n_items, 1), dtype=torch.int64).pin_memory()
+                        for c in self.codecs]
+        self.lens = [None] * len(self.codecs)
+
+    def round_trip(self, h_in, h_out, lag: int = 1) -> None:
+        """Compress the pinned host chunks h_in (uint8 tensors of `sizes`) into
+        pinned host streams and decompress those back into the pinned host
+        tensors h_out, group by group with copies and kernels overlapped."""
+        G = len(self.codecs)
+        lag = max(0, lag)
+        ev = [{k: torch.cuda.Event() for k in ("in", "c", "d2h", "up", "dc")} for _ in range(G)]
+        for step in range(G + lag):
+            g = step
+            if g < G:
+                c, (g0, _) = self.codecs[g], self.groups[g]
+                with torch.cuda.stream(self.s_upc):
+                    for k, x in enumerate(c.inputs):
+                        x.copy_(h_in[g0 + k], non_blocking=True)
+                    ev[g]["in"].record(self.s_upc)
+                self.s_k.wait_event(ev[g]["in"])
+                with torch.cuda.stream(self.s_k):
+                    c.compress(self.s_k)
+                    self.h_len[g].copy_(c.out_bytes, non_blocking=True)
+                    ev[g]["c"].record(self.s_k)
+            j = step - lag
+            if j >= 0:
+                c, (g0, _) = self.codecs[j], self.groups[j]
+                ev[j]["c"].synchronize()               # the stream lengths, for exact copies
+                lens = self.h_len[j].tolist()
+                self.lens[j] = lens
+                self.s_dns.wait_event(ev[j]["c"])
+                with torch.cuda.stream(self.s_dns):
+                    for k, L in enumerate(lens):
+                        o = c.stream_off[k]
+                        self.h_streams[j][k][:L].copy_(c.stream_arena[o:o + L], non_blocking=True)
+                    self.h_index[j][:c.n_items].copy_(c.offsets, non_blocking=True)
+                    ev[j]["d2h"].record(self.s_dns)
+                self.s_ups.wait_event(ev[j]["d2h"])
+                with torch.cuda.stream(self.s_ups):
+                    for k, L in enumerate(lens):
+                        o = c.stream_off[k]
+                        c.stream_arena[o:o + L].copy_(self.h_streams[j][k][:L], non_blocking=True)
+                    c.offsets.copy_(self.h_index[j][:c.n_items], non_blocking=True)
+                    c.out_bytes.copy_(self.h_len[j], non_blocking=True)
+                    ev[j]["up"].record(self.s_ups)
+                self.s_k.wait_event(ev[j]["up"])
+                with torch.cuda.stream(self.s_k):
+                    c.decompress(self.s_k)
+                    ev[j]["dc"].record(self.s_k)
+                self.s_dnc.wait_event(ev[j]["dc"])
+                with torch.cuda.stream(self.s_dnc):
+                    for k in range(c.n):
+                        h_out[g0 + k].copy_(c.output(k), non_blocking=True)
+        torch.cuda.synchronize(self.dev)
+
+    def statuses(self):
+        return [c.statuses() for c in self.codecs]
+
+    def bytes_moved(self):
+        """(host-to-device, device-to-host) bytes of one round trip."""
+        data = sum(self.sizes)
+        streams = sum(sum(l) for l in self.lens if l)
+        idx = sum(8 * c.n_items for c in self.codecs)
+        lens = sum(8 * c.n for c in self.codecs)
+        return data + streams + idx + lens, streams + idx + data + lens

@@ -64,3 +64,38 @@ def test_round_trip_with_other_time_axes(mods, orc, cfg):
         flat = want[f0:f1].view(np.float32).reshape(-1)
         rc, back = orc.decompress(c.stream.numpy().tobytes(), flat.size, np.float32, 2048)
         assert rc == 0 and np.array_equal(back.view(np.uint32), flat.view(np.uint32))
+
+
+@pytest.mark.parametrize("group_bytes,lag", [(1 << 20, 1), (3 << 20, 2), (64 << 20, 1)])
+def test_batch_round_trip_through_host(mods, orc, group_bytes, lag):
+    """Chunks of 1-, 2-, 4- and 8-byte elements in pinned host memory go
+    through the pipelined batch codec in groups: every output equals its
+    input, and every stream read back from host memory decodes with the
+    oracle's decoder."""
+    bs, hostio = mods
+    rng = np.random.default_rng(7)
+    arrays, es_l, bl = [], [], []
+    for k in range(23):
+        es = (1, 2, 4, 8)[k % 4]
+        n = int(rng.integers(1000, 300_000)) // es
+        dt = {1: np.uint8, 2: np.uint16, 4: np.int32, 8: np.float64}[es]
+        arrays.append(synth.random_walk(n, dt, seed=k))
+        es_l.append(es)
+        bl.append(8192 // es)
+    h_in = [torch.from_numpy(a.view(np.uint8).copy()).pin_memory() for a in arrays]
+    h_out = [torch.empty_like(h).pin_memory() for h in h_in]
+    hb = hostio.HostBatchCodec([h.numel() for h in h_in], es_l, bl, group_bytes=group_bytes)
+    assert len(hb.groups) > (1 if group_bytes < (8 << 20) else 0)
+    hb.round_trip(h_in, h_out, lag=lag)
+    for sc, sd in hb.statuses():
+        assert sc == [0] * len(sc) and sd == [0] * len(sd)
+    for i in range(len(h_in)):
+        assert torch.equal(h_out[i], h_in[i]), i
+    for g, (g0, g1) in enumerate(hb.groups):
+        for k in range(g1 - g0):
+            i = g0 + k
+            s = hb.h_streams[g][k][:hb.lens[g][k]].numpy().tobytes()
+            rc, back = orc.decompress(s, arrays[i].size, arrays[i].dtype, bl[i])
+            assert rc == 0 and np.array_equal(back.view(np.uint8), arrays[i].view(np.uint8))
+    h2d, d2h = hb.bytes_moved()
+    assert h2d > sum(h.numel() for h in h_in) and d2h > sum(h.numel() for h in h_in)
