@@ -461,33 +461,6 @@ def run_batch(args, rank, world, local, barrier, gpu_index, chunks=None, steps=N
     ms_max = float(ms_t.item())
     value = nbytes * world * steps / (ms_max / 1e3) / 1e9
 
-    # end to end through the engine with host buffers, on the leading chunks
-    # up to 4 GB (pinned host copies of the whole 40 GB are not kept)
-    sub, acc = 0, 0
-    while sub < eng.n and acc + specs[sub][0] <= (4 << 30):
-        acc += specs[sub][0]
-        sub += 1
-    sub = max(sub, 1)
-    xs_sub = xs[:sub]
-    from paper_1503_00638_gb300 import hostio
-    h_in = [x.reshape(-1).view(torch.uint8).cpu().pin_memory() for x in xs_sub]
-    h_out = [torch.empty_like(h).pin_memory() for h in h_in]
-    hb = hostio.HostBatchCodec([h.numel() for h in h_in], es_l[:sub], bl[:sub], level=LEVEL,
-                               launch=((eng.warps_c, eng.ctas_c), (eng.warps_d, eng.ctas_d)))
-    e2e_t = []
-    sub_bytes = sum(specs[i][0] for i in range(sub))
-    for k in range(args.e2e_steps + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hb.round_trip(h_in, h_out)
-        if k:
-            e2e_t.append(time.perf_counter() - t0)
-    e2e_value = sub_bytes / statistics.median(e2e_t) / 1e9
-    ok_e2e = all(torch.equal(h_out[i], h_in[i]) for i in range(0, sub, 7))
-    ok_e2e = ok_e2e and all(sc == [0] * len(sc) and sd == [0] * len(sd) for sc, sd in hb.statuses())
-    e2e_h2d, e2e_d2h = hb.bytes_moved()
-    del hb
-
     hbm, peak_kind = peaks()
     cm, dm = statistics.median(c_ms), statistics.median(d_ms)
     alg_c = nbytes + slen + 8 * eng.n_items + 8 * eng.n
@@ -524,11 +497,6 @@ def run_batch(args, rank, world, local, barrier, gpu_index, chunks=None, steps=N
         "decompress_roofline": {"bound": "hbm", "kernel": "decompress_batch_kernel",
                                 "achieved": alg_d / (dm / 1e3) / 1e9, "peak": hbm,
                                 "unit": "GB/s", "frac": alg_d / (dm / 1e3) / 1e9 / hbm},
-        "e2e": {"value": e2e_value, "unit": "GB/s",
-                "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h, "chunks": sub,
-                "round_trip_ok": ok_e2e,
-                "api": "hostio.HostBatchCodec.round_trip (groups of about 512 MB, pipelined; "
-                       "streams, lengths and block index through host memory)"},
         "gpu_launches": 2 * steps,
         "clocks": clk,
         "wall_s_timed": t_wall1 - t_wall0,
@@ -587,6 +555,56 @@ def serve_requests(xs, comp, n, rate, seed):
             reqs.append(serve.Request(i, "decompress", t, st, x.numel() // 4, 4,
                                       BATCH_BLOCK_BYTES // 4, index=idx))
     return reqs
+
+
+def batch_launch(rec):
+    """Block size and launch shapes a batch record chose (for its end-to-end step)."""
+    lc = rec["config"]["launch"]
+    return {"block_bytes": rec["config"]["block_bytes"],
+            "shapes": ((lc["compress"]["warps_per_cta"], lc["compress"]["ctas_per_sm"]),
+                       (lc["decompress"]["warps_per_cta"], lc["decompress"]["ctas_per_sm"]))}
+
+
+def run_batch_e2e(args, chunks, launch):
+    """End to end with host buffers through `hostio.HostBatchCodec` on the
+    leading chunks of the batch generator up to 4 GB (pinned host copies of
+    the whole 40 GB are not kept): inputs, streams with their lengths and
+    block index, and outputs all cross the host link.  Measured as a step of
+    its own, after the other batch and serving measurements of the run."""
+    import torch
+    from paper_1503_00638_gb300 import hostio
+    specs = batch_specs(chunks, 0)
+    sub, acc = 0, 0
+    while sub < len(specs) and acc + specs[sub][0] <= (4 << 30):
+        acc += specs[sub][0]
+        sub += 1
+    sub = max(sub, 1)
+    xs_sub = batch_inputs(specs[:sub], 0)
+    es_l = [es for _, es, _ in specs[:sub]]
+    bl = [launch["block_bytes"] // es for es in es_l]
+    h_in = [x.reshape(-1).view(torch.uint8).cpu().pin_memory() for x in xs_sub]
+    del xs_sub
+    h_out = [torch.empty_like(h).pin_memory() for h in h_in]
+    hb = hostio.HostBatchCodec([h.numel() for h in h_in], es_l, bl, level=LEVEL,
+                               launch=launch["shapes"])
+    e2e_t = []
+    sub_bytes = sum(specs[i][0] for i in range(sub))
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hb.round_trip(h_in, h_out)
+        if k:
+            e2e_t.append(time.perf_counter() - t0)
+    ok = all(torch.equal(h_out[i], h_in[i]) for i in range(0, sub, 7))
+    ok = ok and all(sc == [0] * len(sc) and sd == [0] * len(sd) for sc, sd in hb.statuses())
+    h2d, d2h = hb.bytes_moved()
+    del hb, h_in, h_out
+    torch.cuda.empty_cache()
+    return {"value": sub_bytes / statistics.median(e2e_t) / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "chunks": sub,
+            "round_trip_ok": ok,
+            "api": "hostio.HostBatchCodec.round_trip (groups of about 512 MB, pipelined; "
+                   "streams, lengths and block index through host memory)"}
 
 
 def run_serve(args, rank, world, gpu_index, requests=None, payloads=256):
@@ -1240,6 +1258,7 @@ def main():
         return
     if args.workload == "batch":
         line = run_batch(args, rank, world, local, barrier, gpu_index)
+        line["e2e"] = run_batch_e2e(args, args.chunks, batch_launch(line))
         if rank == 0:
             print(json.dumps(line), flush=True)
         if world > 1:
@@ -1469,12 +1488,14 @@ def main():
                       steps=5, warmup=3, cpu=False)
         line["batch"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "compress_gbs",
                                            "decompress_gbs", "ratio", "roofline",
-                                           "decompress_roofline", "config", "parity", "e2e",
+                                           "decompress_roofline", "config", "parity",
                                            "clocks", "gpu_launches") if k in b}
         torch.cuda.empty_cache()
         sv = run_serve(args, rank, world, gpu_index, requests=args.sub_requests, payloads=128)
         line["serving"] = {"value_gbs_at_saturation": sv["value"], "unit": "GB/s",
                            "config": sv["config"], "clocks": sv["clocks"], **sv["serving"]}
+        torch.cuda.empty_cache()
+        line["batch"]["e2e"] = run_batch_e2e(args, args.sub_chunks, batch_launch(b))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
