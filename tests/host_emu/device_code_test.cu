@@ -196,6 +196,49 @@ static int test_inplace_unshuffle(std::mt19937 &rng)
     return bad;
 }
 
+// In-place decoding of blocks over 8 KiB as decompress_inplace_any_kernel
+// lays them out: a buffer of S + 2 S / 255 + 160 bytes (rounded up to 16; the
+// kernel's inplace_any_buf), the stream's image 32 bytes before its end at
+// each 16-byte phase, oracle streams of incompressible, compressible and
+// mixed blocks (a long literal run after compressible data stresses the
+// margin most).
+static int test_inplace_large(std::mt19937 &rng)
+{
+    int bad = 0;
+    static uint8_t IB[66208 + 64];
+    for (uint32_t S : {16384u, 32768u, 65536u}) {
+        const uint32_t E = (S + 2u * S / 255u + 160u + 15u) & ~15u;
+        for (int kind = 0; kind < 4; kind++) {
+            std::vector<uint8_t> m(S);
+            for (uint32_t i = 0; i < S; i++) {
+                const uint8_t r = (uint8_t)rng();
+                m[i] = kind == 0 ? r                                    // incompressible
+                     : kind == 1 ? (uint8_t)((i / 300) & 3)             // long matches
+                     : kind == 2 ? (i < S / 2 ? 0 : r)                  // zeros, then noise
+                                 : ((i / 97) % 3 == 0 ? r : (uint8_t)(i / 1000));
+            }
+            std::vector<uint8_t> oc(lz4_bound(S) + 16);
+            const uint32_t cs = (uint32_t)orc_lz4_compress_block(m.data(), S, oc.data(), oc.size());
+            for (uint32_t ph : {0u, 7u, 15u}) {
+                const uint32_t len = cs + 4, off = (E - len - 32u) & ~15u;
+                memset(IB, 0x5A, sizeof IB);
+                memcpy(IB + off + ph + 4, oc.data(), cs);
+                int rc = -1;
+                run_warp([&] {
+                    int r = lz4_decode_warp(IB + off, ph + 4, cs, IB, S);
+                    if (threadIdx.x == 0) rc = r;
+                });
+                if (rc || memcmp(IB, m.data(), S)) {
+                    fprintf(stderr, "large in-place decode differs S=%u kind=%d phase=%u rc=%d\n", S,
+                            kind, ph, rc);
+                    bad++;
+                }
+            }
+        }
+    }
+    return bad;
+}
+
 static int test_lz4(std::mt19937 &rng, int level, double &gpu_ratio, double &orc_ratio)
 {
     int bad = 0;
@@ -407,6 +450,7 @@ int main()
     double gr0 = 0, gr1 = 0, orr = 0;
     int l0 = test_lz4(rng, 0, gr0, orr);
     int l1 = test_lz4(rng, 1, gr1, orr);
+    l0 += test_inplace_large(rng);
     printf("transpose %d granularity %d shuffle %d lz4 %d %d ratio level0 %.4f level1 %.4f "
            "oracle %.4f\n", t, g, s, l0, l1, gr0, gr1, orr);
     return (t || g || s || l0 || l1) ? 1 : 0;
