@@ -180,6 +180,20 @@ class HostVisCodec:
         return cube + streams + idx, streams + idx + cube + 8 * len(chunks)
 
 
+def chunk_groups(sizes, group_bytes: int):
+    """Consecutive chunks in groups of at most group_bytes (a chunk larger
+    than that is a group of its own): [(first, end), ...] covering all."""
+    groups, i, n = [], 0, len(sizes)
+    while i < n:
+        j, acc = i, 0
+        while j < n and (j == i or acc + sizes[j] <= group_bytes):
+            acc += sizes[j]
+            j += 1
+        groups.append((i, j))
+        i = j
+    return groups
+
+
 class HostBatchCodec:
     """Round trip of many chunks that live in pinned host memory (the batch
     workload: uneven sizes and element widths), in groups of consecutive
@@ -207,15 +221,7 @@ class HostBatchCodec:
         self.es = [int(e) for e in elem_sizes]
         n = len(self.sizes)
         bl = block_elems if isinstance(block_elems, (list, tuple)) else [block_elems] * n
-        self.groups = []
-        i = 0
-        while i < n:
-            j, acc = i, 0
-            while j < n and (j == i or acc + self.sizes[j] <= group_bytes):
-                acc += self.sizes[j]
-                j += 1
-            self.groups.append((i, j))
-            i = j
+        self.groups = chunk_groups(self.sizes, group_bytes)
         self.codecs = []
         for g0, g1 in self.groups:
             xs = [torch.empty(self.sizes[k], dtype=torch.uint8, device=self.dev) for k in range(g0, g1)]
